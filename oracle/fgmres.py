@@ -1,0 +1,82 @@
+"""Oracle: Algorithm 2 line 7 -- split-preconditioned FGMRES on the augmented system.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Eq. (1.2) defines the preconditioned augmented system
+    M_L^-1 Atilde M_R^-1 y = s,   Atilde = [[I, A], [A^T, 0]],
+    M_L^-1 = diag(I, R^-T),   M_R^-1 = diag(I, R^-1),
+solved by flexible GMRES (Saad, SIAM J. Sci. Comput. 14, 1993) because the
+right preconditioner is applied inexactly (precision u_R).  FGMRES keeps the
+preconditioned vectors z_j = M_R^-1 v_j and returns the correction
+d = Z_k y_k = [delta r; delta x] directly; the top block of z_j equals that of
+v_j, so only the bottom n x k block of Z is kept.
+
+Readings where the paper is silent: x0 = 0, no restart, modified
+Gram-Schmidt Arnoldi and Givens rotations in FP64, stop when the residual
+estimate |g_{k+1}| <= tol ||s||, at most ``maxit`` iterations (50 in Sec. 5).
+The products with Atilde, M_L^-1 and M_R^-1 are formed in ``op_dtype``
+(u_A = u_L = u_R).
+"""
+import numpy as np
+
+from .qr import solve_upper, solve_upper_t
+
+
+def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64):
+    """Solve M_L^-1 Atilde M_R^-1 y = [f; h]; return (dr, dx, info)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    m, n = A64.shape
+    Ao = A64.astype(op_dtype)
+    Ro = np.asarray(R, dtype=op_dtype)
+
+    def apply(vtop, vbot):
+        """z = M_R^-1 v (u_R), then w = M_L^-1 Atilde z (u_A, u_L)."""
+        zb = solve_upper(Ro, vbot.astype(op_dtype)).astype(op_dtype)
+        zt = vtop.astype(op_dtype)
+        wt = zt + Ao @ zb
+        wb = solve_upper_t(Ro, (Ao.T @ zt).astype(op_dtype)).astype(op_dtype)
+        return zb.astype(np.float64), np.concatenate([wt, wb]).astype(np.float64)
+
+    rhs = np.concatenate([np.asarray(f, np.float64), np.asarray(h, np.float64)])
+    beta = np.linalg.norm(rhs)
+    info = dict(its=0, relres=0.0, converged=True)
+    if beta == 0:
+        return np.zeros(m), np.zeros(n), info
+    V = np.zeros((m + n, maxit + 1))
+    Zb = np.zeros((n, maxit))
+    H = np.zeros((maxit + 1, maxit))
+    cs = np.zeros(maxit)
+    sn = np.zeros(maxit)
+    g = np.zeros(maxit + 1)
+    g[0] = beta
+    V[:, 0] = rhs / beta
+    k = 0
+    relres = 1.0
+    for j in range(maxit):
+        Zb[:, j], w = apply(V[:m, j], V[m:, j])
+        for i in range(j + 1):                 # modified Gram-Schmidt
+            H[i, j] = np.dot(w, V[:, i])
+            w = w - H[i, j] * V[:, i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] > 0:
+            V[:, j + 1] = w / H[j + 1, j]
+        for i in range(j):                     # previous rotations
+            t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+            H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+            H[i, j] = t
+        den = np.hypot(H[j, j], H[j + 1, j])
+        cs[j] = H[j, j] / den
+        sn[j] = H[j + 1, j] / den
+        H[j, j] = den
+        H[j + 1, j] = 0.0
+        g[j + 1] = -sn[j] * g[j]
+        g[j] = cs[j] * g[j]
+        k = j + 1
+        relres = abs(g[j + 1]) / beta
+        if relres <= tol:
+            break
+    y = solve_upper(H[:k, :k], g[:k])
+    dr = V[:m, :k] @ y
+    dx = Zb[:, :k] @ y
+    info.update(its=k, relres=relres, converged=relres <= tol)
+    return dr, dx, info

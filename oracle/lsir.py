@@ -1,0 +1,96 @@
+"""Oracle: Algorithm 2 -- augmented-system LSIR with randomized preconditioning.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Steps in the paper's order (Alg. 2, Sec. 4):
+  1. x_0 = LSQR(A, b) right-preconditioned by R, started at x_s      (u)
+  2. r_0 = b - A x_0                                                (u)
+  loop i = 0, 1, ...:
+  5. [f_i; g_i] = [b; 0] - [[I, A], [A^T, 0]] [r_i; x_i]             (u_r)
+  6. h_i = R^-T g_i                                                 (u_r)
+  7. FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f_i; h_i], dx = R^-1 dz
+                                                   (u, u_A, u_L, u_R)
+  8. [r_{i+1}; x_{i+1}] = [r_i; x_i] + [dr; dx]                       (u)
+Sec. 5: at most 30 refinement steps; FGMRES at most 50 iterations with the
+LSQR tolerance; if the loop does not converge and kappa(A) < u_s^-1, the
+loop is run again from (x_0, r_0) with u_A = u_L = u_R = u^2.
+
+Stopping.  The paper stops when both forward errors against the true x*, r*
+are <= 4u; ``lsir`` does exactly that when (xstar, rstar) are given.
+Otherwise it uses the computable rule of this build:
+||dx_i|| <= u ||x_{i+1}|| and ||dr_i|| <= u ||r_{i+1}||.
+
+Here u_r is the correctly rounded residual of ``exact.residual_aug`` when
+``ur='exact'`` and plain FP64 otherwise; h_i is solved in FP64.
+"""
+import numpy as np
+
+from . import exact
+from .fgmres import fgmres
+from .lsqr import lsqr
+from .qr import solve_upper_t
+
+
+def _residual(A, b, r, x, ur):
+    if ur == "exact":
+        return exact.residual_aug(A, b, r, x)
+    f = b - r - A @ x
+    g = -(A.T @ r)
+    return f, g
+
+
+def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None, rstar=None):
+    """Steps 4-11 of Alg. 2 from (x0, r0).  Returns (x, r, info)."""
+    x = np.array(x0, np.float64, copy=True)
+    r = np.array(r0, np.float64, copy=True)
+    its, gm_total, converged = 0, 0, False
+    gm_its = []
+    for _ in range(ir_maxit):
+        f, g = _residual(A, b, r, x, ur)
+        h = solve_upper_t(R, g)
+        dr, dx, ginfo = fgmres(A, R, f, h, tol, gm_maxit, op_dtype=op_dtype)
+        x = x + dx
+        r = r + dr
+        its += 1
+        gm_total += ginfo["its"]
+        gm_its.append(ginfo["its"])
+        if xstar is not None:
+            ex, er = exact.forward_errors(x, r, xstar, rstar)
+            done = ex <= 4 * u and er <= 4 * u
+        else:
+            done = (np.linalg.norm(dx) <= u * np.linalg.norm(x)
+                    and np.linalg.norm(dr) <= u * np.linalg.norm(r))
+        if done:
+            converged = True
+            break
+    return x, r, dict(its=its, gmres_total=gm_total, gmres_its=gm_its, converged=converged)
+
+
+def lsir(A, b, R, xs, u, tol, lsqr_maxit=None, ir_maxit=30, gm_maxit=50,
+         w_dtype=np.float64, op_dtype=None, ur="exact", us=None, kappa=None,
+         xstar=None, rstar=None, escalate=True):
+    """Algorithm 2.  ``u`` is the unit roundoff of ``w_dtype``.
+
+    Returns (x, r, info).  ``us`` (unit roundoff of the sketch) and ``kappa``
+    drive the escalation rule of Sec. 5.
+    """
+    A = np.asarray(A, np.float64)
+    b = np.asarray(b, np.float64)
+    n = A.shape[1]
+    if lsqr_maxit is None:
+        lsqr_maxit = 2 * n
+    if op_dtype is None:
+        op_dtype = w_dtype
+    x0, linfo = lsqr(A, b, R, xs, tol, lsqr_maxit, dtype=w_dtype)
+    Aw = A.astype(w_dtype)
+    r0 = (b.astype(w_dtype) - Aw @ x0.astype(w_dtype)).astype(np.float64)
+    x0 = x0.astype(w_dtype).astype(np.float64)
+    x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar, rstar)
+    info["escalated"] = False
+    if (not info["converged"] and escalate and us is not None and kappa is not None
+            and kappa < 1.0 / us):
+        x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, np.float64, ur,
+                            xstar, rstar)
+        info["escalated"] = True
+    info["lsqr"] = linfo
+    return x, r, info

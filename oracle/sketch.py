@@ -1,0 +1,70 @@
+"""Oracle: Algorithm 1 step 1 -- the sketch Y = Omega [A | b] in precision u_s.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+* Sec. 3.2 (one-sided diagonal scaling): each column is scaled before the
+  cast to the low precision, so the largest entry sits near the top of the
+  format's range; the preconditioner becomes R S^-1.  This build's reading
+  uses a power of two d_j per column (exact, so S^-1 is exact), chosen so
+  that max_i |a_ij| d_j lies in [T, 2T) with T = 2^14 for f16/bf16 and
+  T = 2^7 for e4m3 (T = 1, no scaling, for f32/f64).
+* Alg. 1 input: "A stored in precision u_s" -- A_s = fl_s(A D), and the
+  right-hand side is appended as an extra column (its own d_b) so that the
+  same pass also yields Omega b, needed by the sketch-and-solve start
+  x_s = R^-1 Q^T Omega b (Sec. 4).
+* The sketch operand is fl_s(G) from ``oracle.rng``; Omega = s^-1/2 fl_s(G).
+* The product of the rounded operands is accumulated in FP64 here (a library
+  matmul is one step); the scale s^-1/2 and D^-1 are applied afterwards.
+"""
+import numpy as np
+
+from . import rng
+
+#: power-of-two target T for the largest entry of each scaled column
+SCALE_TARGET_LOG2 = {"f64": None, "f32": None, "f16": 14, "bf16": 14, "e4m3": 7}
+
+
+def column_scale_exponents(M, fmt):
+    """Integer exponents k_j with max_i |M_ij| 2^k_j in [2^t, 2^(t+1)).
+
+    Columns that are entirely zero get k_j = 0.  Formats without scaling
+    return zeros.
+    """
+    M = np.asarray(M, dtype=np.float64)
+    t = SCALE_TARGET_LOG2[fmt]
+    if t is None:
+        return np.zeros(M.shape[1], dtype=np.int64)
+    cmax = np.abs(M).max(axis=0)
+    _, ex = np.frexp(cmax)                 # cmax = f 2^ex, f in [0.5, 1)
+    k = t - (ex.astype(np.int64) - 1)
+    return np.where(cmax == 0, 0, k)
+
+
+def cast_scaled(A, b, fmt):
+    """Return (A_s, b_s, kA, kb): fl_s(A 2^kA), fl_s(b 2^kb) as FP64 arrays."""
+    Ab = np.concatenate([np.asarray(A, dtype=np.float64),
+                         np.asarray(b, dtype=np.float64).reshape(-1, 1)], axis=1)
+    k = column_scale_exponents(Ab, fmt)
+    As = rng.round_to_format(np.ldexp(Ab, k[None, :]), fmt)
+    return As[:, :-1], As[:, -1], k[:-1], int(k[-1])
+
+
+def sketch(A, b, s, seed, fmt):
+    """Y = Omega [A | b] with Omega = s^-1/2 fl_s(G), A and b cast to ``fmt``.
+
+    Returns Y (s x (n+1), FP64) already unscaled: column j is divided by the
+    power of two 2^k_j used for the cast, so Y approximates Omega [A | b].
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    As, bs, kA, kb = cast_scaled(A, b, fmt)
+    Ab = np.concatenate([As, bs.reshape(-1, 1)], axis=1)
+    Y = np.zeros((s, n + 1))
+    step = 1 << 14
+    for j0 in range(0, m, step):           # blocks of A's rows; FP64 accumulation
+        j1 = min(m, j0 + step)
+        Gs = rng.sketch_operand(s, j0, j1, seed, fmt)
+        Y += Gs @ Ab[j0:j1]
+    Y *= 1.0 / np.sqrt(float(s))
+    k = np.concatenate([kA, [kb]])
+    return np.ldexp(Y, -k[None, :])

@@ -1,0 +1,148 @@
+"""Pins for the oracle's Algorithm 1: sketch (step 1) and Householder R (step 2)."""
+import numpy as np
+import pytest
+
+from lsq_synth import randsvd_problem, paper_problem
+from oracle import qr, rng, sketch, theory
+
+
+def _explicit_omega(s, m, seed, fmt="f64"):
+    return rng.round_to_format(rng.gaussian_block(0, s, 0, m, seed), fmt) / np.sqrt(s)
+
+
+def test_column_scale_puts_column_max_in_target_binade():
+    r = np.random.default_rng(0)
+    M = r.standard_normal((50, 7)) * np.array([1e-30, 1e-5, 1, 3, 1e5, 1e20, 0.0])
+    for fmt, t in (("f16", 14), ("bf16", 14), ("e4m3", 7)):
+        k = sketch.column_scale_exponents(M, fmt)
+        cm = np.abs(np.ldexp(M, k[None, :])).max(axis=0)
+        assert np.all((cm[:-1] >= 2.0 ** t) & (cm[:-1] < 2.0 ** (t + 1)))
+        assert k[-1] == 0                       # an all-zero column is left alone
+    assert np.all(sketch.column_scale_exponents(M, "f32") == 0)
+
+
+def test_sketch_f64_is_omega_times_data():
+    P = randsvd_problem(300, 6, 1e3, seed=1)
+    Y = sketch.sketch(P.A, P.b, 24, 5, "f64")
+    Om = _explicit_omega(24, 300, 5)
+    ref = Om @ np.column_stack([P.A, P.b])
+    assert np.allclose(Y, ref, rtol=0, atol=1e-13 * (np.abs(Om) @ np.abs(np.column_stack([P.A, P.b]))).max())
+
+
+def test_sketch_cast_error_within_paper_model():
+    """Sec. 3.2: ||Delta_s|| <= u_s ||A|| ||Omega|| (+ product term, here FP64 and negligible)."""
+    P = randsvd_problem(2000, 20, 1e2, seed=2)
+    Y64 = sketch.sketch(P.A, P.b, 80, 1, "f64")
+    for fmt in ("bf16", "f16", "e4m3"):
+        Ys = sketch.sketch(P.A, P.b, 80, 1, fmt)
+        Om = _explicit_omega(80, 2000, 1, fmt)
+        Ab = np.column_stack([P.A, P.b])
+        # the rounded Omega is a fixed sketch; the cast of A is the error term
+        ref = Om @ Ab
+        err = np.linalg.norm(Ys - ref, 2)
+        us = rng.UNIT_ROUNDOFF[fmt]
+        bound = us * np.linalg.norm(Ab, 2) * np.linalg.norm(Om, 2) * np.sqrt(Ab.shape[1])
+        assert err <= bound
+        assert err > 0
+        assert np.linalg.norm(Y64 - Ys, 2) > 0
+
+
+def test_sketch_preserves_norms_in_expectation():
+    r = np.random.default_rng(3)
+    x = r.standard_normal((4000, 1))
+    vals = []
+    for seed in range(40):
+        y = sketch.sketch(x, np.zeros(4000), 32, seed, "f64")[:, 0]
+        vals.append(np.dot(y, y) / np.dot(x[:, 0], x[:, 0]))
+    vals = np.array(vals)
+    # E ||Omega x||^2 = ||x||^2; Var = 2/s per draw
+    assert abs(vals.mean() - 1) < 4 * np.sqrt(2 / 32 / len(vals))
+
+
+def test_householder_r_matches_lapack_up_to_row_signs():
+    r = np.random.default_rng(4)
+    Y = r.standard_normal((60, 9))
+    R, c = qr.householder_qr(Y, 8)
+    Rl = np.linalg.qr(Y[:, :8], mode="r")
+    Rl = Rl * np.where(np.diag(Rl) < 0, -1.0, 1.0)[:, None]
+    assert np.allclose(R, Rl, atol=1e-12)
+    Q, _ = np.linalg.qr(Y[:, :8])
+    cl = (Q.T @ Y[:, 8]) * np.where(np.diag(np.linalg.qr(Y[:, :8], mode="r")) < 0, -1.0, 1.0)
+    assert np.allclose(c, cl, atol=1e-12)
+    assert np.all(np.diag(R) >= 0) and np.allclose(np.tril(R, -1), 0)
+    assert np.allclose(R.T @ R, Y[:, :8].T @ Y[:, :8], atol=1e-11)
+
+
+def test_householder_closed_forms_small_n():
+    y = np.array([[3.0, 1.0], [4.0, 2.0]])
+    R, c = qr.householder_qr(y, 1)
+    assert R.shape == (1, 1) and abs(R[0, 0] - 5.0) < 1e-15     # n = 1: R = ||y||
+    assert abs(c[0] - (3 * 1 + 4 * 2) / 5.0) < 1e-15            # q^T b
+    Y = np.array([[1.0, 1.0], [0.0, 1.0], [1.0, 0.0]])
+    R, _ = qr.householder_qr(Y, 2)
+    # Gram-Schmidt by hand: r11 = sqrt2, r12 = 1/sqrt2, r22 = sqrt(3/2)
+    assert np.allclose(R, [[np.sqrt(2), 1 / np.sqrt(2)], [0, np.sqrt(1.5)]], atol=1e-15)
+
+
+def test_householder_float32_backward_error():
+    r = np.random.default_rng(6)
+    Y = r.standard_normal((200, 40)) @ np.diag(np.logspace(0, -3, 40))
+    R, _ = qr.householder_qr(Y, 40, dtype=np.float32)
+    err = np.linalg.norm(R.T @ R - Y.T @ Y) / np.linalg.norm(Y) ** 2
+    assert err < 200 * 40 * 2.0 ** -24
+
+
+def test_sketch_and_solve_is_sketched_lstsq():
+    P = randsvd_problem(500, 8, 1e2, seed=7)
+    Y = sketch.sketch(P.A, P.b, 32, 3, "f64")
+    R, c = qr.householder_qr(Y, 8)
+    xs = qr.sketch_and_solve(R, c)
+    ref = np.linalg.lstsq(Y[:, :8], Y[:, 8], rcond=None)[0]
+    assert np.allclose(xs, ref, rtol=1e-12, atol=1e-12 * np.linalg.norm(ref))
+
+
+def test_preconditioned_kappa_equals_kappa_omega_u():
+    """Sec. 2: kappa(A R^-1) = kappa(Omega U), ||A R^-1|| = ||(Omega U)^+|| (exact sketch)."""
+    P = randsvd_problem(800, 10, 1e3, seed=8)
+    Y = sketch.sketch(P.A, P.b, 40, 9, "f64")
+    R, _ = qr.householder_qr(Y, 10)
+    sv = np.linalg.svd(P.A @ np.linalg.inv(R), compute_uv=False)
+    U = np.linalg.svd(P.A, full_matrices=False)[0]
+    so = np.linalg.svd(_explicit_omega(40, 800, 9) @ U, compute_uv=False)
+    assert abs(sv[0] / sv[-1] - so[0] / so[-1]) < 1e-9 * so[0] / so[-1]
+    assert abs(sv[0] - 1 / so[-1]) < 1e-9 * sv[0]
+    assert abs(1 / sv[-1] - so[0]) < 1e-9 * so[0]
+
+
+def test_paper_good_regime_values(golden):
+    """Fig. 3(b)/4(c): ||AR^-1|| ~ 2.03, ||(AR^-1)^+|| ~ 1.46, kappa ~ 2.97 (m=1000, n=100, s=4n)."""
+    vals = {r[0]: float(r[1]) for r in golden("paper_fig3_good_regime.txt")}
+    na, npv, ka = [], [], []
+    for seed in range(3):
+        P = paper_problem(1e2, seed=seed)
+        Y = sketch.sketch(P.A, P.b, 400, seed, "f32")
+        R, _ = qr.householder_qr(Y, 100, dtype=np.float32)
+        sv = np.linalg.svd(P.A @ np.linalg.inv(R), compute_uv=False)
+        na.append(sv[0]); npv.append(1 / sv[-1]); ka.append(sv[0] / sv[-1])
+    assert abs(np.mean(na) - vals["norm_AR"]) < 0.1 * vals["norm_AR"]
+    assert abs(np.mean(npv) - vals["norm_AR_pinv"]) < 0.05 * vals["norm_AR_pinv"]
+    assert abs(np.mean(ka) - vals["kappa_AR"]) < 0.1 * vals["kappa_AR"]
+    # and the Marchenko-Pastur limits at n/s = 1/4 (2, 1.5, 3) hold to ~10%
+    mp = theory.mp_limits(100, 400)
+    assert abs(np.mean(ka) - mp[2]) < 0.1 * mp[2]
+
+
+def test_low_precision_sketch_degrades_as_paper_predicts():
+    """Sec. 3.4 / Fig. 3(a): kappa(A) u_s >> 1 makes ||(A R^-1)^+|| grow; << 1 keeps it ~1.5."""
+    P = paper_problem(1e6, seed=1)
+    out = {}
+    for fmt in ("f32", "bf16"):
+        Y = sketch.sketch(P.A, P.b, 400, 1, fmt)
+        R, _ = qr.householder_qr(Y, 100)
+        sv = np.linalg.svd(P.A @ np.linalg.inv(R), compute_uv=False)
+        out[fmt] = 1 / sv[-1]
+    assert out["f32"] < 1.7
+    assert out["bf16"] > 20 * out["f32"]
+    # Corollary bound of Sec. 3.4: ||(A R_s^-1)^+|| <= (1 + sqrt(n) u_s kappa) ||Omega||
+    Om = _explicit_omega(400, 1000, 1, "bf16")
+    assert out["bf16"] <= (1 + np.sqrt(100) * 2.0 ** -8 * 1e6) * np.linalg.norm(Om, 2)
