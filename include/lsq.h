@@ -1,0 +1,204 @@
+/*
+ * lsq.h -- C ABI of the GB300 (sm_103a) mixed-precision sketch-and-precondition
+ * least-squares solver.
+ *
+ * Method: Carson & Dauzickaite, "Mixed precision sketching for least-squares
+ * problems and its application in GMRES-based iterative refinement",
+ * arXiv 2410.06319.  The problem is min_x ||b - A x||_2 with A (m x n) of full
+ * rank and m >> n (Sec. 1, Eq. 1.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A is a DEVICE pointer to FP64, row-major, m rows, row stride opts->lda
+ *   (elements, >= n; 0 means n).  b is a DEVICE pointer to m FP64 values.
+ *   All array arguments are caller-owned device buffers; the library never
+ *   frees them and writes only the outputs named in each call.
+ * - The handle owns its workspace (device memory, grown on demand) and runs
+ *   everything on the CUDA stream given to lsq_create.  Every call below
+ *   synchronises that stream once before it returns, so outputs and the info
+ *   struct are valid on return.
+ * - Arguments are validated before any launch: 1 <= n <= m, n <= s <= m,
+ *   tol > 0 and finite, supported precisions, non-null pointers, n <= 1024.
+ *   A bad argument returns LSQ_E_INVAL and writes nothing.
+ * - Numerical outcomes are statuses, never aborts: iteration caps give
+ *   LSQ_NOT_CONVERGED with the last iterate written; device-side waits that
+ *   run out give LSQ_E_TIMEOUT; CUDA errors give LSQ_E_CUDA.
+ * - The common argument tuple is (A, b, m, n, s, u_s, u_p, u_w, u_r, tol,
+ *   seed): u_s = sketch precision (Alg. 1 step 1), u_p = QR precision u_QR
+ *   (Alg. 1 step 2), u_w = working precision u (Alg. 2), u_r = residual
+ *   precision (Alg. 2 lines 5-6), tol = LSQR and FGMRES tolerance (Sec. 5),
+ *   seed = key of the Philox4x32-10 stream that defines the sketch matrix.
+ *   A call ignores the members of the tuple it does not use.
+ *
+ * Sketch matrix.  Omega = s^-1/2 fl_s(G) (Sec. 2 Gaussian embedding, Sec. 5
+ * scaling).  G[i, j] (i < s, j < m) is Box-Muller in FP64 of one word pair of
+ * Philox4x32-10(counter = (j>>2, i, j>>34, 0), key = (seed lo, seed hi));
+ * words 0,1 serve j%4 in {0,1} (cos, sin), words 2,3 serve j%4 in {2,3};
+ * U1 = (a+1) 2^-32, U2 = b 2^-32; ln and cos/sin(2 pi U2) are fixed IEEE
+ * double sequences (no FMA); fl_s rounds to nearest-even.  G is never stored.
+ */
+#ifndef LSQ_H
+#define LSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Precisions.  F16 = IEEE half (the paper's "half"), BF16 and E4M3 are the
+ * GB300 tensor-core formats (sketch only), F32 = single, F64 = double. */
+typedef enum lsq_prec {
+  LSQ_F64 = 0,
+  LSQ_F32 = 1,
+  LSQ_F16 = 2,
+  LSQ_BF16 = 3,
+  LSQ_E4M3 = 4
+} lsq_prec;
+
+typedef enum lsq_status {
+  LSQ_OK = 0,
+  LSQ_NOT_CONVERGED = 1,   /* iteration cap reached; last iterate written */
+  LSQ_E_INVAL = -1,        /* bad argument; nothing written */
+  LSQ_E_RANK = -2,         /* R has a zero (or non-finite) diagonal entry */
+  LSQ_E_BREAKDOWN = -3,
+  LSQ_E_NONFINITE = -4,    /* non-finite value met in a stage output */
+  LSQ_E_CUDA = -5,         /* a CUDA call failed (see lsq_last_cuda_error) */
+  LSQ_E_TIMEOUT = -6,      /* a bounded device-side wait ran out */
+  LSQ_E_NOMEM = -7,        /* workspace allocation failed */
+  LSQ_E_UNSUPPORTED = -8   /* valid but not supported on this device/build */
+} lsq_status;
+
+/* info.flags bits */
+#define LSQ_WARN_COND 1     /* kappa_est(R) * u_s >= 1: outside Thm 3.1 (Sec. 3.4) */
+#define LSQ_INFO_ESCALATED 2 /* refinement re-run with u_A = u_L = u_R = u_r (Sec. 5) */
+
+typedef struct lsq_handle lsq_handle;
+
+/* Options.  Zero-initialised fields mean "default" (see lsq_opts_default). */
+typedef struct lsq_opts {
+  int64_t lda;            /* row stride of A in elements; 0 -> n */
+  int32_t lsqr_maxit;     /* LSQR cap; 0 -> 2n (Sec. 5) */
+  int32_t ir_maxit;       /* refinement cap; 0 -> 30 (Sec. 5) */
+  int32_t gmres_maxit;    /* FGMRES cap per refinement step; 0 -> 50 (Sec. 5) */
+  int32_t no_escalate;    /* 1 disables the Sec. 5 re-run with u_A=u_L=u_R=u^2 */
+  int32_t no_colscale;    /* 1 disables the power-of-two column scaling (Sec. 3.2) */
+  int32_t ir_stop;        /* 0: stop when ||dx|| <= u||x|| and ||dr|| <= u||r|| */
+  int32_t reserved0;
+  double gmres_tol;       /* FGMRES relative-residual tolerance; 0 -> tol */
+  double kappa_hint;      /* kappa(A) for the escalation rule; 0 -> estimate from R */
+  const double* Y_in;     /* optional device sketch, s x (n+1) column-major (ld = s):
+                             skips the sketch inside lsq_qr_r/lsq_lsqr/lsq_lsir */
+  const double* R_in;     /* optional device R, n x n column-major upper triangular:
+                             skips sketch and QR inside lsq_lsqr/lsq_lsir */
+  const double* x0_in;    /* optional device LSQR start (n); used with R_in */
+} lsq_opts;
+
+/* Diagnostics of one call. */
+typedef struct lsq_info {
+  int32_t status;
+  int32_t flags;
+  int32_t lsqr_its;
+  int32_t lsqr_flag;        /* 1: ||r|| <= tol||b||, 2: ||Ahat^T r|| test, 3: breakdown, 0: cap */
+  int32_t ir_its;
+  int32_t gmres_its_total;
+  int32_t escalated;
+  int32_t ir_converged;
+  int32_t gmres_its[32];    /* FGMRES iterations of each refinement step */
+  double lsqr_normr;        /* ||b - A x|| estimate at LSQR exit */
+  double lsqr_normar;       /* ||Ahat^T r|| estimate at LSQR exit */
+  double lsqr_normA;        /* Frobenius-type ||Ahat|| estimate */
+  double kappa_R_est;       /* max|r_ii| / min|r_ii| (a lower bound on kappa(R)) */
+  double ir_dx_rel;         /* ||dx|| / ||x|| of the last refinement step */
+  double ir_dr_rel;         /* ||dr|| / ||r|| of the last refinement step */
+  double stage_ms[8];       /* cast, sketch, qr, lsqr, residual, fgmres, update, total */
+  int64_t gpu_launches;     /* kernels launched by the call */
+} lsq_info;
+
+/* sizeof(lsq_opts) for which = 0, sizeof(lsq_info) for which = 1, else 0: lets
+ * bindings check their struct layouts without a GPU. */
+size_t lsq_sizeof(int which);
+
+/* Fills *o with the defaults (all zero = defaults). */
+void lsq_opts_default(lsq_opts* o);
+
+/* Creates a handle bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Ownership of *h goes to
+ * the caller, who releases it with lsq_destroy. */
+lsq_status lsq_create(lsq_handle** h, void* cuda_stream);
+lsq_status lsq_destroy(lsq_handle* h);
+
+/* Human-readable name of a status; last CUDA error text seen by the handle. */
+const char* lsq_status_string(lsq_status st);
+const char* lsq_last_cuda_error(const lsq_handle* h);
+
+/*
+ * lsq_sketch -- Algorithm 1 step 1 (Sec. 3): Y = Omega [A | b] in precision
+ * u_s, with the one-sided power-of-two column scaling of Sec. 3.2 (on unless
+ * opts->no_colscale) applied before the cast and removed from Y afterwards.
+ * F16/BF16 use tcgen05 kind::f16 tensor cores, E4M3 kind::f8f6f4, all with
+ * FP32 accumulation per split of the m range and an FP64 sum of the splits;
+ * F32 and F64 use CUDA cores in that precision.
+ * Out: Y, device FP64, s x (n+1) column-major with leading dimension s; its
+ * last column is Omega b (used for x_s = R^-1 Q^T Omega b, Sec. 4).
+ */
+lsq_status lsq_sketch(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                      int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
+                      double tol, uint64_t seed, const lsq_opts* opts, double* Y);
+
+/*
+ * lsq_qr_r -- Algorithm 1 step 2: Householder QR of Y[:, :n] in precision
+ * u_p (F32 or F64), reflectors also applied to Y[:, n].  R is normalised to a
+ * non-negative diagonal.  Y is computed by lsq_sketch unless opts->Y_in.
+ * Out: R, device FP64 n x n column-major (ld = n), upper triangular, values
+ * representable in u_p; xs (device, n) = R^-1 (Q^T Omega b), the
+ * sketch-and-solve start of Alg. 2 (Sec. 4).  Either output may be NULL.
+ */
+lsq_status lsq_qr_r(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                    int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
+                    double tol, uint64_t seed, const lsq_opts* opts, double* R, double* xs);
+
+/*
+ * lsq_lsqr -- Algorithm 2 line 1: LSQR (Paige & Saunders 1982) on A R^-1
+ * in working precision u_w (F32 or F64), started from x_s (or opts->x0_in),
+ * at most opts->lsqr_maxit (2n) iterations, stopping tests
+ * ||r|| <= tol ||b|| or ||Ahat^T r|| <= tol ||Ahat||_est ||r||.
+ * Each iteration reads A once (fused A t and A^T q pass) and solves with R
+ * and R^T once each.
+ * Out: x (device FP64, n).  info may be NULL.
+ */
+lsq_status lsq_lsqr(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                    int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
+                    double tol, uint64_t seed, const lsq_opts* opts, double* x, lsq_info* info);
+
+/*
+ * lsq_lsir -- Algorithm 2: LSQR start, then augmented-system refinement:
+ * [f; g] = [b; 0] - [[I, A], [A^T, 0]] [r; x] in u_r (F64), h = R^-T g in u_r,
+ * split-preconditioned FGMRES (Eq. 1.2; products with Atilde, M_L^-1, M_R^-1
+ * in u_w, Arnoldi and Givens in FP64), update in FP64.  Stops when
+ * ||dx|| <= u_w ||x|| and ||dr|| <= u_w ||r||, or after opts->ir_maxit steps;
+ * then, if not converged and kappa < 1/u_s (kappa_hint, else kappa_est(R)),
+ * re-runs the refinement from the LSQR result with the FGMRES products in
+ * FP64 (Sec. 5).
+ * Out: x (device FP64, n) and r = b - A x (device FP64, m; may be NULL).
+ */
+lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                    int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
+                    double tol, uint64_t seed, const lsq_opts* opts, double* x, double* r,
+                    lsq_info* info);
+
+/*
+ * lsq_omega -- the sketch operand fl_s(G)[i, j] for i in [0, s) and
+ * j in [j0, j0 + cols), written as FP64 to `out` (device, row-major s x cols),
+ * computed by the same device code the sketch kernels use (fast FP32
+ * evaluation with the FP64 definition as fallback near rounding boundaries).
+ * For testing that the in-kernel Gaussian is the defined one, bit for bit.
+ */
+lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_prec u_s,
+                     uint64_t seed, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSQ_H */

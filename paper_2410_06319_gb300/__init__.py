@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) mixed-precision sketch-and-precondition least squares.
+
+Python binding of the C ABI in ``include/lsq.h`` (Carson & Dauzickaite,
+arXiv 2410.06319: Algorithm 1 -- sketch and Householder R; Algorithm 2 --
+R-preconditioned LSQR and FGMRES-based augmented-system refinement).
+
+The functions ``lsq_sketch``, ``lsq_qr_r``, ``lsq_lsqr``, ``lsq_lsir`` and
+``lsq_omega`` keep the C names and arguments; they only marshal arguments
+(torch CUDA tensors or raw device pointers) and call the library, whose
+kernels do all the work.  Importing this module fails loudly if the CUDA
+library has not been built; there is no fallback.
+"""
+from ._lib import (  # noqa: F401
+    PREC, STATUS, Handle, Info, LsqError, Opts, lib, lsq_lsir, lsq_lsqr, lsq_omega, lsq_qr_r,
+    lsq_sketch, library_path, declared_functions,
+)

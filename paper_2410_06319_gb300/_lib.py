@@ -1,0 +1,191 @@
+"""ctypes marshalling for liblsq.so (see include/lsq.h for every contract)."""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "lsq.h")
+
+
+def library_path():
+    return os.path.join(HERE, "_lib", "liblsq.so")
+
+
+if not os.path.exists(library_path()):
+    raise ImportError(
+        "liblsq.so is not built: run `python paper_2410_06319_gb300/build.py` "
+        "(or __graft_entry__.build()); the solver has no non-CUDA fallback")
+
+lib = ctypes.CDLL(library_path())
+
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4}
+STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RANK",
+          -3: "LSQ_E_BREAKDOWN", -4: "LSQ_E_NONFINITE", -5: "LSQ_E_CUDA", -6: "LSQ_E_TIMEOUT",
+          -7: "LSQ_E_NOMEM", -8: "LSQ_E_UNSUPPORTED"}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("lda", ctypes.c_int64), ("lsqr_maxit", ctypes.c_int32),
+                ("ir_maxit", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
+                ("no_escalate", ctypes.c_int32), ("no_colscale", ctypes.c_int32),
+                ("ir_stop", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
+                ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("lsqr_its", ctypes.c_int32), ("lsqr_flag", ctypes.c_int32),
+                ("ir_its", ctypes.c_int32), ("gmres_its_total", ctypes.c_int32),
+                ("escalated", ctypes.c_int32), ("ir_converged", ctypes.c_int32),
+                ("gmres_its", ctypes.c_int32 * 32),
+                ("lsqr_normr", ctypes.c_double), ("lsqr_normar", ctypes.c_double),
+                ("lsqr_normA", ctypes.c_double), ("kappa_R_est", ctypes.c_double),
+                ("ir_dx_rel", ctypes.c_double), ("ir_dr_rel", ctypes.c_double),
+                ("stage_ms", ctypes.c_double * 8), ("gpu_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["gmres_its"] = list(self.gmres_its)[: max(0, self.ir_its)]
+        d["stage_ms"] = dict(zip(["cast", "sketch", "qr", "lsqr", "residual", "fgmres", "update",
+                                  "total"], list(self.stage_ms)))
+        return d
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_TUPLE = [_P, _P, _P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+          ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(Opts)]
+lib.lsq_create.argtypes = [ctypes.POINTER(_P), _P]
+lib.lsq_destroy.argtypes = [_P]
+lib.lsq_status_string.argtypes = [ctypes.c_int]
+lib.lsq_status_string.restype = ctypes.c_char_p
+lib.lsq_last_cuda_error.argtypes = [_P]
+lib.lsq_last_cuda_error.restype = ctypes.c_char_p
+lib.lsq_opts_default.argtypes = [ctypes.POINTER(Opts)]
+lib.lsq_sizeof.argtypes = [ctypes.c_int]
+lib.lsq_sizeof.restype = ctypes.c_size_t
+lib.lsq_sketch.argtypes = _TUPLE + [_P]
+lib.lsq_qr_r.argtypes = _TUPLE + [_P, _P]
+lib.lsq_lsqr.argtypes = _TUPLE + [_P, ctypes.POINTER(Info)]
+lib.lsq_lsir.argtypes = _TUPLE + [_P, _P, ctypes.POINTER(Info)]
+lib.lsq_omega.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_uint64, _P]
+for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir",
+           "lsq_omega"):
+    getattr(lib, _f).restype = ctypes.c_int
+
+
+def declared_functions():
+    """Names of the functions declared in include/lsq.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsq_[a-z_0-9]+)\s*\(", text)))
+
+
+class LsqError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} {detail}".strip())
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (checked: CUDA, contiguous) or a raw int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+class Handle:
+    """Owns an lsq_handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = _P()
+        st = lib.lsq_create(ctypes.byref(self._h), _P(stream))
+        if st != 0:
+            raise LsqError(st, "lsq_create")
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def last_cuda_error(self):
+        return lib.lsq_last_cuda_error(self._h).decode()
+
+    def close(self):
+        if self._h:
+            lib.lsq_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _opts(opts):
+    if opts is None:
+        return Opts()
+    if isinstance(opts, Opts):
+        return opts
+    o = Opts()
+    for k, v in opts.items():
+        if k in ("Y_in", "R_in", "x0_in"):
+            v = _ptr(v)
+        setattr(o, k, v)
+    return o
+
+
+def _check(h, st, where, allow=(0, 1)):
+    if st not in allow:
+        raise LsqError(st, where, h.last_cuda_error() if st == -5 else "")
+    return st
+
+
+def _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts):
+    o = _opts(opts)
+    return [h.ptr, _ptr(A), _ptr(b), m, n, s, _prec(u_s), _prec(u_p), _prec(u_w), _prec(u_r),
+            float(tol), int(seed), ctypes.byref(o)], o
+
+
+def lsq_sketch(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, Y):
+    args, _o = _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts)
+    return _check(h, lib.lsq_sketch(*args, _ptr(Y)), "lsq_sketch")
+
+
+def lsq_qr_r(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, R, xs):
+    args, _o = _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts)
+    return _check(h, lib.lsq_qr_r(*args, _ptr(R), _ptr(xs)), "lsq_qr_r")
+
+
+def lsq_lsqr(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, x, info=None):
+    args, _o = _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts)
+    info = info if info is not None else Info()
+    st = _check(h, lib.lsq_lsqr(*args, _ptr(x), ctypes.byref(info)), "lsq_lsqr")
+    return st, info
+
+
+def lsq_lsir(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, x, r, info=None):
+    args, _o = _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts)
+    info = info if info is not None else Info()
+    st = _check(h, lib.lsq_lsir(*args, _ptr(x), _ptr(r), ctypes.byref(info)), "lsq_lsir")
+    return st, info
+
+
+def lsq_omega(h, s, j0, cols, u_s, seed, out):
+    return _check(h, lib.lsq_omega(h.ptr, s, j0, cols, _prec(u_s), int(seed), _ptr(out)),
+                  "lsq_omega", allow=(0,))

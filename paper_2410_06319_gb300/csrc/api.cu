@@ -1,0 +1,795 @@
+// C ABI (include/lsq.h) and host orchestration of Algorithms 1 and 2.
+//
+// Everything runs on the handle's stream.  Iterative stages keep their
+// scalars on the device; the host enqueues iterations in batches and reads a
+// small state block once per batch (kernels of an iteration that starts after
+// convergence exit immediately).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gauss.cuh"
+#include "iter.h"
+#include "kernels.h"
+#include "lsq.h"
+
+namespace {
+
+using namespace lsq;
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+struct StatusFail {
+  lsq_status st;
+};
+
+#define CK(expr)                                     \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) throw CudaFail{e_, #expr}; \
+  } while (0)
+
+constexpr int kBatch = 8;        // iterations enqueued between host checks
+constexpr int kMaxGmres = 127;   // cap of the FGMRES basis size
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lsq_handle {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::unordered_map<std::string, Buf> bufs;
+  int* d_err = nullptr;
+  unsigned char* h_pinned = nullptr;   // 4 KB pinned host block for state reads
+  std::string last_cuda;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> events;
+  size_t next_event = 0;
+  struct Mark {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+};
+
+namespace {
+
+void* ws(lsq_handle* h, const char* name, size_t bytes, bool zero = false) {
+  if (bytes == 0) bytes = 16;
+  Buf& b = h->bufs[name];
+  if (b.bytes < bytes) {
+    if (b.p) CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw StatusFail{LSQ_E_NOMEM};
+    }
+    b.bytes = bytes;
+    CK(cudaMemsetAsync(b.p, 0, bytes, h->stream));
+  } else if (zero) {
+    CK(cudaMemsetAsync(b.p, 0, bytes, h->stream));
+  }
+  return b.p;
+}
+
+cudaEvent_t next_event(lsq_handle* h) {
+  if (h->next_event == h->events.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->events.push_back(e);
+  }
+  return h->events[h->next_event++];
+}
+
+struct StageTimer {
+  lsq_handle* h;
+  int stage;
+  cudaEvent_t a;
+  StageTimer(lsq_handle* hh, int s) : h(hh), stage(s) {
+    a = next_event(h);
+    CK(cudaEventRecord(a, h->stream));
+  }
+  ~StageTimer() {
+    try {
+      cudaEvent_t b = next_event(h);
+      if (cudaEventRecord(b, h->stream) == cudaSuccess) h->marks.push_back({stage, a, b});
+    } catch (...) {
+    }
+  }
+};
+
+enum Stage { ST_CAST = 0, ST_SKETCH, ST_QR, ST_LSQR, ST_RES, ST_FGMRES, ST_UPDATE, ST_TOTAL };
+
+int fmt_of(lsq_prec p) {
+  switch (p) {
+    case LSQ_F64: return FMT_F64;
+    case LSQ_F32: return FMT_F32;
+    case LSQ_F16: return FMT_F16;
+    case LSQ_BF16: return FMT_BF16;
+    case LSQ_E4M3: return FMT_E4M3;
+  }
+  return -1;
+}
+
+double unit_roundoff(lsq_prec p) {
+  switch (p) {
+    case LSQ_F64: return std::ldexp(1.0, -53);
+    case LSQ_F32: return std::ldexp(1.0, -24);
+    case LSQ_F16: return std::ldexp(1.0, -11);
+    case LSQ_BF16: return std::ldexp(1.0, -8);
+    case LSQ_E4M3: return std::ldexp(1.0, -4);
+  }
+  return 1.0;
+}
+
+int64_t round_up(int64_t v, int64_t q) { return ((v + q - 1) / q) * q; }
+
+struct Ctx {
+  lsq_handle* h;
+  const double* A;
+  const double* b;
+  int64_t m, n, s, lda, lda32;
+  lsq_prec us, up, uw, ur;
+  double tol;
+  uint64_t seed;
+  lsq_opts o;
+  cudaStream_t st;
+  int nblk;        // pass grid
+  int nblk2;       // vector-kernel grid
+};
+
+#define L(expr)         \
+  do {                  \
+    CK(expr);           \
+    ++c.h->launches;    \
+  } while (0)
+
+lsq_status validate(const Ctx& c, bool need_b) {
+  if (!c.h) return LSQ_E_INVAL;
+  if (!c.A || (need_b && !c.b)) return LSQ_E_INVAL;
+  if (c.n < 1 || c.m < c.n || c.s < c.n || c.s > c.m) return LSQ_E_INVAL;
+  if (c.n > 1024 || c.s > 16384) return LSQ_E_INVAL;
+  if (c.m > ((int64_t)1 << 36)) return LSQ_E_INVAL;
+  if (c.lda < c.n) return LSQ_E_INVAL;
+  if (!(c.tol > 0.0) || !std::isfinite(c.tol)) return LSQ_E_INVAL;
+  if (fmt_of(c.us) < 0) return LSQ_E_INVAL;
+  if (c.up != LSQ_F32 && c.up != LSQ_F64) return LSQ_E_INVAL;
+  if (c.uw != LSQ_F32 && c.uw != LSQ_F64) return LSQ_E_INVAL;
+  if (c.ur != LSQ_F64) return LSQ_E_INVAL;
+  if (c.o.gmres_maxit < 0 || c.o.gmres_maxit > kMaxGmres) return LSQ_E_INVAL;
+  if (c.o.ir_maxit < 0 || c.o.ir_maxit > 32) return LSQ_E_INVAL;
+  if (c.o.lsqr_maxit < 0) return LSQ_E_INVAL;
+  return LSQ_OK;
+}
+
+Ctx make_ctx(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+             lsq_prec us, lsq_prec up, lsq_prec uw, lsq_prec ur, double tol, uint64_t seed,
+             const lsq_opts* opts) {
+  Ctx c{};
+  c.h = h;
+  c.A = A;
+  c.b = b;
+  c.m = m;
+  c.n = n;
+  c.s = s;
+  c.us = us;
+  c.up = up;
+  c.uw = uw;
+  c.ur = ur;
+  c.tol = tol;
+  c.seed = seed;
+  if (opts) c.o = *opts;
+  else std::memset(&c.o, 0, sizeof(c.o));
+  c.lda = c.o.lda > 0 ? c.o.lda : n;
+  c.lda32 = round_up(n, 4);
+  if (h) {
+    c.st = h->stream;
+    c.nblk = pass_blocks(h->num_sms);
+    c.nblk2 = 2 * h->num_sms;
+  }
+  return c;
+}
+
+void check_dev_error(lsq_handle* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(h->h_pinned, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(&e, h->h_pinned, sizeof(int));
+  if (e != 0) {
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    throw StatusFail{LSQ_E_TIMEOUT};
+  }
+}
+
+template <typename S>
+S read_state(Ctx& c, const S* d) {
+  S s;
+  CK(cudaMemcpyAsync(c.h->h_pinned, d, sizeof(S), cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  std::memcpy(&s, c.h->h_pinned, sizeof(S));
+  return s;
+}
+
+double read_scalar(Ctx& c, const double* d) { return read_state<double>(c, d); }
+
+// -------------------------------------------------------------- stages
+// Pass 1 (column maxima and, for u_w = F32, the FP32 working copy of A).
+float* stage_cast(Ctx& c) {
+  StageTimer t(c.h, ST_CAST);
+  auto* cmax = static_cast<unsigned long long*>(ws(c.h, "cmax", (c.n + 1) * 8, true));
+  float* a32 = nullptr;
+  if (c.uw == LSQ_F32) a32 = static_cast<float*>(ws(c.h, "a32", (size_t)c.m * c.lda32 * 4));
+  L(launch_colmax_a32(c.A, c.lda, c.b, c.m, c.n, cmax, a32, c.lda32, c.st));
+  return a32;
+}
+
+// Alg. 1 step 1 -> Y (s x (n+1), column-major, FP64).
+void stage_sketch(Ctx& c, double* Y) {
+  const int fmt = fmt_of(c.us);
+  const int64_t ncols = c.n + 1;
+  auto* cmax = static_cast<unsigned long long*>(ws(c.h, "cmax", ncols * 8));
+  int* kexp = static_cast<int*>(ws(c.h, "kexp", ncols * 4));
+  if (fmt == FMT_F16 || fmt == FMT_BF16 || fmt == FMT_E4M3) {
+    SketchPlan p;
+    if (!plan_sketch_tc(fmt, c.s, c.m, ncols, c.h->num_sms, &p)) throw StatusFail{LSQ_E_UNSUPPORTED};
+    const int t = c.o.no_colscale ? -1 : (fmt == FMT_E4M3 ? 7 : 14);
+    const int eb = (fmt == FMT_E4M3) ? 1 : 2;
+    const int64_t ldb = round_up(c.m, 16 / eb);
+    const int64_t rows = (int64_t)p.ngroups * p.bn;
+    void* Bt;
+    {
+      StageTimer tt(c.h, ST_CAST);
+      L(launch_scale_exps(cmax, ncols, t, kexp, c.st));
+      Bt = ws(c.h, "bt", (size_t)rows * ldb * eb);
+      L(launch_cast_transpose(fmt, c.A, c.lda, c.b, c.m, c.n, kexp, Bt, ldb, rows, c.st));
+    }
+    StageTimer tt(c.h, ST_SKETCH);
+    CUtensorMap tm;
+    if (!encode_bt_tmap(&tm, Bt, fmt, rows, c.m, ldb, p.bn / p.nsub)) throw StatusFail{LSQ_E_UNSUPPORTED};
+    float* partial = static_cast<float*>(ws(c.h, "partial", (size_t)p.splits * ncols * p.s_pad * 4));
+    L(launch_sketch_tc(p, tm, c.seed, partial, c.h->d_err, c.st));
+    L(launch_sketch_reduce(partial, false, p.splits, ncols, c.s, p.s_pad, kexp, Y, c.st));
+  } else {
+    StageTimer tt(c.h, ST_SKETCH);
+    const int64_t base = ((c.s + 15) / 16) * ((ncols + 255) / 256);
+    int64_t splits = (8 * (int64_t)c.h->num_sms + base - 1) / base;
+    const int64_t ksteps = (c.m + 15) / 16;
+    if (splits > ksteps) splits = ksteps;
+    if (splits < 1) splits = 1;
+    const int64_t kchunk = ((ksteps + splits - 1) / splits) * 16;
+    splits = (c.m + kchunk - 1) / kchunk;
+    const size_t esz = (fmt == FMT_F64) ? 8 : 4;
+    void* partial = ws(c.h, "partial", (size_t)splits * ncols * c.s * esz);
+    L(launch_sketch_cc(fmt, c.A, c.lda, c.b, c.m, c.n, c.s, c.seed, (int)splits, kchunk, partial, c.s,
+                       c.st));
+    L(launch_sketch_reduce(partial, fmt == FMT_F64, (int)splits, ncols, c.s, c.s, nullptr, Y, c.st));
+  }
+}
+
+struct RCopies {
+  float *R32, *L32;
+  double *R64, *L64;
+  double* kappa;
+};
+
+RCopies stage_prepare_r(Ctx& c, const double* R) {
+  RCopies r;
+  const size_t nn = (size_t)c.n * c.n;
+  r.R32 = static_cast<float*>(ws(c.h, "R32", nn * 4));
+  r.L32 = static_cast<float*>(ws(c.h, "L32", nn * 4));
+  r.R64 = static_cast<double*>(ws(c.h, "R64", nn * 8));
+  r.L64 = static_cast<double*>(ws(c.h, "L64", nn * 8));
+  r.kappa = static_cast<double*>(ws(c.h, "kappaR", 8));
+  L(launch_prepare_r(R, c.n, r.R32, r.L32, r.R64, r.L64, r.kappa, c.st));
+  return r;
+}
+
+// Alg. 1 step 2 -> R (n x n) and c; then x_s = R^-1 c in u_QR.
+void stage_qr(Ctx& c, const double* Y, double* R, double* xs, RCopies* rc) {
+  {
+    StageTimer t(c.h, ST_QR);
+    const bool f64 = (c.up == LSQ_F64);
+    void* work = ws(c.h, "qrwork", (size_t)c.s * (c.n + 1) * (f64 ? 8 : 4));
+    double* aux = static_cast<double*>(ws(c.h, "qraux", (2 * c.n + 8) * 8));
+    unsigned* bar = static_cast<unsigned*>(ws(c.h, "qrbar", 64));
+    double* cvec = static_cast<double*>(ws(c.h, "qrc", c.n * 8));
+    L(launch_qr(f64, Y, c.s, c.n, work, aux, bar, R, cvec, c.h->d_err, c.h->num_sms, c.st));
+    c.h->launches += 2;
+    *rc = stage_prepare_r(c, R);
+    if (xs) {
+      if (f64) L((launch_trsv<double, double, double>(true, rc->R64, c.n, cvec, 1.0, xs, nullptr, c.st)));
+      else L((launch_trsv<float, double, double>(true, rc->R32, c.n, cvec, 1.0, xs, nullptr, c.st)));
+    }
+  }
+}
+
+struct LsqrOut {
+  LsqrState st;
+};
+
+// Alg. 2 line 1: preconditioned LSQR in working precision W from x0 -> x.
+template <typename W>
+LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const W* Rw, const W* Lw, const double* x0,
+                     double* x) {
+  StageTimer tmr(c.h, ST_LSQR);
+  const int64_t n = c.n, m = c.m;
+  const int64_t nvec = round_up(n, 4) + 4;
+  W* bw;
+  if constexpr (sizeof(W) == 4) {
+    bw = static_cast<W*>(ws(c.h, "b32", m * 4));
+    L((launch_axpby<double, double, float>(c.b, 1.0, nullptr, 0.0, bw, m, c.st)));
+  } else {
+    bw = const_cast<double*>(c.b);
+  }
+  W* u = static_cast<W*>(ws(c.h, "lsqr_u", m * sizeof(W)));
+  W* t = static_cast<W*>(ws(c.h, "lsqr_t", nvec * sizeof(W)));
+  W* sv = static_cast<W*>(ws(c.h, "lsqr_s", nvec * sizeof(W)));
+  W* vt = static_cast<W*>(ws(c.h, "lsqr_vt", nvec * sizeof(W)));
+  W* v = static_cast<W*>(ws(c.h, "lsqr_v", nvec * sizeof(W)));
+  W* w = static_cast<W*>(ws(c.h, "lsqr_w", nvec * sizeof(W)));
+  W* z = static_cast<W*>(ws(c.h, "lsqr_z", nvec * sizeof(W)));
+  for (W* vec : {t, sv, vt, v, w, z}) CK(cudaMemsetAsync(vec, 0, nvec * sizeof(W), c.st));
+  W* P = static_cast<W*>(ws(c.h, "pblk", (size_t)c.nblk * n * sizeof(W)));
+  double* sq = static_cast<double*>(ws(c.h, "sq", c.nblk * 8));
+  double* part = static_cast<double*>(ws(c.h, "part", c.nblk2 * 8));
+  LsqrState* dst = static_cast<LsqrState*>(ws(c.h, "lsqr_state", sizeof(LsqrState)));
+  const int maxit = c.o.lsqr_maxit > 0 ? c.o.lsqr_maxit : (int)(2 * n);
+  LsqrState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.tol = c.tol;
+  hs.maxit = maxit;
+  std::memcpy(c.h->h_pinned + 2048, &hs, sizeof(hs));
+  CK(cudaMemcpyAsync(dst, c.h->h_pinned + 2048, sizeof(hs), cudaMemcpyHostToDevice, c.st));
+  L(launch_dot(c.b, c.b, m, part, c.nblk2, &dst->normb, true, c.st));
+  c.h->launches += 1;
+  // u = b - A x0, A^T u  (t = -x0 so that q = A t + 1 * b)
+  L((launch_axpby<double, double, W>(x0, -1.0, nullptr, 0.0, t, n, c.st)));
+  L(launch_pass_lsqr_any<W>(Aw, ldw, m, n, t, bw, nullptr, 1.0, u, P, sq, c.nblk, nullptr, c.st));
+  L(launch_lsqr_beta(sq, c.nblk, dst, true, c.st));
+  L((launch_colsum<W, W>(P, c.nblk, n, &dst->us, 1.0, sv, nullptr, c.st)));
+  L((launch_trsv<W, W, W>(false, Lw, n, sv, 1.0, vt, nullptr, c.st)));
+  L(launch_lsqr_init<W>(vt, n, v, w, z, dst, c.st));
+  int done = 0, its = 0;
+  LsqrState out{};
+  while (!done) {
+    for (int k = 0; k < kBatch; ++k) {
+      const int* dn = &dst->done;
+      L((launch_trsv<W, W, W>(true, Rw, n, v, 1.0, t, dn, c.st)));
+      L(launch_pass_lsqr_any<W>(Aw, ldw, m, n, t, u, &dst->cu, 1.0, u, P, sq, c.nblk, dn, c.st));
+      L(launch_lsqr_beta(sq, c.nblk, dst, false, c.st));
+      L((launch_colsum<W, W>(P, c.nblk, n, &dst->us, 1.0, sv, dn, c.st)));
+      L((launch_trsv<W, W, W>(false, Lw, n, sv, 1.0, vt, dn, c.st)));
+      L(launch_lsqr_update<W>(vt, n, v, w, z, dst, c.st));
+    }
+    out = read_state<LsqrState>(c, dst);
+    done = out.done;
+    its = out.its;
+    if (its > maxit + kBatch) break;  // defensive: the device flag ends the loop
+  }
+  // x = x0 + R^-1 z
+  L((launch_trsv<W, W, W>(true, Rw, n, z, 1.0, t, nullptr, c.st)));
+  L((launch_axpby<W, double, double>(t, 1.0, x0, 1.0, x, n, c.st)));
+  return out;
+}
+
+struct GmOut {
+  int its;
+  double relres;
+  double dr2, r2, dx2, x2;
+};
+
+// Alg. 2 line 7: FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (operator
+// products in TOP), x0 = 0; r += dr, x += dx.
+template <typename TOP>
+GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const TOP* Lop,
+                   const double* f, const double* hv, double tol, int maxit, double* r, double* x) {
+  StageTimer tmr(c.h, ST_FGMRES);
+  const int64_t m = c.m, n = c.n, ld = m + n;
+  const int ldh = maxit + 1;
+  double* V = static_cast<double*>(ws(c.h, "gmV", (size_t)ld * (maxit + 1) * 8));
+  TOP* Zb = static_cast<TOP*>(ws(c.h, "gmZ", (size_t)(round_up(n, 4) + 4) * (maxit + 1) * sizeof(TOP)));
+  const int64_t ldz = round_up(n, 4) + 4;
+  double* wv = static_cast<double*>(ws(c.h, "gmW", ld * 8));
+  TOP* P = static_cast<TOP*>(ws(c.h, "gmP", (size_t)c.nblk * n * sizeof(TOP)));
+  TOP* sb = static_cast<TOP*>(ws(c.h, "gmS", (round_up(n, 4) + 4) * sizeof(TOP)));
+  CK(cudaMemsetAsync(Zb, 0, (size_t)(round_up(n, 4) + 4) * (maxit + 1) * sizeof(TOP), c.st));
+  CK(cudaMemsetAsync(sb, 0, (round_up(n, 4) + 4) * sizeof(TOP), c.st));
+  double* H = static_cast<double*>(ws(c.h, "gmH", (size_t)ldh * maxit * 8, true));
+  double* cs = static_cast<double*>(ws(c.h, "gmcs", (maxit + 1) * 8));
+  double* sn = static_cast<double*>(ws(c.h, "gmsn", (maxit + 1) * 8));
+  double* g = static_cast<double*>(ws(c.h, "gmg", (maxit + 2) * 8, true));
+  double* y = static_cast<double*>(ws(c.h, "gmy", (maxit + 1) * 8));
+  double* hh = static_cast<double*>(ws(c.h, "gmhh", (maxit + 1) * 8));
+  double* Dp = static_cast<double*>(ws(c.h, "gmDp", (size_t)c.nblk2 * (maxit + 1) * 8));
+  double* sqp = static_cast<double*>(ws(c.h, "gmsq", c.nblk2 * 8));
+  double* p4 = static_cast<double*>(ws(c.h, "gmp4", 4 * c.nblk2 * 8));
+  double* nrm = static_cast<double*>(ws(c.h, "gmnrm", 4 * 8));
+  GmState* gst = static_cast<GmState*>(ws(c.h, "gm_state", sizeof(GmState)));
+  GmState hs{};
+  hs.tol = tol;
+  hs.maxit = maxit;
+  std::memcpy(c.h->h_pinned + 2048, &hs, sizeof(hs));
+  CK(cudaMemcpyAsync(gst, c.h->h_pinned + 2048, sizeof(hs), cudaMemcpyHostToDevice, c.st));
+  L(launch_gm_rhs(f, hv, m, n, V, sqp, c.nblk2, c.st));
+  L(launch_gm_init(sqp, c.nblk2, gst, g, c.st));
+  L(launch_gm_scale0(V, ld, gst, c.nblk2, c.st));
+  const int maxc = maxit + 1;
+  int j = 0;
+  GmState out{};
+  while (j < maxit) {
+    const int jend = std::min(maxit, j + kBatch);
+    for (; j < jend; ++j) {
+      const int* dn = &gst->done;
+      const double* vj = V + (int64_t)j * ld;
+      TOP* zj = Zb + (int64_t)j * ldz;
+      L((launch_trsv<TOP, double, TOP>(true, Rop, n, vj + m, 1.0, zj, dn, c.st)));
+      L(launch_pass_fgm<TOP>(Aop, ldop, m, n, zj, vj, nullptr, wv, P, c.nblk, dn, c.st));
+      L((launch_colsum<TOP, TOP>(P, c.nblk, n, nullptr, 1.0, sb, dn, c.st)));
+      L((launch_trsv<TOP, TOP, double>(false, Lop, n, sb, 1.0, wv + m, dn, c.st)));
+      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+        L(launch_gm_mdot(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st));
+        L(launch_gm_hsum(Dp, c.nblk2, maxc, gst, hh, H, ldh, c.st));
+        L(launch_gm_axpy(V, ld, hh, wv, ld, gst, pass == 1 ? sqp : nullptr, c.nblk2, c.st));
+      }
+      L(launch_gm_finish(sqp, c.nblk2, gst, H, ldh, cs, sn, g, c.st));
+      L(launch_gm_newcol(wv, ld, gst, V, ld, c.nblk2, c.st));
+    }
+    out = read_state<GmState>(c, gst);
+    if (out.done) break;
+  }
+  StageTimer tu(c.h, ST_UPDATE);
+  L(launch_gm_solve(gst, H, ldh, g, y, c.st));
+  L(launch_gm_apply<double>(V, ld, m, gst, y, r, p4, p4 + c.nblk2, c.nblk2, c.st));
+  L(launch_gm_apply<TOP>(Zb, ldz, n, gst, y, x, p4 + 2 * c.nblk2, p4 + 3 * c.nblk2, c.nblk2, c.st));
+  for (int k = 0; k < 4; ++k) L(launch_sum_partials(p4 + k * c.nblk2, c.nblk2, nrm + k, true, c.st));
+  double hn[4];
+  CK(cudaMemcpyAsync(c.h->h_pinned, nrm, 32, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  std::memcpy(hn, c.h->h_pinned, 32);
+  GmOut go;
+  go.its = out.j;
+  go.relres = out.relres;
+  go.dr2 = hn[0];
+  go.r2 = hn[1];
+  go.dx2 = hn[2];
+  go.x2 = hn[3];
+  return go;
+}
+
+// Steps 4-11 of Alg. 2 from (x0, r0), FGMRES products in TOP.
+template <typename TOP>
+bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const TOP* Lop,
+                  const RCopies& rc, double* x, double* r, lsq_info* info) {
+  const int64_t m = c.m, n = c.n;
+  double* f = static_cast<double*>(ws(c.h, "ir_f", m * 8));
+  double* gv = static_cast<double*>(ws(c.h, "ir_g", (n + 4) * 8));
+  double* hv = static_cast<double*>(ws(c.h, "ir_h", (n + 4) * 8));
+  double* P = static_cast<double*>(ws(c.h, "respblk", (size_t)c.nblk * n * 8));
+  const int irmax = c.o.ir_maxit > 0 ? c.o.ir_maxit : 30;
+  const int gmax = c.o.gmres_maxit > 0 ? c.o.gmres_maxit : 50;
+  const double gtol = c.o.gmres_tol > 0 ? c.o.gmres_tol : c.tol;
+  const double u = unit_roundoff(c.uw);
+  bool converged = false;
+  info->ir_its = 0;
+  info->gmres_its_total = 0;
+  for (int i = 0; i < irmax; ++i) {
+    {
+      StageTimer t(c.h, ST_RES);
+      L(launch_pass_res(c.A, c.lda, m, n, x, r, c.b, f, P, c.nblk, c.st));
+      L((launch_colsum<double, double>(P, c.nblk, n, nullptr, 1.0, gv, nullptr, c.st)));
+      L((launch_trsv<double, double, double>(false, rc.L64, n, gv, 1.0, hv, nullptr, c.st)));
+    }
+    GmOut go = stage_fgmres<TOP>(c, Aop, ldop, Rop, Lop, f, hv, gtol, gmax, r, x);
+    info->gmres_its[i] = go.its;
+    info->gmres_its_total += go.its;
+    info->ir_its = i + 1;
+    info->ir_dx_rel = go.x2 > 0 ? go.dx2 / go.x2 : 0.0;
+    info->ir_dr_rel = go.r2 > 0 ? go.dr2 / go.r2 : 0.0;
+    if (!std::isfinite(go.x2) || !std::isfinite(go.r2)) throw StatusFail{LSQ_E_NONFINITE};
+    if (go.dx2 <= u * go.x2 && go.dr2 <= u * go.r2) {
+      converged = true;
+      break;
+    }
+  }
+  return converged;
+}
+
+void finish_timing(lsq_handle* h, lsq_info* info) {
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) {
+    for (int k = 0; k < 8; ++k) info->stage_ms[k] = 0.0;
+    for (auto& mk : h->marks) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, mk.a, mk.b));
+      info->stage_ms[mk.stage] += ms;
+    }
+  }
+  h->marks.clear();
+  h->next_event = 0;
+}
+
+lsq_status run_guarded(lsq_handle* h, lsq_info* info, const std::function<lsq_status()>& fn) {
+  lsq_status st;
+  const int64_t l0 = h->launches;
+  try {
+    h->marks.clear();
+    h->next_event = 0;
+    st = fn();
+    check_dev_error(h);
+    finish_timing(h, info);
+  } catch (const CudaFail& f) {
+    h->last_cuda = std::string(f.what) + ": " + cudaGetErrorString(f.e);
+    cudaGetLastError();
+    st = LSQ_E_CUDA;
+    h->marks.clear();
+    h->next_event = 0;
+  } catch (const StatusFail& f) {
+    st = f.st;
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    h->marks.clear();
+    h->next_event = 0;
+  }
+  if (info) {
+    info->status = st;
+    info->gpu_launches = h->launches - l0;
+  }
+  return st;
+}
+
+// Common front part of lsq_lsqr / lsq_lsir: sketch + QR (or R_in), LSQR.
+struct Front {
+  RCopies rc;
+  double* x0;       // start of LSQR (x_s or x0_in or 0)
+  float* a32;
+  LsqrState ls;
+};
+
+Front run_front(Ctx& c, double* x, lsq_info* info) {
+  Front fr{};
+  fr.a32 = stage_cast(c);
+  double* R;
+  fr.x0 = static_cast<double*>(ws(c.h, "x0", (c.n + 4) * 8));
+  if (c.o.R_in) {
+    R = const_cast<double*>(c.o.R_in);
+    fr.rc = stage_prepare_r(c, R);
+    if (c.o.x0_in) CK(cudaMemcpyAsync(fr.x0, c.o.x0_in, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
+    else CK(cudaMemsetAsync(fr.x0, 0, c.n * 8, c.st));
+  } else {
+    const double* Y = c.o.Y_in;
+    if (!Y) {
+      double* Yw = static_cast<double*>(ws(c.h, "Y", (size_t)c.s * (c.n + 1) * 8));
+      stage_sketch(c, Yw);
+      Y = Yw;
+    }
+    R = static_cast<double*>(ws(c.h, "R", (size_t)c.n * c.n * 8));
+    stage_qr(c, Y, R, fr.x0, &fr.rc);
+    if (c.o.x0_in) CK(cudaMemcpyAsync(fr.x0, c.o.x0_in, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
+  }
+  const double kap = read_scalar(c, fr.rc.kappa);
+  info->kappa_R_est = kap;
+  if (!(kap < INFINITY)) throw StatusFail{LSQ_E_RANK};
+  if (kap * unit_roundoff(c.us) >= 1.0) info->flags |= LSQ_WARN_COND;
+  if (c.uw == LSQ_F32)
+    fr.ls = stage_lsqr<float>(c, fr.a32, c.lda32, fr.rc.R32, fr.rc.L32, fr.x0, x);
+  else
+    fr.ls = stage_lsqr<double>(c, c.A, c.lda, fr.rc.R64, fr.rc.L64, fr.x0, x);
+  info->lsqr_its = fr.ls.its;
+  info->lsqr_flag = fr.ls.flag;
+  info->lsqr_normr = fr.ls.normr;
+  info->lsqr_normar = fr.ls.normar;
+  info->lsqr_normA = fr.ls.normA;
+  return fr;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+size_t lsq_sizeof(int which) {
+  if (which == 0) return sizeof(lsq_opts);
+  if (which == 1) return sizeof(lsq_info);
+  return 0;
+}
+
+void lsq_opts_default(lsq_opts* o) {
+  if (o) std::memset(o, 0, sizeof(*o));
+}
+
+const char* lsq_status_string(lsq_status st) {
+  switch (st) {
+    case LSQ_OK: return "LSQ_OK";
+    case LSQ_NOT_CONVERGED: return "LSQ_NOT_CONVERGED";
+    case LSQ_E_INVAL: return "LSQ_E_INVAL";
+    case LSQ_E_RANK: return "LSQ_E_RANK";
+    case LSQ_E_BREAKDOWN: return "LSQ_E_BREAKDOWN";
+    case LSQ_E_NONFINITE: return "LSQ_E_NONFINITE";
+    case LSQ_E_CUDA: return "LSQ_E_CUDA";
+    case LSQ_E_TIMEOUT: return "LSQ_E_TIMEOUT";
+    case LSQ_E_NOMEM: return "LSQ_E_NOMEM";
+    case LSQ_E_UNSUPPORTED: return "LSQ_E_UNSUPPORTED";
+  }
+  return "LSQ_UNKNOWN";
+}
+
+const char* lsq_last_cuda_error(const lsq_handle* h) { return h ? h->last_cuda.c_str() : ""; }
+
+lsq_status lsq_create(lsq_handle** out, void* cuda_stream) {
+  if (!out) return LSQ_E_INVAL;
+  *out = nullptr;
+  auto* h = new (std::nothrow) lsq_handle();
+  if (!h) return LSQ_E_NOMEM;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return LSQ_E_CUDA;
+  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaMalloc(&h->d_err, 64) != cudaSuccess || cudaMemset(h->d_err, 0, 64) != cudaSuccess ||
+      cudaMallocHost(&h->h_pinned, 4096) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->d_err) cudaFree(h->d_err);
+    delete h;
+    return LSQ_E_NOMEM;
+  }
+  *out = h;
+  return LSQ_OK;
+}
+
+lsq_status lsq_destroy(lsq_handle* h) {
+  if (!h) return LSQ_E_INVAL;
+  cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  for (auto e : h->events) cudaEventDestroy(e);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  delete h;
+  return LSQ_OK;
+}
+
+lsq_status lsq_sketch(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+                      lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol, uint64_t seed,
+                      const lsq_opts* opts, double* Y) {
+  Ctx c = make_ctx(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts);
+  lsq_status v = validate(c, true);
+  if (v != LSQ_OK) return v;
+  if (!Y) return LSQ_E_INVAL;
+  c.uw = LSQ_F64;  // no FP32 working copy needed
+  return run_guarded(h, nullptr, [&]() {
+    stage_cast(c);
+    stage_sketch(c, Y);
+    return LSQ_OK;
+  });
+}
+
+lsq_status lsq_qr_r(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+                    lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol, uint64_t seed,
+                    const lsq_opts* opts, double* R, double* xs) {
+  Ctx c = make_ctx(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts);
+  if (c.o.Y_in && !c.A) c.A = c.o.Y_in;  // A is not read when Y is given
+  lsq_status v = validate(c, !c.o.Y_in);
+  if (v != LSQ_OK) return v;
+  return run_guarded(h, nullptr, [&]() {
+    const double* Y = c.o.Y_in;
+    if (!Y) {
+      c.uw = LSQ_F64;
+      stage_cast(c);
+      double* Yw = static_cast<double*>(ws(c.h, "Y", (size_t)c.s * (c.n + 1) * 8));
+      stage_sketch(c, Yw);
+      Y = Yw;
+    }
+    double* Rw = R ? R : static_cast<double*>(ws(c.h, "R", (size_t)c.n * c.n * 8));
+    RCopies rc;
+    stage_qr(c, Y, Rw, xs, &rc);
+    const double kap = read_scalar(c, rc.kappa);
+    if (!(kap < INFINITY)) return LSQ_E_RANK;
+    return LSQ_OK;
+  });
+}
+
+lsq_status lsq_lsqr(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+                    lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol, uint64_t seed,
+                    const lsq_opts* opts, double* x, lsq_info* info) {
+  Ctx c = make_ctx(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts);
+  lsq_status v = validate(c, true);
+  if (v != LSQ_OK) return v;
+  if (!x) return LSQ_E_INVAL;
+  lsq_info local;
+  lsq_info* inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  return run_guarded(h, inf, [&]() {
+    StageTimer tt(c.h, ST_TOTAL);
+    Front fr = run_front(c, x, inf);
+    return fr.ls.flag != 0 ? LSQ_OK : LSQ_NOT_CONVERGED;
+  });
+}
+
+lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+                    lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol, uint64_t seed,
+                    const lsq_opts* opts, double* x, double* r, lsq_info* info) {
+  Ctx c = make_ctx(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts);
+  lsq_status v = validate(c, true);
+  if (v != LSQ_OK) return v;
+  if (!x) return LSQ_E_INVAL;
+  lsq_info local;
+  lsq_info* inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  return run_guarded(h, inf, [&]() {
+    StageTimer tt(c.h, ST_TOTAL);
+    double* x0 = static_cast<double*>(ws(c.h, "ir_x0", (c.n + 4) * 8));
+    Front fr = run_front(c, x0, inf);
+    double* rr = r ? r : static_cast<double*>(ws(c.h, "ir_r", c.m * 8));
+    double* r0 = static_cast<double*>(ws(c.h, "ir_r0", c.m * 8));
+    // r0 = b - A x0 in the working precision (Alg. 2 line 2)
+    {
+      StageTimer t(c.h, ST_RES);
+      const int64_t nvec = round_up(c.n, 4) + 4;
+      double* sq = static_cast<double*>(ws(c.h, "sq", c.nblk * 8));
+      if (c.uw == LSQ_F32) {
+        float* t32 = static_cast<float*>(ws(c.h, "lsqr_t", nvec * 4));
+        CK(cudaMemsetAsync(t32, 0, nvec * 4, c.st));
+        float* q = static_cast<float*>(ws(c.h, "lsqr_u", c.m * 4));
+        float* b32 = static_cast<float*>(ws(c.h, "b32", c.m * 4));
+        float* P = static_cast<float*>(ws(c.h, "pblk", (size_t)c.nblk * c.n * 4));
+        L((launch_axpby<double, double, float>(x0, -1.0, nullptr, 0.0, t32, c.n, c.st)));
+        L(launch_pass_lsqr_any<float>(fr.a32, c.lda32, c.m, c.n, t32, b32, nullptr, 1.0, q, P, sq,
+                                      c.nblk, nullptr, c.st));
+        L((launch_axpby<float, double, double>(q, 1.0, nullptr, 0.0, r0, c.m, c.st)));
+      } else {
+        double* t64 = static_cast<double*>(ws(c.h, "lsqr_t", nvec * 8));
+        CK(cudaMemsetAsync(t64, 0, nvec * 8, c.st));
+        double* P = static_cast<double*>(ws(c.h, "pblk", (size_t)c.nblk * c.n * 8));
+        L((launch_axpby<double, double, double>(x0, -1.0, nullptr, 0.0, t64, c.n, c.st)));
+        L(launch_pass_lsqr_any<double>(c.A, c.lda, c.m, c.n, t64, c.b, nullptr, 1.0, r0, P, sq, c.nblk,
+                                       nullptr, c.st));
+      }
+    }
+    CK(cudaMemcpyAsync(x, x0, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
+    CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
+    bool conv;
+    if (c.uw == LSQ_F32)
+      conv = stage_refine<float>(c, fr.a32, c.lda32, fr.rc.R32, fr.rc.L32, fr.rc, x, rr, inf);
+    else
+      conv = stage_refine<double>(c, c.A, c.lda, fr.rc.R64, fr.rc.L64, fr.rc, x, rr, inf);
+    const double kap = c.o.kappa_hint > 0 ? c.o.kappa_hint : inf->kappa_R_est;
+    if (!conv && !c.o.no_escalate && kap < 1.0 / unit_roundoff(c.us) && c.uw == LSQ_F32) {
+      // Sec. 5: re-run the refinement from (x0, r0) with u_A = u_L = u_R = u^2 (FP64 here)
+      CK(cudaMemcpyAsync(x, x0, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
+      CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
+      inf->escalated = 1;
+      inf->flags |= LSQ_INFO_ESCALATED;
+      conv = stage_refine<double>(c, c.A, c.lda, fr.rc.R64, fr.rc.L64, fr.rc, x, rr, inf);
+    }
+    inf->ir_converged = conv ? 1 : 0;
+    return conv ? LSQ_OK : LSQ_NOT_CONVERGED;
+  });
+}
+
+lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_prec u_s, uint64_t seed,
+                     double* out) {
+  if (!h || !out || s < 1 || cols < 1 || j0 < 0 || s > ((int64_t)1 << 31) || fmt_of(u_s) < 0)
+    return LSQ_E_INVAL;
+  return run_guarded(h, nullptr, [&]() {
+    CK(launch_omega(fmt_of(u_s), s, j0, cols, seed, out, h->stream));
+    ++h->launches;
+    return LSQ_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// The sketch matrix G of Omega = s^-1/2 fl_s(G), generated on the fly.
+//
+// Definition (Sec. 2 Gaussian embedding with N(0, 1/s) entries; Sec. 5 uses
+// Omega = (4n)^-1/2 G): G[i, j] for sketch row i and data row j is
+//   (x0, x1, x2, x3) = Philox4x32-10(counter = (j>>2, i, j>>34, 0),
+//                                    key = (seed lo, seed hi))        [SC'11]
+//   (a, b) = (x0, x1) if j%4 < 2 else (x2, x3)
+//   U1 = (a + 1) 2^-32,  U2 = b 2^-32,  R = sqrt(-2 ln U1)
+//   G = R cos(2 pi U2) for even j, R sin(2 pi U2) for odd j; G = +0 if a = 2^32-1
+// with ln and (cos, sin)(2 pi U2) evaluated by the fixed IEEE double sequences
+// spec_ln_u1 / spec_cos_sin_2pi below (no fused multiply-add).  The operand
+// used by a sketch in precision u_s is fl_s(G), round to nearest even.
+//
+// Evaluation on GB300: FP64 is a slow pipe, so G is first evaluated in FP32
+// (fast_*) with a relative error below 2^-21 against the FP64 definition;
+// if both ends of [g32 (1 - 2^-19), g32 (1 + 2^-19)] round to the same u_s
+// value, that value is fl_s(G) exactly.  Otherwise the FP64 definition is
+// evaluated and rounded (round-to-odd to FP32, then to u_s: a single
+// rounding of the FP64 value).  The result is bit-identical to rounding the
+// FP64 definition directly.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+namespace lsq {
+
+enum SFmt : int { FMT_F64 = 0, FMT_F32 = 1, FMT_F16 = 2, FMT_BF16 = 3, FMT_E4M3 = 4 };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Counter of the Philox call serving sketch row i, data rows 4q .. 4q+3.
+__device__ __forceinline__ uint4 gauss_counter(uint64_t q, uint32_t i) {
+  return make_uint4((uint32_t)q, i, (uint32_t)(q >> 32), 0u);
+}
+
+// ------------------------------------------------------------ FP64 definition
+__device__ __forceinline__ double spec_ln_u1(uint32_t a) {
+  // U1 = 2^e f, f in [sqrt(1/2), sqrt(2)); ln f = 2 atanh(z), z = (f-1)/(f+1),
+  // series 2z (1 + w/3 + ... + w^11/23), w = z^2, Horner with separate * and +.
+  const double u1 = (double)((uint64_t)a + 1ull) * 0x1p-32;
+  const long long bits = __double_as_longlong(u1);
+  double e = (double)((int)((bits >> 52) & 0x7FF) - 1023);
+  double f = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  if (f > 1.4142135623730951) {
+    f = __dmul_rn(f, 0.5);
+    e = __dadd_rn(e, 1.0);
+  }
+  const double z = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
+  const double w = __dmul_rn(z, z);
+  double p = 1.0 / 23.0;
+  p = __dadd_rn(1.0 / 21.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 19.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 17.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 15.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 13.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 11.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 9.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 7.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 5.0, __dmul_rn(w, p));
+  p = __dadd_rn(1.0 / 3.0, __dmul_rn(w, p));
+  const double z2 = __dmul_rn(z, 2.0);
+  const double lnf = __dadd_rn(z2, __dmul_rn(z2, __dmul_rn(w, p)));
+  return __dadd_rn(__dmul_rn(e, 0.6931471805599453), lnf);
+}
+
+__device__ __forceinline__ void spec_cos_sin_2pi(uint32_t b, double& c, double& s) {
+  // 4 U2 = q + r, r moved to [-1/2, 1/2); phi = r (pi/2); Taylor series of sin
+  // and cos to phi^21 / phi^20 (Horner, separate * and +); rotate by q.
+  uint32_t q = b >> 30;
+  int32_t rb = (int32_t)(b & 0x3FFFFFFFu);
+  if (rb >= (1 << 29)) {
+    rb -= (1 << 30);
+    q = (q + 1u) & 3u;
+  }
+  const double r = (double)rb * 0x1p-30;
+  const double phi = __dmul_rn(r, 1.5707963267948966);
+  const double w = __dmul_rn(phi, phi);
+  double ps = 1.0 / 51090942171709440000.0;           // +1/21!
+  ps = __dadd_rn(-1.0 / 121645100408832000.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(1.0 / 355687428096000.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(-1.0 / 1307674368000.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(1.0 / 6227020800.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(-1.0 / 39916800.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(1.0 / 362880.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(-1.0 / 5040.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(1.0 / 120.0, __dmul_rn(w, ps));
+  ps = __dadd_rn(-1.0 / 6.0, __dmul_rn(w, ps));
+  const double sphi = __dadd_rn(phi, __dmul_rn(phi, __dmul_rn(w, ps)));
+  double pc = 1.0 / 2432902008176640000.0;            // +1/20!
+  pc = __dadd_rn(-1.0 / 6402373705728000.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(1.0 / 20922789888000.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(-1.0 / 87178291200.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(1.0 / 479001600.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(-1.0 / 3628800.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(1.0 / 40320.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(-1.0 / 720.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(1.0 / 24.0, __dmul_rn(w, pc));
+  pc = __dadd_rn(-1.0 / 2.0, __dmul_rn(w, pc));
+  const double cphi = __dadd_rn(1.0, __dmul_rn(w, pc));
+  switch (q) {
+    case 0: c = cphi; s = sphi; break;
+    case 1: c = -sphi; s = cphi; break;
+    case 2: c = -cphi; s = -sphi; break;
+    default: c = sphi; s = -cphi; break;
+  }
+}
+
+__device__ __forceinline__ void spec_gauss_pair(uint32_t a, uint32_t b, double& ge, double& go) {
+  if (a == 0xFFFFFFFFu) {
+    ge = 0.0;
+    go = 0.0;
+    return;
+  }
+  const double rad = __dsqrt_rn(__dmul_rn(-2.0, spec_ln_u1(a)));
+  double c, s;
+  spec_cos_sin_2pi(b, c, s);
+  ge = __dmul_rn(rad, c);
+  go = __dmul_rn(rad, s);
+}
+
+// ------------------------------------------------------------ FP32 evaluation
+// Relative error against the FP64 definition is below 2^-21 (argument: U1 or
+// 1 - U1 and r are converted with relative error 2^-24, the atanh and sin/cos
+// series are truncated below 2^-28, every other step adds a few FP32 ulps,
+// and the radius halves the relative error of ln).  kFastRelBound = 2^-19
+// leaves a factor-four margin.
+constexpr float kFastRelBound = 0x1p-19f;
+
+__device__ __forceinline__ float fast_ln_u1(uint32_t a) {
+  float z, e;
+  if (a >= 0xB504F334u) {  // U1 > sqrt(1/2): ln(1 - V) with V = 1 - U1 exact in integers
+    const float V = (float)(~a) * 0x1p-32f;
+    z = __fdividef(-V, 2.0f - V);
+    e = 0.0f;
+  } else {
+    const float u = (float)(a + 1u) * 0x1p-32f;
+    const uint32_t ub = __float_as_uint(u);
+    int ex = (int)(ub >> 23) - 127;
+    float f = __uint_as_float((ub & 0x007FFFFFu) | 0x3F800000u);
+    if (f > 1.41421356f) {
+      f *= 0.5f;
+      ex += 1;
+    }
+    z = __fdividef(f - 1.0f, f + 1.0f);
+    e = (float)ex;
+  }
+  const float w = z * z;
+  float p = 1.0f / 13.0f;
+  p = fmaf(w, p, 1.0f / 11.0f);
+  p = fmaf(w, p, 1.0f / 9.0f);
+  p = fmaf(w, p, 1.0f / 7.0f);
+  p = fmaf(w, p, 1.0f / 5.0f);
+  p = fmaf(w, p, 1.0f / 3.0f);
+  const float z2 = 2.0f * z;
+  const float lnf = fmaf(z2 * w, p, z2);
+  return fmaf(e, 0.693147180559945f, lnf);
+}
+
+__device__ __forceinline__ void fast_cos_sin_2pi(uint32_t b, float& c, float& s) {
+  uint32_t q = b >> 30;
+  int32_t rb = (int32_t)(b & 0x3FFFFFFFu);
+  if (rb >= (1 << 29)) {
+    rb -= (1 << 30);
+    q = (q + 1u) & 3u;
+  }
+  const float phi = ((float)rb * 0x1p-30f) * 1.57079632679489662f;
+  const float w = phi * phi;
+  float ps = 1.0f / 6227020800.0f;
+  ps = fmaf(w, ps, -1.0f / 39916800.0f);
+  ps = fmaf(w, ps, 1.0f / 362880.0f);
+  ps = fmaf(w, ps, -1.0f / 5040.0f);
+  ps = fmaf(w, ps, 1.0f / 120.0f);
+  ps = fmaf(w, ps, -1.0f / 6.0f);
+  const float sphi = fmaf(phi * w, ps, phi);
+  float pc = 1.0f / 479001600.0f;
+  pc = fmaf(w, pc, -1.0f / 3628800.0f);
+  pc = fmaf(w, pc, 1.0f / 40320.0f);
+  pc = fmaf(w, pc, -1.0f / 720.0f);
+  pc = fmaf(w, pc, 1.0f / 24.0f);
+  pc = fmaf(w, pc, -0.5f);
+  const float cphi = fmaf(w, pc, 1.0f);
+  const bool swap = (q & 1u) != 0;
+  const float cc = swap ? sphi : cphi;
+  const float ss = swap ? cphi : sphi;
+  c = (q == 1u || q == 2u) ? -cc : cc;
+  s = (q >= 2u) ? -ss : ss;
+}
+
+// ------------------------------------------------------------ rounding to u_s
+template <int FMT>
+__device__ __forceinline__ uint32_t round_f32(float x) {
+  if constexpr (FMT == FMT_F16) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(x));
+  } else if constexpr (FMT == FMT_BF16) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+  } else {
+    return (uint32_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// Single rounding of an FP64 value: round to odd into FP32 (24 bits, at least
+// two more than every target), then round to nearest even into the target.
+template <int FMT>
+__device__ __forceinline__ uint32_t round_f64(double g) {
+  float t = __double2float_rz(g);
+  if ((double)t != g) t = __uint_as_float(__float_as_uint(t) | 1u);
+  return round_f32<FMT>(t);
+}
+
+template <int FMT>
+__device__ __forceinline__ double bits_to_double(uint32_t v) {
+  if constexpr (FMT == FMT_F16) {
+    return (double)__half2float(__ushort_as_half((unsigned short)v));
+  } else if constexpr (FMT == FMT_BF16) {
+    return (double)__bfloat162float(__ushort_as_bfloat16((unsigned short)v));
+  } else {
+    __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)v, __NV_E4M3);
+    return (double)__half2float(__half(hr));
+  }
+}
+
+// Rounds one FP32 estimate; returns false when the FP64 definition is needed.
+template <int FMT>
+__device__ __forceinline__ bool round_checked(float g, uint32_t& out) {
+  const float d = kFastRelBound * fabsf(g);
+  const uint32_t lo = round_f32<FMT>(g - d);
+  const uint32_t hi = round_f32<FMT>(g + d);
+  out = round_f32<FMT>(g);
+  return lo == hi;
+}
+
+// fl_s(G) bits of the two entries served by one (a, b) word pair.
+template <int FMT>
+__device__ __forceinline__ void gauss_pair_bits(uint32_t a, uint32_t b, uint32_t& be, uint32_t& bo) {
+  bool ok = false;
+  if (a != 0xFFFFFFFFu) {
+    const float rad = __fsqrt_rn(-2.0f * fast_ln_u1(a));
+    float c, s;
+    fast_cos_sin_2pi(b, c, s);
+    const bool oke = round_checked<FMT>(rad * c, be);
+    const bool oko = round_checked<FMT>(rad * s, bo);
+    ok = oke && oko;
+  }
+  if (!ok) {  // rare: within the error bound of a rounding boundary, or U1 = 1
+    double ge, go;
+    spec_gauss_pair(a, b, ge, go);
+    be = round_f64<FMT>(ge);
+    bo = round_f64<FMT>(go);
+  }
+}
+
+}  // namespace lsq

@@ -1,0 +1,63 @@
+// Device-resident state of the iterative stages and the launch wrappers of
+// their small kernels (LSQR, FGMRES, vector reductions).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsq {
+
+// LSQR (Paige & Saunders 1982) scalars, kept on the device so that iterations
+// run without host round trips; kernels of an iteration exit early once done.
+struct LsqrState {
+  double alpha, beta, rhobar, phibar, anorm2, normb, tol;
+  double normr, normar, normA;
+  double us;   // u = u_stored * us (u_stored is the unnormalised q)
+  double cu;   // coefficient of u_stored in the next pass: -alpha * us
+  int its, flag, done, maxit;
+};
+
+// FGMRES scalars (Arnoldi column count j, residual estimate).
+struct GmState {
+  double beta0, relres, tol, inv_h;
+  int j, done, maxit, pad;
+};
+
+template <typename TP>
+cudaError_t launch_pass_lsqr_any(const TP* A, int64_t lda, int64_t m, int64_t n, const TP* t,
+                                 const TP* u_in, const double* cu_ptr, double cu_mul, TP* u_out,
+                                 TP* Pblk, double* sq, int nblk, const int* done, cudaStream_t st);
+cudaError_t launch_lsqr_beta(const double* sq, int nblk, LsqrState* st, bool init, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lsqr_init(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lsqr_update(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s);
+
+template <typename TX, typename TY, typename TO>
+cudaError_t launch_axpby(const TX* x, double a, const TY* y, double b, TO* out, int64_t len,
+                         cudaStream_t st);
+cudaError_t launch_dot(const double* x, const double* y, int64_t len, double* partial, int nblk,
+                       double* out, bool take_sqrt, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partial, int nblk, double* out, bool take_sqrt,
+                                cudaStream_t st);
+
+cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n, double* V0,
+                          double* sq_partial, int nblk, cudaStream_t s);
+cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s);
+cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, int nblk, cudaStream_t s);
+cudaError_t launch_gm_mdot(const double* V, int64_t ld, const double* w, int64_t len, const GmState* st,
+                           int maxc, double* Dp, int nblk, cudaStream_t s);
+cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
+                           int ldh, cudaStream_t s);
+cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
+                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s);
+cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
+                             double* cs, double* sn, double* g, cudaStream_t s);
+cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
+                             int nblk, cudaStream_t s);
+cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
+                            cudaStream_t s);
+template <typename TB>
+cudaError_t launch_gm_apply(const TB* B, int64_t ld, int64_t len, const GmState* st, const double* y,
+                            double* d, double* part_dd, double* part_d, int nblk, cudaStream_t s);
+
+}  // namespace lsq

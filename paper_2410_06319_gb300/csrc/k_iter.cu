@@ -1,0 +1,758 @@
+// Streaming passes over A and the small kernels of LSQR and FGMRES (Alg. 2).
+//
+// Passes (one coalesced, 128-bit vectorised read of A per call, a warp per
+// row, the row kept in registers for both products):
+//   LSQR   (Alg. 2 line 1):  q = A t + cu u ; P = A^T q ; sum q^2
+//   FGMRES (Alg. 2 line 7):  w_top = v_top + A z_bot ; P = A^T v_top
+//   residual (line 5, u_r):  f = b - r - A x ; P = A^T (-r)
+// P is reduced per CTA (fixed order) and then across CTAs by colsum, so the
+// results are deterministic.
+#include "common.cuh"
+#include "kernels.h"
+#include "iter.h"
+
+namespace lsq {
+
+template <typename T, int VW>
+struct VecOf;
+template <>
+struct VecOf<float, 4> {
+  using type = float4;
+};
+template <>
+struct VecOf<double, 2> {
+  using type = double2;
+};
+template <>
+struct VecOf<double, 1> {
+  using type = double;
+};
+
+template <typename T, int VW>
+__device__ __forceinline__ void load_vec(const T* p, T (&o)[VW], bool streaming) {
+  using V = typename VecOf<T, VW>::type;
+  V v = streaming ? __ldcs(reinterpret_cast<const V*>(p)) : *reinterpret_cast<const V*>(p);
+  const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+  for (int k = 0; k < VW; ++k) o[k] = e[k];
+}
+
+enum PassMode { PM_LSQR = 0, PM_FGM = 1, PM_RES = 2 };
+
+template <typename T>
+struct PassArgs {
+  const T* A;
+  int64_t lda, m;
+  int n, nv;             // nv = vectors per row (ceil(n / VW), padded rows for A32)
+  const T* x;            // multiplied vector, nv * VW entries (zero padded)
+  const T* uin;          // LSQR
+  T* uout;
+  const double* cu_ptr;
+  double cu_mul;
+  const double* v;       // FGMRES
+  const double* vs_ptr;
+  double* wtop;
+  const double* r;       // residual
+  const double* b;
+  double* f;
+  T* Pblk;
+  double* sq;
+  const int* done;
+};
+
+template <typename T, int VW, int VPL, int MODE>
+__global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> p) {
+  if (p.done && *p.done) return;
+  extern __shared__ __align__(16) unsigned char pass_smem[];
+  T* red = reinterpret_cast<T*>(pass_smem);          // [8 warps][nv * VW]
+  __shared__ double sqred[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + warp, tw = (int64_t)gridDim.x * 8;
+  T xv[VPL][VW], acc[VPL][VW];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int idx = lane + 32 * v;
+    if (idx < p.nv) {
+      load_vec<T, VW>(p.x + (int64_t)idx * VW, xv[v], false);
+    } else {
+      for (int k = 0; k < VW; ++k) xv[v][k] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < VW; ++k) acc[v][k] = T(0);
+  }
+  T cu = T(0);
+  double vs = 1.0;
+  if (MODE == PM_LSQR) cu = (T)((p.cu_ptr ? *p.cu_ptr : 1.0) * p.cu_mul);
+  if (MODE == PM_FGM) vs = p.vs_ptr ? *p.vs_ptr : 1.0;
+  double sqacc = 0.0;
+  for (int64_t i = gw; i < p.m; i += 2 * tw) {
+    const int64_t i2 = i + tw;
+    const bool has2 = i2 < p.m;
+    T a[VPL][VW], a2[VPL][VW];
+    const T* row = p.A + i * p.lda;
+    const T* row2 = p.A + i2 * p.lda;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      const int idx = lane + 32 * v;
+      if (idx < p.nv) {
+        load_vec<T, VW>(row + (int64_t)idx * VW, a[v], true);
+      } else {
+        for (int k = 0; k < VW; ++k) a[v][k] = T(0);
+      }
+      if (has2 && idx < p.nv) {
+        load_vec<T, VW>(row2 + (int64_t)idx * VW, a2[v], true);
+      } else {
+        for (int k = 0; k < VW; ++k) a2[v][k] = T(0);
+      }
+    }
+    T d = 0, d2 = 0;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+      for (int k = 0; k < VW; ++k) {
+        d = fma(a[v][k], xv[v][k], d);
+        d2 = fma(a2[v][k], xv[v][k], d2);
+      }
+    d = warp_sum(d);
+    d2 = warp_sum(d2);
+    T c1, c2 = T(0);
+    if (MODE == PM_LSQR) {
+      const T q = d + cu * p.uin[i];
+      c1 = q;
+      if (lane == 0) {
+        p.uout[i] = q;
+        sqacc += (double)q * (double)q;
+      }
+      if (has2) {
+        const T q2 = d2 + cu * p.uin[i2];
+        c2 = q2;
+        if (lane == 0) {
+          p.uout[i2] = q2;
+          sqacc += (double)q2 * (double)q2;
+        }
+      }
+    } else if (MODE == PM_FGM) {
+      const double vi = p.v[i] * vs;
+      c1 = (T)vi;
+      if (lane == 0) p.wtop[i] = vi + (double)d;
+      if (has2) {
+        const double vi2 = p.v[i2] * vs;
+        c2 = (T)vi2;
+        if (lane == 0) p.wtop[i2] = vi2 + (double)d2;
+      }
+    } else {
+      const double ri = p.r[i];
+      c1 = (T)(-ri);
+      if (lane == 0) p.f[i] = (p.b[i] - ri) - (double)d;
+      if (has2) {
+        const double ri2 = p.r[i2];
+        c2 = (T)(-ri2);
+        if (lane == 0) p.f[i2] = (p.b[i2] - ri2) - (double)d2;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+      for (int k = 0; k < VW; ++k) acc[v][k] = fma(c1, a[v][k], fma(c2, a2[v][k], acc[v][k]));
+  }
+  // CTA reduction of acc (fixed order over warps)
+  const int width = p.nv * VW;
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int idx = lane + 32 * v;
+    if (idx < p.nv) {
+      for (int k = 0; k < VW; ++k) red[warp * width + idx * VW + k] = acc[v][k];
+    }
+  }
+  if (MODE == PM_LSQR && lane == 0) sqred[warp] = sqacc;
+  __syncthreads();
+  for (int c = threadIdx.x; c < p.n; c += blockDim.x) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += red[w * width + c];
+    p.Pblk[(int64_t)blockIdx.x * p.n + c] = s;
+  }
+  if (MODE == PM_LSQR && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sqred[w];
+    p.sq[blockIdx.x] = s;
+  }
+}
+
+int pass_blocks(int num_sms) { return 2 * num_sms; }
+
+template <typename T, int VW, int MODE>
+static cudaError_t dispatch_pass(const PassArgs<T>& p, int nblk, cudaStream_t st) {
+  const int vpl = (p.nv + 31) / 32;
+  const size_t smem = (size_t)8 * p.nv * VW * sizeof(T);
+  auto go = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<nblk, 256, smem, st>>>(p);
+    return cudaGetLastError();
+  };
+  if (vpl <= 1) return go(pass_kernel<T, VW, 1, MODE>);
+  if (vpl <= 2) return go(pass_kernel<T, VW, 2, MODE>);
+  if (vpl <= 4) return go(pass_kernel<T, VW, 4, MODE>);
+  if (vpl <= 8) return go(pass_kernel<T, VW, 8, MODE>);
+  if constexpr (VW <= 2) {
+    if (vpl <= 16) return go(pass_kernel<T, VW, 16, MODE>);
+  }
+  if constexpr (VW == 1) {
+    if (vpl <= 32) return go(pass_kernel<T, VW, 32, MODE>);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Vector width for an FP64 matrix: double2 when rows and the base are 16-byte aligned.
+static int f64_vw(const double* A, int64_t lda, int64_t n) {
+  return ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda % 2) == 0 && (n % 2) == 0) ? 2 : 1;
+}
+
+template <typename T>
+cudaError_t launch_pass_lsqr_t(const T* A, int64_t lda, int64_t m, int64_t n, const T* t,
+                               const T* u_in, const double* cu_ptr, double cu_mul, T* u_out, T* Pblk,
+                               double* sq, int nblk, const int* done, cudaStream_t st) {
+  PassArgs<T> p{};
+  p.A = A; p.lda = lda; p.m = m; p.n = (int)n;
+  p.x = t; p.uin = u_in; p.uout = u_out; p.cu_ptr = cu_ptr; p.cu_mul = cu_mul;
+  p.Pblk = Pblk; p.sq = sq; p.done = done;
+  if constexpr (sizeof(T) == 4) {
+    p.nv = (int)((lda + 3) / 4);   // A32 rows are zero padded to lda (a multiple of 4)
+    return dispatch_pass<float, 4, PM_LSQR>(p, nblk, st);
+  } else {
+    if (f64_vw(A, lda, n) == 2) {
+      p.nv = (int)(n / 2);
+      return dispatch_pass<double, 2, PM_LSQR>(p, nblk, st);
+    }
+    p.nv = (int)n;
+    return dispatch_pass<double, 1, PM_LSQR>(p, nblk, st);
+  }
+}
+
+cudaError_t launch_pass_lsqr(const float* A32, int64_t lda32, int64_t m, int64_t n, const float* t,
+                             const float* u_in, const double* cu_ptr, double cu_mul, float* u_out,
+                             float* Pblk, double* sq, int nblk, const int* done, cudaStream_t st) {
+  return launch_pass_lsqr_t<float>(A32, lda32, m, n, t, u_in, cu_ptr, cu_mul, u_out, Pblk, sq, nblk,
+                                   done, st);
+}
+
+template <typename TA>
+cudaError_t launch_pass_fgm(const TA* A, int64_t lda, int64_t m, int64_t n, const TA* z,
+                            const double* v, const double* vs_ptr, double* wtop, TA* Pblk, int nblk,
+                            const int* done, cudaStream_t st) {
+  PassArgs<TA> p{};
+  p.A = A; p.lda = lda; p.m = m; p.n = (int)n;
+  p.x = z; p.v = v; p.vs_ptr = vs_ptr; p.wtop = wtop; p.Pblk = Pblk; p.done = done;
+  if constexpr (sizeof(TA) == 4) {
+    p.nv = (int)((lda + 3) / 4);
+    return dispatch_pass<float, 4, PM_FGM>(p, nblk, st);
+  } else {
+    if (f64_vw(A, lda, n) == 2) {
+      p.nv = (int)(n / 2);
+      return dispatch_pass<double, 2, PM_FGM>(p, nblk, st);
+    }
+    p.nv = (int)n;
+    return dispatch_pass<double, 1, PM_FGM>(p, nblk, st);
+  }
+}
+template cudaError_t launch_pass_fgm<float>(const float*, int64_t, int64_t, int64_t, const float*,
+                                            const double*, const double*, double*, float*, int,
+                                            const int*, cudaStream_t);
+template cudaError_t launch_pass_fgm<double>(const double*, int64_t, int64_t, int64_t, const double*,
+                                             const double*, const double*, double*, double*, int,
+                                             const int*, cudaStream_t);
+
+cudaError_t launch_pass_res(const double* A, int64_t lda, int64_t m, int64_t n, const double* x,
+                            const double* r, const double* b, double* f, double* Pblk, int nblk,
+                            cudaStream_t st) {
+  PassArgs<double> p{};
+  p.A = A; p.lda = lda; p.m = m; p.n = (int)n;
+  p.x = x; p.r = r; p.b = b; p.f = f; p.Pblk = Pblk;
+  if (f64_vw(A, lda, n) == 2) {
+    p.nv = (int)(n / 2);
+    return dispatch_pass<double, 2, PM_RES>(p, nblk, st);
+  }
+  p.nv = (int)n;
+  return dispatch_pass<double, 1, PM_RES>(p, nblk, st);
+}
+
+// ------------------------------------------------------------ column sums
+template <typename TP, typename TO>
+__global__ void colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, const double* scale_ptr,
+                              double scale_mul, TO* __restrict__ out, const int* done) {
+  if (done && *done) return;
+  __shared__ double part[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+  double s = 0.0;
+  if (c < n)
+    for (int b = ty; b < nblk; b += 32) s += (double)P[(int64_t)b * n + c];
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && c < n) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += part[k][tx];
+    const double sc = (scale_ptr ? *scale_ptr : 1.0) * scale_mul;
+    out[c] = (TO)(t * sc);
+  }
+}
+
+template <typename TP, typename TO>
+cudaError_t launch_colsum(const TP* P, int nblk, int64_t n, const double* scale_ptr, double scale_mul,
+                          TO* out, const int* done, cudaStream_t st) {
+  colsum_kernel<TP, TO><<<(unsigned)((n + 31) / 32), dim3(32, 32), 0, st>>>(P, nblk, n, scale_ptr,
+                                                                           scale_mul, out, done);
+  return cudaGetLastError();
+}
+template cudaError_t launch_colsum<float, float>(const float*, int, int64_t, const double*, double,
+                                                 float*, const int*, cudaStream_t);
+template cudaError_t launch_colsum<double, double>(const double*, int, int64_t, const double*, double,
+                                                   double*, const int*, cudaStream_t);
+template cudaError_t launch_colsum<double, float>(const double*, int, int64_t, const double*, double,
+                                                  float*, const int*, cudaStream_t);
+template cudaError_t launch_colsum<float, double>(const float*, int, int64_t, const double*, double,
+                                                  double*, const int*, cudaStream_t);
+
+// ============================================================ block helpers
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[32] = t;
+  __syncthreads();
+  return red[32];
+}
+
+// ============================================================ LSQR kernels
+// beta = sqrt(sum sq); us = 1/beta.
+__global__ void lsqr_beta_kernel(const double* sq, int nblk, LsqrState* st, bool init) {
+  if (!init && st->done) return;
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq[b];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(s);
+    st->beta = beta;
+    st->us = beta > 0.0 ? 1.0 / beta : 0.0;
+    if (init) st->phibar = beta;
+  }
+}
+
+template <typename T>
+__global__ void lsqr_init_kernel(const T* vt, int n, T* v, T* w, T* z, LsqrState* st) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)vt[i] * (double)vt[i];
+  s = block_sum_d(s, red);
+  const double alpha = sqrt(s);
+  const T ia = alpha > 0.0 ? (T)(1.0 / alpha) : T(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T vi = vt[i] * ia;
+    v[i] = vi;
+    w[i] = vi;
+    z[i] = T(0);
+  }
+  if (threadIdx.x == 0) {
+    st->alpha = alpha;
+    st->rhobar = alpha;
+    st->anorm2 = 0.0;
+    st->its = 0;
+    st->flag = 0;
+    st->normr = st->beta;
+    st->normar = alpha * st->beta;
+    st->normA = 0.0;
+    st->cu = -alpha * st->us;
+    st->done = (st->beta == 0.0 || alpha == 0.0 || st->maxit <= 0) ? 1 : 0;
+    if (st->beta == 0.0 || alpha == 0.0) st->flag = 3;
+  }
+}
+
+// vv = vt - beta v ; alpha = ||vv|| ; v = vv / alpha ; plane rotation ; z, w
+// updates ; stopping tests (Paige-Saunders, with the S1/S2 tests of this build).
+template <typename T>
+__global__ void lsqr_update_kernel(const T* vt, int n, T* v, T* w, T* z, LsqrState* st) {
+  if (st->done) return;
+  __shared__ double red[33];
+  __shared__ double coef[2];
+  const double beta = st->beta;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T vv = vt[i] - (T)beta * v[i];
+    s += (double)vv * (double)vv;
+  }
+  s = block_sum_d(s, red);
+  const double alpha_old = st->alpha;
+  const double alpha = sqrt(s);
+  if (threadIdx.x == 0) {
+    const double anorm2 = st->anorm2 + alpha_old * alpha_old + beta * beta;
+    const double rhobar = st->rhobar;
+    const double rho = sqrt(rhobar * rhobar + beta * beta);
+    const double c = rhobar / rho, sn = beta / rho;
+    const double theta = sn * alpha;
+    const double phi = c * st->phibar;
+    const double phibar = sn * st->phibar;
+    coef[0] = phi / rho;
+    coef[1] = theta / rho;
+    st->rhobar = -c * alpha;
+    st->phibar = phibar;
+    st->anorm2 = anorm2;
+    st->alpha = alpha;
+    st->its += 1;
+    st->normr = fabs(phibar);
+    st->normar = fabs(phibar * alpha * c);
+    st->normA = sqrt(anorm2);
+    st->cu = -alpha * st->us;
+    int flag = 0;
+    if (st->normr <= st->tol * st->normb) flag = 1;
+    else if (st->normar <= st->tol * st->normA * st->normr) flag = 2;
+    else if (beta == 0.0 || alpha == 0.0) flag = 3;
+    st->flag = flag;
+    st->done = (flag != 0 || st->its >= st->maxit) ? 1 : 0;
+  }
+  __syncthreads();
+  const T ia = alpha > 0.0 ? (T)(1.0 / alpha) : T(0);
+  const T c0 = (T)coef[0], c1 = (T)coef[1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T vn = (vt[i] - (T)beta * v[i]) * ia;
+    const T wi = w[i];
+    z[i] = z[i] + c0 * wi;
+    w[i] = vn - c1 * wi;
+    v[i] = vn;
+  }
+}
+
+
+template <typename T>
+cudaError_t launch_lsqr_init(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s) {
+  lsqr_init_kernel<T><<<1, 1024, 0, s>>>(vt, (int)n, v, w, z, st);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_lsqr_update(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s) {
+  lsqr_update_kernel<T><<<1, 1024, 0, s>>>(vt, (int)n, v, w, z, st);
+  return cudaGetLastError();
+}
+template cudaError_t launch_lsqr_init<float>(const float*, int64_t, float*, float*, float*, LsqrState*, cudaStream_t);
+template cudaError_t launch_lsqr_init<double>(const double*, int64_t, double*, double*, double*, LsqrState*, cudaStream_t);
+template cudaError_t launch_lsqr_update<float>(const float*, int64_t, float*, float*, float*, LsqrState*, cudaStream_t);
+template cudaError_t launch_lsqr_update<double>(const double*, int64_t, double*, double*, double*, LsqrState*, cudaStream_t);
+
+cudaError_t launch_lsqr_beta(const double* sq, int nblk, LsqrState* st, bool init, cudaStream_t s) {
+  lsqr_beta_kernel<<<1, 1024, 0, s>>>(sq, nblk, st, init);
+  return cudaGetLastError();
+}
+
+template <typename TP>
+cudaError_t launch_pass_lsqr_any(const TP* A, int64_t lda, int64_t m, int64_t n, const TP* t,
+                                 const TP* u_in, const double* cu_ptr, double cu_mul, TP* u_out,
+                                 TP* Pblk, double* sq, int nblk, const int* done, cudaStream_t st) {
+  return launch_pass_lsqr_t<TP>(A, lda, m, n, t, u_in, cu_ptr, cu_mul, u_out, Pblk, sq, nblk, done, st);
+}
+template cudaError_t launch_pass_lsqr_any<float>(const float*, int64_t, int64_t, int64_t, const float*,
+                                                 const float*, const double*, double, float*, float*,
+                                                 double*, int, const int*, cudaStream_t);
+template cudaError_t launch_pass_lsqr_any<double>(const double*, int64_t, int64_t, int64_t, const double*,
+                                                  const double*, const double*, double, double*,
+                                                  double*, double*, int, const int*, cudaStream_t);
+
+// ============================================================ vector kernels
+// out[i] = x[i] * a + y[i] * b  (types converted), i < len
+template <typename TX, typename TY, typename TO>
+__global__ void axpby_kernel(const TX* x, double a, const TY* y, double b, TO* out, int64_t len) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  double v = (double)x[i] * a;
+  if (y) v += (double)y[i] * b;
+  out[i] = (TO)v;
+}
+
+template <typename TX, typename TY, typename TO>
+cudaError_t launch_axpby(const TX* x, double a, const TY* y, double b, TO* out, int64_t len,
+                         cudaStream_t st) {
+  if (len <= 0) return cudaSuccess;
+  axpby_kernel<TX, TY, TO><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(x, a, y, b, out, len);
+  return cudaGetLastError();
+}
+template cudaError_t launch_axpby<double, double, float>(const double*, double, const double*, double, float*, int64_t, cudaStream_t);
+template cudaError_t launch_axpby<double, double, double>(const double*, double, const double*, double, double*, int64_t, cudaStream_t);
+template cudaError_t launch_axpby<float, double, double>(const float*, double, const double*, double, double*, int64_t, cudaStream_t);
+template cudaError_t launch_axpby<double, float, double>(const double*, double, const float*, double, double*, int64_t, cudaStream_t);
+template cudaError_t launch_axpby<float, float, double>(const float*, double, const float*, double, double*, int64_t, cudaStream_t);
+template cudaError_t launch_axpby<float, float, float>(const float*, double, const float*, double, float*, int64_t, cudaStream_t);
+
+// partial[b] = sum over the block's range of x_i * y_i (x, y double; y = x for norms)
+__global__ void dot_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                   int64_t len, double* partial) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void sum_partials_kernel(const double* partial, int nblk, double* out, bool take_sqrt) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[b];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) *out = take_sqrt ? sqrt(s) : s;
+}
+
+cudaError_t launch_dot(const double* x, const double* y, int64_t len, double* partial, int nblk,
+                       double* out, bool take_sqrt, cudaStream_t st) {
+  dot_partial_kernel<<<nblk, 256, 0, st>>>(x, y, len, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_partials_kernel<<<1, 1024, 0, st>>>(partial, nblk, out, take_sqrt);
+  return cudaGetLastError();
+}
+
+// ============================================================ FGMRES kernels
+// V column-major with leading dimension ld = m + n; H column-major (maxit+1 rows).
+__global__ void gm_init_kernel(const double* sq_partial, int nblk, GmState* st, double* g) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(s);
+    st->beta0 = beta;
+    st->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->j = 0;
+    st->relres = beta > 0.0 ? 1.0 : 0.0;
+    st->done = (beta == 0.0 || st->maxit <= 0) ? 1 : 0;
+    g[0] = beta;
+  }
+}
+
+// partial dots of w with V[:, 0..j] over a row range: Dp[b][c]
+__global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
+                               int64_t len, const GmState* st, int maxc, double* Dp) {
+  if (st->done) return;
+  __shared__ double red[33];
+  const int ncols = st->j + 1;
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(len, r0 + chunk);
+  for (int c = 0; c < ncols; ++c) {
+    double s = 0.0;
+    const double* vc = V + (int64_t)c * ld;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) s += vc[i] * w[i];
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) Dp[(int64_t)blockIdx.x * maxc + c] = s;
+  }
+}
+
+// h[c] = sum_b Dp[b][c] ; H[c][j] += h[c]
+__global__ void gm_hsum_kernel(const double* Dp, int nblk, int maxc, GmState* st, double* h,
+                               double* H, int ldh) {
+  if (st->done) return;
+  const int ncols = st->j + 1;
+  const int c = threadIdx.x;
+  if (c >= ncols) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += Dp[(int64_t)b * maxc + c];
+  h[c] = s;
+  H[(int64_t)st->j * ldh + c] += s;
+}
+
+// w[i] -= sum_c V[c][i] h[c] ; optional partial ||w||^2
+__global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
+                               double* __restrict__ w, int64_t len, const GmState* st,
+                               double* sq_partial) {
+  if (st->done) return;
+  __shared__ double hs[128];
+  __shared__ double red[33];
+  const int ncols = st->j + 1;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int c = 0; c < ncols; ++c) acc -= V[(int64_t)c * ld + i] * hs[c];
+    w[i] = acc;
+    s += acc * acc;
+  }
+  if (sq_partial) {
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) sq_partial[blockIdx.x] = s;
+  }
+}
+
+// h_{j+1,j} = ||w|| ; Givens rotations on column j ; residual estimate ; j++.
+__global__ void gm_finish_kernel(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
+                                 double* cs, double* sn, double* g) {
+  if (st->done) return;
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
+  s = block_sum_d(s, red);
+  if (threadIdx.x != 0) return;
+  const int j = st->j;
+  double* hc = H + (int64_t)j * ldh;
+  const double hn = sqrt(s);
+  hc[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
+    hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+    hc[i] = t;
+  }
+  const double den = hypot(hc[j], hc[j + 1]);
+  cs[j] = den > 0.0 ? hc[j] / den : 1.0;
+  sn[j] = den > 0.0 ? hc[j + 1] / den : 0.0;
+  hc[j] = den;
+  hc[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  st->relres = fabs(g[j + 1]) / st->beta0;
+  st->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
+  st->j = j + 1;
+  st->done = (st->relres <= st->tol || st->j >= st->maxit || hn == 0.0) ? 1 : 0;
+}
+
+// V[:, j] = w * inv_h  (j read after gm_finish incremented it)
+__global__ void gm_newcol_kernel(const double* __restrict__ w, int64_t len, const GmState* st,
+                                 double* __restrict__ V, int64_t ld) {
+  if (st->done) return;
+  const double s = st->inv_h;
+  double* vc = V + (int64_t)st->j * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    vc[i] = w[i] * s;
+}
+
+// y = H[:k,:k]^-1 g[:k]  (k = st->j)
+__global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, const double* g, double* y) {
+  if (threadIdx.x != 0) return;
+  const int k = st->j;
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int c = i + 1; c < k; ++c) t -= H[(int64_t)c * ldh + i] * y[c];
+    y[i] = t / H[(int64_t)i * ldh + i];
+  }
+}
+
+// d[i] += sum_c B[c][i] y[c] for i < len (B column-major, ld); partial sums of
+// the correction squared and of the updated vector squared.
+template <typename TB>
+__global__ void gm_apply_kernel(const TB* __restrict__ B, int64_t ld, int64_t len, const GmState* st,
+                                const double* __restrict__ y, double* __restrict__ d,
+                                double* part_dd, double* part_d) {
+  __shared__ double ys[128];
+  __shared__ double red[33];
+  const int k = st->j;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = y[c];
+  __syncthreads();
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < k; ++c) acc += (double)B[(int64_t)c * ld + i] * ys[c];
+    const double nv = d[i] + acc;
+    d[i] = nv;
+    s1 += acc * acc;
+    s2 += nv * nv;
+  }
+  s1 = block_sum_d(s1, red);
+  s2 = block_sum_d(s2, red);
+  if (threadIdx.x == 0) {
+    part_dd[blockIdx.x] = s1;
+    part_d[blockIdx.x] = s2;
+  }
+}
+
+cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s) {
+  gm_init_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, st, g);
+  return cudaGetLastError();
+}
+cudaError_t launch_gm_mdot(const double* V, int64_t ld, const double* w, int64_t len, const GmState* st,
+                           int maxc, double* Dp, int nblk, cudaStream_t s) {
+  gm_mdot_kernel<<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp);
+  return cudaGetLastError();
+}
+cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
+                           int ldh, cudaStream_t s) {
+  gm_hsum_kernel<<<1, 128, 0, s>>>(Dp, nblk, maxc, st, h, H, ldh);
+  return cudaGetLastError();
+}
+cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
+                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s) {
+  gm_axpy_kernel<<<nblk, 256, 0, s>>>(V, ld, h, w, len, st, sq_partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
+                             double* cs, double* sn, double* g, cudaStream_t s) {
+  gm_finish_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, st, H, ldh, cs, sn, g);
+  return cudaGetLastError();
+}
+cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
+                             int nblk, cudaStream_t s) {
+  gm_newcol_kernel<<<nblk, 256, 0, s>>>(w, len, st, V, ld);
+  return cudaGetLastError();
+}
+cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
+                            cudaStream_t s) {
+  gm_solve_kernel<<<1, 32, 0, s>>>(st, H, ldh, g, y);
+  return cudaGetLastError();
+}
+template <typename TB>
+cudaError_t launch_gm_apply(const TB* B, int64_t ld, int64_t len, const GmState* st, const double* y,
+                            double* d, double* part_dd, double* part_d, int nblk, cudaStream_t s) {
+  gm_apply_kernel<TB><<<nblk, 256, 0, s>>>(B, ld, len, st, y, d, part_dd, part_d);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gm_apply<double>(const double*, int64_t, int64_t, const GmState*, const double*,
+                                             double*, double*, double*, int, cudaStream_t);
+template cudaError_t launch_gm_apply<float>(const float*, int64_t, int64_t, const GmState*, const double*,
+                                            double*, double*, double*, int, cudaStream_t);
+
+cudaError_t launch_sum_partials(const double* partial, int nblk, double* out, bool take_sqrt,
+                                cudaStream_t st) {
+  sum_partials_kernel<<<1, 1024, 0, st>>>(partial, nblk, out, take_sqrt);
+  return cudaGetLastError();
+}
+
+// Copies [f; h] into V[:, 0] and leaves partial sums of squares.
+__global__ void gm_rhs_kernel(const double* __restrict__ f, const double* __restrict__ h, int64_t m,
+                              int64_t n, double* __restrict__ V0, double* sq_partial) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m + n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (i < m) ? f[i] : h[i - m];
+    V0[i] = v;
+    s += v * v;
+  }
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) sq_partial[blockIdx.x] = s;
+}
+
+cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n, double* V0,
+                          double* sq_partial, int nblk, cudaStream_t s) {
+  gm_rhs_kernel<<<nblk, 256, 0, s>>>(f, h, m, n, V0, sq_partial);
+  return cudaGetLastError();
+}
+
+// V[:, 0] *= inv_h (after gm_init)
+__global__ void gm_scale0_kernel(double* V0, int64_t len, const GmState* st) {
+  const double s = st->inv_h;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    V0[i] *= s;
+}
+cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, int nblk, cudaStream_t s) {
+  gm_scale0_kernel<<<nblk, 256, 0, s>>>(V0, len, st);
+  return cudaGetLastError();
+}
+
+}  // namespace lsq

@@ -1,0 +1,568 @@
+// Algorithm 1 step 1 (Sec. 3): the sketch Y = Omega [A | b] in precision u_s.
+//
+//  * cast pass (Sec. 3.2 one-sided scaling): column maxima of [A | b] -> a
+//    power-of-two exponent per column -> A_s = fl_s(2^k A) written K-major
+//    (one row of Bt per column of A, contiguous over the m data rows), so
+//    both tensor-core operands are K-major in 128-byte swizzled tiles.
+//  * tcgen05 sketch: per CTA a 128-row slab of the sketch matrix, up to 512
+//    columns of [A | b] in TMEM (FP32), a split of the m range.  Warp 0 feeds
+//    Bt tiles by TMA, warp 1 issues tcgen05.mma (kind::f16 or kind::f8f6f4),
+//    sixteen generator warps synthesise the sketch tile fl_s(G) in registers
+//    and store it swizzled into shared memory; four warps drain TMEM into an
+//    FP32 partial per split.  G is never stored in global memory.
+//  * CUDA-core sketch for u_s = F64 / F32 (no tensor-core format).
+//  * reduce: FP64 sum of the split partials, times s^-1/2 and 2^-k_j.
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "gauss.cuh"
+#include "kernels.h"
+
+namespace lsq {
+
+// ============================================================ omega test hook
+template <int FMT>
+__global__ void omega_kernel(int64_t s, int64_t j0, int64_t cols, uint32_t k0, uint32_t k1,
+                             double* out) {
+  const int64_t q_first = j0 >> 2, q_last = (j0 + cols - 1) >> 2;
+  const int64_t nq = q_last - q_first + 1;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= s * nq) return;
+  const int64_t i = idx / nq;
+  const int64_t q = q_first + idx % nq;
+  const uint4 x = philox4x32_10(gauss_counter((uint64_t)q, (uint32_t)i), k0, k1);
+  double v[4];
+  if constexpr (FMT == FMT_F64 || FMT == FMT_F32) {
+    spec_gauss_pair(x.x, x.y, v[0], v[1]);
+    spec_gauss_pair(x.z, x.w, v[2], v[3]);
+    if constexpr (FMT == FMT_F32) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = (double)__double2float_rn(v[t]);
+    }
+  } else {
+    uint32_t e0, o0, e1, o1;
+    gauss_pair_bits<FMT>(x.x, x.y, e0, o0);
+    gauss_pair_bits<FMT>(x.z, x.w, e1, o1);
+    v[0] = bits_to_double<FMT>(e0);
+    v[1] = bits_to_double<FMT>(o0);
+    v[2] = bits_to_double<FMT>(e1);
+    v[3] = bits_to_double<FMT>(o1);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int64_t j = q * 4 + t;
+    if (j >= j0 && j < j0 + cols) out[i * cols + (j - j0)] = v[t];
+  }
+}
+
+cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t seed, double* out,
+                         cudaStream_t st) {
+  const int64_t nq = ((j0 + cols - 1) >> 2) - (j0 >> 2) + 1;
+  const int64_t total = s * nq;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  switch (fmt) {
+    case FMT_F64: omega_kernel<FMT_F64><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
+    case FMT_F32: omega_kernel<FMT_F32><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
+    case FMT_F16: omega_kernel<FMT_F16><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
+    case FMT_BF16: omega_kernel<FMT_BF16><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
+    case FMT_E4M3: omega_kernel<FMT_E4M3><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ============================================================ cast pass
+__global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
+                                  const double* __restrict__ b, int64_t m, int64_t n,
+                                  unsigned long long* cmax, float* __restrict__ a32, int64_t lda32,
+                                  int64_t rows_per_block) {
+  const int64_t r0 = blockIdx.x * rows_per_block;
+  const int64_t r1 = min(m, r0 + rows_per_block);
+  const int64_t cend = a32 ? max(n + 1, lda32) : n + 1;
+  for (int64_t c = threadIdx.x; c < cend; c += blockDim.x) {
+    double mx = 0.0;
+    if (c < n) {
+#pragma unroll 4
+      for (int64_t i = r0; i < r1; ++i) {
+        const double v = __ldcs(A + i * lda + c);
+        mx = fmax(mx, fabs(v));
+        if (a32) a32[i * lda32 + c] = (float)v;
+      }
+    } else if (c == n) {
+      for (int64_t i = r0; i < r1; ++i) mx = fmax(mx, fabs(b[i]));
+      if (a32 && c < lda32)
+        for (int64_t i = r0; i < r1; ++i) a32[i * lda32 + c] = 0.0f;
+    } else {
+      for (int64_t i = r0; i < r1; ++i) a32[i * lda32 + c] = 0.0f;
+    }
+    if (c <= n && mx > 0.0) atomicMax(cmax + c, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int64_t m, int64_t n,
+                              unsigned long long* cmax_bits, float* a32, int64_t lda32,
+                              cudaStream_t st) {
+  const int64_t rows_per_block = 64;
+  const unsigned blocks = (unsigned)((m + rows_per_block - 1) / rows_per_block);
+  colmax_a32_kernel<<<blocks, 256, 0, st>>>(A, lda, b, m, n, cmax_bits, a32, lda32, rows_per_block);
+  return cudaGetLastError();
+}
+
+__global__ void scale_exps_kernel(const unsigned long long* cmax, int64_t ncols, int t, int* kexp) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const double mx = __longlong_as_double((long long)cmax[c]);
+  int k = 0;
+  if (t >= 0 && mx > 0.0 && isfinite(mx)) {
+    int ex;
+    frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1)
+    k = t - (ex - 1);
+  }
+  kexp[c] = k;
+}
+
+cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols, int t, int* kexp,
+                              cudaStream_t st) {
+  scale_exps_kernel<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(cmax_bits, ncols, t, kexp);
+  return cudaGetLastError();
+}
+
+template <int FMT>
+__global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
+                                      const double* __restrict__ b, int64_t m, int64_t n,
+                                      const int* __restrict__ kexp, void* __restrict__ Bt,
+                                      int64_t ldb) {
+  __shared__ double tile[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t j = j0 + r, c = c0 + threadIdx.x;
+    double v = 0.0;
+    if (j < m) {
+      if (c < n) v = A[j * lda + c];
+      else if (c == n) v = b[j];
+    }
+    tile[r][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t c = c0 + r, j = j0 + threadIdx.x;
+    if (c <= n && j < m) {
+      const double v = ldexp(tile[threadIdx.x][r], kexp[c]);
+      if constexpr (FMT == FMT_F32) {
+        reinterpret_cast<float*>(Bt)[c * ldb + j] = __double2float_rn(v);
+      } else if constexpr (FMT == FMT_E4M3) {
+        reinterpret_cast<uint8_t*>(Bt)[c * ldb + j] = (uint8_t)round_f64<FMT>(v);
+      } else {
+        reinterpret_cast<uint16_t*>(Bt)[c * ldb + j] = (uint16_t)round_f64<FMT>(v);
+      }
+    }
+  }
+}
+
+cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
+                                  int64_t n, const int* kexp, void* Bt, int64_t ldb,
+                                  int64_t nrows_pad, cudaStream_t st) {
+  const int esz = (fmt == FMT_E4M3) ? 1 : (fmt == FMT_F32 ? 4 : 2);
+  if (nrows_pad > n + 1) {
+    cudaError_t e = cudaMemsetAsync(static_cast<uint8_t*>(Bt) + (size_t)(n + 1) * ldb * esz, 0,
+                                    (size_t)(nrows_pad - n - 1) * ldb * esz, st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 1 + 31) / 32));
+  dim3 block(32, 8);
+  switch (fmt) {
+    case FMT_F16: cast_transpose_kernel<FMT_F16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
+    case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
+    case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
+    case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ============================================================ tcgen05 sketch
+constexpr int kSkGenWarps = 16;
+constexpr int kSkThreads = (2 + kSkGenWarps) * 32;
+constexpr uint32_t kSkSBytes = 128u * 128u;  // one 128 x 128-byte sketch tile
+
+struct SketchTcArgs {
+  int64_t s, m, ncols, kchunk, s_pad;
+  int bn, nsub, tmem_cols;
+  uint32_t k0, k1;
+  float* partial;
+  int* err;
+};
+
+template <int FMT, int STAGES>
+__global__ void __launch_bounds__(kSkThreads, 1)
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap tmB, const SketchTcArgs a) {
+  constexpr int EB = (FMT == FMT_E4M3) ? 1 : 2;   // bytes per element
+  constexpr int BK = 128 / EB;                    // K elements per stage (one 128-byte row)
+  constexpr int EPC = 16 / EB;                    // elements per 16-byte chunk
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  const uint32_t stage_bytes = kSkSBytes + (uint32_t)a.bn * 128u;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t done_bar = smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mt = blockIdx.x, ng = blockIdx.y, split = blockIdx.z;
+  const int64_t k_begin = split * a.kchunk;
+  const int64_t k_end = min(a.m, k_begin + a.kchunk);
+  const int nk = (int)((k_end - k_begin + BK - 1) / BK);
+  const int chunk = a.bn / a.nsub;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) {
+      mbar_init(full0 + 8 * st, kSkGenWarps + 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    mbar_init(done_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tslot), (uint32_t)a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: Bt tiles [chunk rows x 128 bytes] per N-chunk
+    if (lane == 0) {
+      prefetch_tmap(&tmB);
+      for (int ks = 0; ks < nk; ++ks) {
+        const int st = ks % STAGES;
+        const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+        if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
+        mbar_arrive_expect_tx(full0 + 8 * st, (uint32_t)a.bn * 128u);
+        const uint32_t sb = smem_u32(smem + st * stage_bytes + kSkSBytes);
+        const int32_t kx = (int32_t)(k_begin + (int64_t)ks * BK);
+        for (int c = 0; c < a.nsub; ++c)
+          tma_load_2d(sb + (uint32_t)(c * chunk * 128), &tmB, kx, (int32_t)(ng * a.bn + c * chunk),
+                      full0 + 8 * st);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(FMT == FMT_BF16 ? 1u : 0u, 128u, (uint32_t)chunk);
+      for (int ks = 0; ks < nk; ++ks) {
+        const int st = ks % STAGES;
+        const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+        if (!mbar_wait(full0 + 8 * st, ph, a.err, DEV_TIMEOUT_FULL)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + st * stage_bytes);
+        const uint32_t sb = sa + kSkSBytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {  // 4 x 32-byte K slices per 128-byte row
+          const uint64_t ad = sw128_desc(sa + kk * 32);
+          for (int c = 0; c < a.nsub; ++c) {
+            const uint64_t bd = sw128_desc(sb + (uint32_t)(c * chunk * 128) + kk * 32);
+            const uint32_t acc = (ks | kk) != 0 ? 1u : 0u;
+            if constexpr (FMT == FMT_E4M3)
+              mma_f8(tmem_base + (uint32_t)(c * chunk), ad, bd, idesc, acc);
+            else
+              mma_f16(tmem_base + (uint32_t)(c * chunk), ad, bd, idesc, acc);
+          }
+        }
+        tc_commit(empty0 + 8 * st);
+      }
+      tc_commit(done_bar);
+    }
+  } else {
+    // ---------------- generator warps: fl_s(G) tile, 128 rows x BK columns
+    const int g = threadIdx.x - 64;
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % STAGES;
+      const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+      if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
+      uint8_t* S = smem + st * stage_bytes;
+      const int64_t kbase = k_begin + (int64_t)ks * BK;
+      for (int c = g; c < 1024; c += kSkGenWarps * 32) {
+        const int row = c >> 3, kc = c & 7;
+        const uint32_t i = (uint32_t)(mt * 128 + row);
+        const uint64_t q0 = (uint64_t)(kbase + kc * EPC) >> 2;
+        uint32_t w[4];
+        if constexpr (EB == 2) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint4 x = philox4x32_10(gauss_counter(q0 + h, i), a.k0, a.k1);
+            uint32_t e0, o0, e1, o1;
+            gauss_pair_bits<FMT>(x.x, x.y, e0, o0);
+            gauss_pair_bits<FMT>(x.z, x.w, e1, o1);
+            w[2 * h] = e0 | (o0 << 16);
+            w[2 * h + 1] = e1 | (o1 << 16);
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const uint4 x = philox4x32_10(gauss_counter(q0 + h, i), a.k0, a.k1);
+            uint32_t e0, o0, e1, o1;
+            gauss_pair_bits<FMT>(x.x, x.y, e0, o0);
+            gauss_pair_bits<FMT>(x.z, x.w, e1, o1);
+            w[h] = e0 | (o0 << 8) | (e1 << 16) | (o1 << 24);
+          }
+        }
+        *reinterpret_cast<uint4*>(S + (row >> 3) * 1024 + (row & 7) * 128 + ((kc ^ (row & 7)) << 4)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full0 + 8 * st);
+    }
+  }
+
+  // ---------------- epilogue: warps 4..7 drain TMEM lanes 32q .. 32q+31
+  if (warp >= 4 && warp < 8) {
+    mbar_wait(done_bar, 0, a.err, DEV_TIMEOUT_DONE);
+    tc_fence_after();
+    const int q = warp & 3;
+    const int64_t i = mt * 128 + q * 32 + lane;
+    for (int c0 = 0; c0 < a.bn; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+      tmem_ld_wait();
+      if (i < a.s) {
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+          const int64_t col = ng * a.bn + c0 + cc;
+          if (c0 + cc < a.bn && col < a.ncols)
+            a.partial[(split * a.ncols + col) * a.s_pad + i] = __uint_as_float(r[cc]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, (uint32_t)a.tmem_cols);
+  }
+}
+
+static int round_up_int(int64_t v, int64_t q) { return (int)(((v + q - 1) / q) * q); }
+
+bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p) {
+  if (fmt != FMT_F16 && fmt != FMT_BF16 && fmt != FMT_E4M3) return false;
+  const int EB = (fmt == FMT_E4M3) ? 1 : 2;
+  const int BK = 128 / EB;
+  p->fmt = fmt;
+  p->s = s;
+  p->m = m;
+  p->ncols = ncols;
+  p->ngroups = (int)((ncols + 511) / 512);
+  int bn = round_up_int((ncols + p->ngroups - 1) / p->ngroups, 16);
+  if (bn > 256) {
+    bn = round_up_int(bn, 32);
+    p->nsub = 2;
+  } else {
+    p->nsub = 1;
+  }
+  p->bn = bn;
+  p->mtiles = (int)((s + 127) / 128);
+  p->stages = (bn > 256) ? 2 : 4;
+  p->smem = 1024 + (size_t)p->stages * (kSkSBytes + (size_t)bn * 128) + 256;
+  if (p->smem > 232448) return false;
+  const int64_t base = (int64_t)p->mtiles * p->ngroups;
+  const int64_t ksteps = (m + BK - 1) / BK;
+  int64_t splits = (2 * (int64_t)num_sms + base - 1) / base;
+  if (splits < 1) splits = 1;
+  if (splits > ksteps) splits = ksteps;
+  const int64_t steps_per = (ksteps + splits - 1) / splits;
+  p->kchunk = steps_per * BK;
+  p->splits = (int)((m + p->kchunk - 1) / p->kchunk);
+  p->s_pad = s;
+  return true;
+}
+
+bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
+                    int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void**>(&fn),
+                                         12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      fn = nullptr;
+      return false;
+    }
+  }
+  const int EB = (fmt == FMT_E4M3) ? 1 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ldb * EB)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / EB), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(tm, EB == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  const_cast<void*>(Bt), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int FMT, int STAGES>
+static cudaError_t launch_tc_inst(const SketchPlan& p, const CUtensorMap& tm, const SketchTcArgs& a,
+                                  cudaStream_t st) {
+  auto kern = sketch_tc_kernel<FMT, STAGES>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
+  kern<<<grid, kSkThreads, p.smem, st>>>(tm, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_t seed,
+                             float* partial, int* err, cudaStream_t st) {
+  SketchTcArgs a;
+  a.s = p.s;
+  a.m = p.m;
+  a.ncols = p.ncols;
+  a.kchunk = p.kchunk;
+  a.s_pad = p.s_pad;
+  a.bn = p.bn;
+  a.nsub = p.nsub;
+  int tc = 32;
+  while (tc < p.bn) tc <<= 1;
+  a.tmem_cols = tc;
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.partial = partial;
+  a.err = err;
+  if (p.stages == 2) {
+    switch (p.fmt) {
+      case FMT_F16: return launch_tc_inst<FMT_F16, 2>(p, tm, a, st);
+      case FMT_BF16: return launch_tc_inst<FMT_BF16, 2>(p, tm, a, st);
+      case FMT_E4M3: return launch_tc_inst<FMT_E4M3, 2>(p, tm, a, st);
+    }
+  } else {
+    switch (p.fmt) {
+      case FMT_F16: return launch_tc_inst<FMT_F16, 4>(p, tm, a, st);
+      case FMT_BF16: return launch_tc_inst<FMT_BF16, 4>(p, tm, a, st);
+      case FMT_E4M3: return launch_tc_inst<FMT_E4M3, 4>(p, tm, a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ============================================================ CUDA-core sketch
+// CTA tile: 16 sketch rows x 256 columns of [A | b]; K step 16; 256 threads,
+// each 4 rows x 4 columns.  The sketch tile is generated once per K step.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    sketch_cc_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ b,
+                     int64_t m, int64_t n, int64_t s, uint32_t k0, uint32_t k1, int64_t kchunk,
+                     T* __restrict__ partial, int64_t s_pad) {
+  constexpr int BM = 16, BN = 256, BKc = 16;
+  __shared__ T Gs[BKc][BM];
+  __shared__ T Bs[BKc][BN];
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * BM, c0 = (int64_t)blockIdx.y * BN;
+  const int64_t split = blockIdx.z;
+  const int64_t kb = split * kchunk, ke = min(m, kb + kchunk);
+  const int tr = (tid >> 6) * 4, tc = (tid & 63) * 4;
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+  for (int64_t k = kb; k < ke; k += BKc) {
+    // sketch tile: 16 rows x 16 K -> 64 Philox calls (4 K each)
+    if (tid < 64) {
+      const int r = tid >> 2, qq = tid & 3;
+      const int64_t j = k + qq * 4;
+      const uint4 x = philox4x32_10(gauss_counter((uint64_t)j >> 2, (uint32_t)(i0 + r)), k0, k1);
+      double v[4];
+      spec_gauss_pair(x.x, x.y, v[0], v[1]);
+      spec_gauss_pair(x.z, x.w, v[2], v[3]);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) Gs[qq * 4 + t][r] = (T)v[t];  // T = float rounds to nearest
+    }
+    for (int e = tid; e < BKc * BN; e += 256) {
+      const int kk = e / BN, cc = e % BN;
+      const int64_t j = k + kk, c = c0 + cc;
+      double v = 0.0;
+      if (j < ke) {
+        if (c < n) v = A[j * lda + c];
+        else if (c == n) v = b[j];
+      }
+      Bs[kk][cc] = (T)v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BKc; ++kk) {
+      T gv[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) gv[x] = Gs[kk][tr + x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bv[y] = Bs[kk][tc + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(gv[x], bv[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    const int64_t c = c0 + tc + y;
+    if (c > n) continue;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int64_t i = i0 + tr + x;
+      if (i < s) partial[(split * (n + 1) + c) * s_pad + i] = acc[x][y];
+    }
+  }
+}
+
+cudaError_t launch_sketch_cc(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
+                             int64_t n, int64_t s, uint64_t seed, int splits, int64_t kchunk,
+                             void* partial, int64_t s_pad, cudaStream_t st) {
+  dim3 grid((unsigned)((s + 15) / 16), (unsigned)((n + 1 + 255) / 256), (unsigned)splits);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if (fmt == FMT_F64)
+    sketch_cc_kernel<double><<<grid, 256, 0, st>>>(A, lda, b, m, n, s, k0, k1, kchunk,
+                                                   static_cast<double*>(partial), s_pad);
+  else if (fmt == FMT_F32)
+    sketch_cc_kernel<float><<<grid, 256, 0, st>>>(A, lda, b, m, n, s, k0, k1, kchunk,
+                                                  static_cast<float*>(partial), s_pad);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ============================================================ split reduce
+template <typename TP>
+__global__ void sketch_reduce_kernel(const TP* __restrict__ partial, int splits, int64_t ncols,
+                                     int64_t s, int64_t s_pad, const int* __restrict__ kexp,
+                                     double inv_sqrt_s, double* __restrict__ Y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (i >= s) return;
+  double acc = 0.0;
+  for (int sp = 0; sp < splits; ++sp) acc += (double)partial[((int64_t)sp * ncols + c) * s_pad + i];
+  const int k = kexp ? kexp[c] : 0;
+  Y[c * s + i] = ldexp(acc * inv_sqrt_s, -k);
+}
+
+cudaError_t launch_sketch_reduce(const void* partial, bool partial_f64, int splits, int64_t ncols,
+                                 int64_t s, int64_t s_pad, const int* kexp, double* Y,
+                                 cudaStream_t st) {
+  dim3 grid((unsigned)((s + 255) / 256), (unsigned)ncols);
+  const double inv = 1.0 / sqrt((double)s);
+  if (partial_f64)
+    sketch_reduce_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(partial), splits,
+                                                       ncols, s, s_pad, kexp, inv, Y);
+  else
+    sketch_reduce_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(partial), splits,
+                                                      ncols, s, s_pad, kexp, inv, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace lsq

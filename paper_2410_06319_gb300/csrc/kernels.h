@@ -1,0 +1,99 @@
+// Host-side launch wrappers of the device kernels (one stream per call).
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace lsq {
+
+// ---------------------------------------------------------------- sketch
+// fl_s(G)[i, j0 + c] as FP64 into out (row-major s x cols).
+cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t seed, double* out,
+                         cudaStream_t st);
+
+// Pass 1 over A: column maxima of [A | b] (as FP64 bit patterns, atomicMax) and,
+// when a32 != nullptr, the FP32 working copy (row stride lda32, zero padded).
+cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int64_t m, int64_t n,
+                              unsigned long long* cmax_bits, float* a32, int64_t lda32,
+                              cudaStream_t st);
+// Power-of-two exponents k_j (int) from the column maxima (target 2^t, t < 0: none).
+cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols, int t, int* kexp,
+                              cudaStream_t st);
+// Pass 2 over A: Bt[c][j] = fl_s(2^k_c [A | b][j][c]) (K-major operand), rows c in
+// [n+1, nrows_pad) zeroed.  fmt in {F16, BF16, E4M3, F32}; element size 2, 2, 1, 4.
+cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
+                                  int64_t n, const int* kexp, void* Bt, int64_t ldb,
+                                  int64_t nrows_pad, cudaStream_t st);
+
+struct SketchPlan {
+  int fmt;             // FMT_F16, FMT_BF16, FMT_E4M3 (tensor cores) or FMT_F32/F64
+  int64_t s, m, ncols; // ncols = n + 1
+  int bn;              // columns per CTA (tensor-core path)
+  int nsub;            // MMA N-chunks per CTA (1 or 2)
+  int ngroups;         // column groups
+  int mtiles;          // ceil(s / 128)
+  int splits;          // K splits
+  int64_t kchunk;      // K extent per split (multiple of the K step)
+  int64_t s_pad;       // rows of the partial buffers
+  int stages;
+  size_t smem;
+};
+
+// Builds the plan for the tensor-core sketch; returns false if unsupported.
+bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p);
+// Encodes the TMA descriptor of the K-major operand Bt (rows x m, row stride ldb elements).
+bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
+                    int box_rows);
+cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_t seed,
+                             float* partial, int* err, cudaStream_t st);
+// CUDA-core sketch in FP64 (fmt F64) or FP32 (fmt F32) from the FP64 data.
+cudaError_t launch_sketch_cc(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
+                             int64_t n, int64_t s, uint64_t seed, int splits, int64_t kchunk,
+                             void* partial, int64_t s_pad, cudaStream_t st);
+// Y[c][i] = 2^-k_c s^-1/2 sum_split partial[split][c][i]  (FP64, column-major, ld = s).
+cudaError_t launch_sketch_reduce(const void* partial, bool partial_f64, int splits, int64_t ncols,
+                                 int64_t s, int64_t s_pad, const int* kexp, double* Y,
+                                 cudaStream_t st);
+
+// ---------------------------------------------------------------- QR
+// Householder QR of Y (s x (n+1), col-major) in FP32 (fp64 = false) or FP64.
+// Outputs R (FP64, n x n col-major, diag >= 0) and c (FP64, n).  `work` holds
+// s*(n+1) elements of the arithmetic type; `aux` >= (2n + 8) doubles.
+cudaError_t launch_qr(bool fp64, const double* Y, int64_t s, int64_t n, void* work, double* aux,
+                      unsigned* bar, double* R, double* c, int* err, int num_sms, cudaStream_t st);
+
+// ---------------------------------------------------------------- TRSV
+// x = R^-1 y (upper, col-major U) or x = L^-1 y with L = R^T stored col-major.
+// T in {float, double}; TIN/TOUT any of float/double.  Skips when *done != 0.
+template <typename T, typename TIN, typename TOUT>
+cudaError_t launch_trsv(bool upper, const T* M, int64_t n, const TIN* y, double yscale, TOUT* x,
+                        const int* done, cudaStream_t st);
+
+// Converts R (FP64, col-major) into FP32/FP64 copies of R and R^T; writes the
+// diagonal ratio max|r_ii| / min|r_ii| to *kappa_est.
+cudaError_t launch_prepare_r(const double* R, int64_t n, float* R32, float* L32, double* R64,
+                             double* L64, double* kappa_est, cudaStream_t st);
+
+// ---------------------------------------------------------------- passes
+int pass_blocks(int num_sms);
+// LSQR pass over A32: q_i = cd * (A t)_i + cu * u_i (cu read from *cu_ptr times cu_mul);
+// u_out = q; Pblk[blk][c] = sum_rows q_i A_ic; sq[blk] = sum q_i^2.
+cudaError_t launch_pass_lsqr(const float* A32, int64_t lda32, int64_t m, int64_t n, const float* t,
+                             const float* u_in, const double* cu_ptr, double cu_mul, float* u_out,
+                             float* Pblk, double* sq, int nblk, const int* done, cudaStream_t st);
+// FGMRES pass: w_top_i = vs v_i + (A z)_i ; Pblk = block sums of (vs v_i) A_i.
+template <typename TA>
+cudaError_t launch_pass_fgm(const TA* A, int64_t lda, int64_t m, int64_t n, const TA* z,
+                            const double* v, const double* vs_ptr, double* wtop, TA* Pblk, int nblk,
+                            const int* done, cudaStream_t st);
+// Residual pass (FP64): f_i = b_i - r_i - (A x)_i ; Pblk = block sums of -r_i A_i.
+cudaError_t launch_pass_res(const double* A, int64_t lda, int64_t m, int64_t n, const double* x,
+                            const double* r, const double* b, double* f, double* Pblk, int nblk,
+                            cudaStream_t st);
+// out[c] = scale * sum_b P[b][c] (FP64 accumulation).  scale = *scale_ptr * scale_mul
+// when scale_ptr != nullptr.
+template <typename TP, typename TO>
+cudaError_t launch_colsum(const TP* P, int nblk, int64_t n, const double* scale_ptr, double scale_mul,
+                          TO* out, const int* done, cudaStream_t st);
+
+}  // namespace lsq

@@ -1,0 +1,83 @@
+"""lsq_sketch (tcgen05 / CUDA-core) against the oracle's Algorithm 1 step 1."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import dev, from_colmajor
+from lsq_synth import randsvd_problem
+from oracle import rng, sketch
+
+pytestmark = pytest.mark.gpu
+
+FMTS = ["f16", "bf16", "e4m3", "f32", "f64"]
+
+
+def gpu_sketch(lsq, handle, A, b, s, fmt, seed, **opts):
+    m, n = A.shape
+    Y = torch.full((s * (n + 1),), float("nan"), dtype=torch.float64, device="cuda")
+    lsq.lsq_sketch(handle, dev(A), dev(b), m, n, s, fmt, "f32", "f32", "f64", 1e-6, seed, opts or None, Y)
+    return from_colmajor(Y, s, n + 1)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+def test_sketch_extracts_columns_exactly(lsq, handle, fmt):
+    """With one-hot columns each Y entry is a single product: exact on both sides."""
+    m, n, s = 4133, 40, 200
+    r = np.random.default_rng(1)
+    perm = r.choice(m, n + 1, replace=False)
+    A = np.zeros((m, n))
+    A[perm[:n], np.arange(n)] = 1.0
+    b = np.zeros(m)
+    b[perm[n]] = -1.0
+    got = gpu_sketch(lsq, handle, A, b, s, fmt, 77)
+    ref = sketch.sketch(A, b, s, 77, fmt)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("m,n,s", [(5000, 37, 150), (3001, 300, 320), (2100, 600, 640)])
+def test_sketch_parity(lsq, handle, fmt, m, n, s):
+    P = randsvd_problem(m, n, 1e3, rho=1e-2, seed=m + n)
+    seed = 31 + n
+    got = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, seed)
+    ref = sketch.sketch(P.A, P.b, s, seed, fmt)
+    As, bs, kA, kb = sketch.cast_scaled(P.A, P.b, fmt)
+    Gs = rng.sketch_operand(s, 0, m, seed, fmt)
+    k = np.concatenate([kA, [kb]])
+    mag = np.ldexp(np.abs(Gs) @ np.abs(np.column_stack([As, bs])), -k[None, :]) / np.sqrt(s)
+    ulp = 2.0 ** -53 if fmt == "f64" else 2.0 ** -24   # accumulation precision
+    err = np.abs(got - ref)
+    # rigorous: every partial sum of m exact products rounds at most once per add
+    assert np.all(err <= (m + 2) * ulp * mag + 1e-300)
+    # typical: random-walk accumulation error, far below the worst case
+    assert np.sqrt(np.mean((err / mag) ** 2)) <= 8 * np.sqrt(m) * ulp
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_sketch_no_colscale_matches_oracle_unscaled(lsq, handle, fmt):
+    P = randsvd_problem(1500, 20, 10.0, seed=3)
+    got = gpu_sketch(lsq, handle, P.A, P.b, 80, fmt, 5, no_colscale=1)
+    Ab = np.column_stack([P.A, P.b])
+    Gs = rng.sketch_operand(80, 0, 1500, 5, fmt)
+    ref = Gs @ rng.round_to_format(Ab, fmt) / np.sqrt(80)
+    mag = np.abs(Gs) @ np.abs(rng.round_to_format(Ab, fmt)) / np.sqrt(80)
+    assert np.all(np.abs(got - ref) <= 1502 * 2.0 ** -24 * mag + 1e-300)
+
+
+def test_sketch_full_size_sampled_entries(lsq, handle):
+    """The bench workload (m=1e5, n=500, s=4n, BF16 and FP16): sampled entries vs the oracle."""
+    m, n, s = 100000, 500, 2000
+    P = randsvd_problem(m, n, 1e6, rho=1e-3, seed=1)
+    for fmt in ("bf16", "f16"):
+        got = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 0)
+        As, bs, kA, kb = sketch.cast_scaled(P.A, P.b, fmt)
+        Ab = np.column_stack([As, bs])
+        k = np.concatenate([kA, [kb]])
+        r = np.random.default_rng(5)
+        for i in r.choice(s, 6, replace=False):
+            g = rng.round_to_format(rng.gaussian_block(int(i), int(i) + 1, 0, m, 0), fmt)
+            row = (g @ Ab)[0] / np.sqrt(s)
+            ref = np.ldexp(row, -k)
+            mag = np.ldexp((np.abs(g) @ np.abs(Ab))[0] / np.sqrt(s), -k)
+            assert np.all(np.abs(got[i] - ref) <= (m + 2) * 2.0 ** -24 * mag)
+            assert np.sqrt(np.mean(((got[i] - ref) / mag) ** 2)) <= 8 * np.sqrt(m) * 2.0 ** -24
