@@ -1,0 +1,401 @@
+"""Benchmark: time-to-solution of the mixed-precision sketch-and-precondition
+least-squares solver on one GB300 (replicas only across GPUs).
+
+Workload (one "step" = one full call of lsq_lsir on data resident in HBM):
+  A = U diag(sigma) V^T, m = 100000, n = 500, kappa = 1e6 (geometric sigma),
+  b = A x + r_perp with ||r_perp|| / ||b|| = 1e-3; Gaussian sketch s = 4n on
+  BF16 tensor cores (FP32 accumulation, power-of-two column scaling), QR in
+  FP32, LSQR in FP32 (tol 1e-6, <= 2n iterations), FGMRES-LSIR with FP64
+  residuals (<= 30 refinement steps of <= 50 FGMRES iterations).
+The sketch precision follows the paper's rule (Sec. 3.4: choose u_s with
+kappa(A) u_s < 1): at kappa = 1e6 single-term BF16 / FP16 / E4M3 violate it,
+so the three-term BF16 split (single precision on BF16 tensor cores) is used;
+the single-term BF16 and FP16 runs are reported beside it.
+Also: the all-FP64 GPU path on the same inputs (FP64 sketch, QR and LSQR),
+forward errors of every run against the oracle's refined solution, the sketch
+in TFLOP/s and the passes in GB/s from CUDA events around each launch in
+separate instrumented steps (events cannot be timed inside CUDA graphs), an
+end-to-end number with host buffers, SM clocks sampled during the timed
+region, and the CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution mixed vs FP64 at fwd err<=u_w bound; sketch TFLOP/s, matvec GB/s"
+WL = dict(workload="randsvd m=100000 n=500 kappa=1e6 rho=1e-3; BF16-tensor-core sketch s=4n, "
+                   "FP32 QR/LSQR, FP64-residual FGMRES-LSIR",
+          m=100000, n=500, s=2000, kappa=1e6, rho=1e-3, u_p="f32", u_w="f32", u_r="f64",
+          tol=1e-6, seed=0, data_seed=1)
+#: sketch precisions in increasing cost, with their unit roundoff
+US_LADDER = [("e4m3", 2.0 ** -4), ("bf16", 2.0 ** -8), ("f16", 2.0 ** -11), ("bf16x3", 2.0 ** -24),
+             ("f64", 2.0 ** -53)]
+
+
+def select_us(kappa):
+    """Cheapest sketch precision with kappa(A) u_s < 1 (Sec. 3.4, Sec. 6)."""
+    for name, u in US_LADDER:
+        if kappa * u < 1.0:
+            return name
+    return "f64"
+
+
+WL["u_s"] = select_us(WL["kappa"])
+FALLBACK_HBM = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, 1900.0, "fallback"
+
+
+def make_problem():
+    from lsq_synth import randsvd_problem
+    return randsvd_problem(WL["m"], WL["n"], WL["kappa"], rho=WL["rho"], seed=WL["data_seed"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(t, world):
+    """max over ranks of a float (host), with a barrier."""
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_step(P, gpu_iters, m_sample):
+    """Times the CPU oracle on a row sample of the workload; returns (ms_estimate, detail).
+
+    The oracle runs Algorithm 1 (BF16 sketch, FP32 Householder QR) and a fixed
+    number of LSQR and FGMRES iterations on the first m_sample rows; each
+    stage's time is scaled to the full m (linear in m for the sketch and the
+    passes, independent of m for the QR) and to the iteration counts the GPU
+    solve used.
+    """
+    from oracle import fgmres, lsqr, qr, sketch
+    A = P.A[:m_sample]
+    b = P.b[:m_sample]
+    s, n = WL["s"], WL["n"]
+    scale = WL["m"] / m_sample
+    t0 = time.perf_counter()
+    Y = sketch.sketch(A, b, s, WL["seed"], WL["u_s"])
+    t1 = time.perf_counter()
+    R, c = qr.householder_qr(Y, n, dtype=np.float32)
+    xs = qr.sketch_and_solve(R, c)
+    t2 = time.perf_counter()
+    k_l = 4
+    lsqr.lsqr(A, b, R, xs, 0.0, k_l, dtype=np.float32)
+    t3 = time.perf_counter()
+    k_g = 4
+    fgmres.fgmres(A, R, b, np.zeros(n), 0.0, k_g, op_dtype=np.float32)
+    t4 = time.perf_counter()
+    est = ((t1 - t0) * scale + (t2 - t1) + (t3 - t2) / k_l * gpu_iters["lsqr"] * scale
+           + (t4 - t3) / k_g * gpu_iters["fgmres"] * scale)
+    return est * 1e3, dict(sketch_s=t1 - t0, qr_s=t2 - t1, lsqr_per_it_s=(t3 - t2) / k_l,
+                           fgmres_per_it_s=(t4 - t3) / k_g, wall_s=t4 - t0)
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    P = make_problem()
+    iters = {"lsqr": 2 * WL["n"], "fgmres": 30 * 50}
+    m_sample = 4000
+    for _ in range(args.warmup):
+        oracle_step(P, iters, m_sample)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, detail = oracle_step(P, iters, m_sample)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": wall / args.steps * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WL,
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "ms", "cores": os.cpu_count(),
+                             "sample": f"first {m_sample} rows; 4 LSQR + 4 FGMRES iterations timed and "
+                                       f"scaled to m={WL['m']}, 2n LSQR and 30x50 FGMRES iterations"},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2410_06319_gb300 as lsq
+
+    P = make_problem()
+    m, n, s = WL["m"], WL["n"], WL["s"]
+    A = torch.from_numpy(P.A).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    h = lsq.Handle()
+    stream = torch.cuda.current_stream()
+    rest = (WL["u_p"], WL["u_w"], WL["u_r"], WL["tol"], WL["seed"])
+
+    def solve(opts=None, AA=A, bb=b, xx=x, rr=r, us=WL["u_s"]):
+        return lsq.lsq_lsir(h, AA, bb, m, n, s, us, *rest, opts, xx, rr)
+
+    for _ in range(args.warmup):
+        solve()
+    # ---- timed region: K full solves (CUDA graphs inside the library)
+    clk = Clocks(local)
+    infos = []
+    barrier(world)
+    torch.cuda.synchronize()
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st, info = solve()
+        infos.append(info.as_dict())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(world)
+    t_ms = ev0.elapsed_time(ev1)
+    t_ms = barrier_max(t_ms, world)
+    value = t_ms / (args.steps * world)       # ms per solve, whole job
+    last = infos[-1]
+    x_mixed = x.cpu().numpy()
+    r_mixed = r.cpu().numpy()
+
+    # ---- instrumented steps: CUDA events around every sketch and pass launch
+    kinfos = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        st, info = solve({"timing": 1})
+        kinfos.append(info.as_dict())
+    hbm, bf16_peak, peak_kind = peaks()
+    lda32 = (n + 3) // 4 * 4
+    kbytes = {"lsqr_pass": 4.0 * m * lda32 + 8.0 * m, "fgmres_pass": 4.0 * m * lda32 + 16.0 * m,
+              "residual_pass": 8.0 * m * n + 24.0 * m}
+    tot = {k: sum(i["kern_ms"][k] for i in kinfos) for k in lsq.KERNELS}
+    cnt = {k: sum(i["kern_launches"][k] for i in kinfos) for k in lsq.KERNELS}
+    passes = {}
+    for k, by in kbytes.items():
+        if cnt[k]:
+            avg_ms = tot[k] / cnt[k]
+            passes[k] = {"launches": cnt[k], "avg_us": avg_ms * 1e3, "gbs": by / (avg_ms * 1e-3) / 1e9,
+                         "total_ms": tot[k], "bytes_per_launch": by}
+    nterms = 3 if WL["u_s"] == "bf16x3" else 1
+    sk_flop = 2.0 * s * m * (n + 1) * nterms
+    sk_ms = tot["sketch_gemm"] / max(1, cnt["sketch_gemm"])
+    sketch = {"us": sk_ms * 1e3, "tflops": sk_flop / (sk_ms * 1e-3) / 1e12 if sk_ms > 0 else None,
+              "flop_per_launch": sk_flop, "bf16_peak_tflops": bf16_peak,
+              "normals_per_s": s * m / (sk_ms * 1e-3) if sk_ms > 0 else None}
+    dom = max(passes, key=lambda k: passes[k]["total_ms"]) if passes else None
+    roofline = None
+    if dom:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["gbs"], "peak": hbm,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": passes[dom]["gbs"] / hbm,
+                    "traffic": None, "algorithmic_bytes_per_launch": kbytes[dom],
+                    "how": "CUDA events around each launch over the instrumented steps"}
+
+    # ---- the configuration's literal single-term sketch precisions (kappa u_s >> 1)
+    single = {}
+    for us in ("bf16", "f16"):
+        xs_, rs_ = torch.zeros_like(x), torch.zeros_like(r)
+        solve(None, xx=xs_, rr=rs_, us=us)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st1, i1 = solve(None, xx=xs_, rr=rs_, us=us)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d1 = i1.as_dict()
+        single[us] = {"tts_ms": e0.elapsed_time(e1), "converged": bool(d1["ir_converged"]),
+                      "lsqr_its": d1["lsqr_its"], "ir_its": d1["ir_its"],
+                      "fgmres_total": d1["gmres_its_total"], "kappa_R_est": d1["kappa_R_est"],
+                      "x": xs_.cpu().numpy(), "r": rs_.cpu().numpy()}
+
+    # ---- all-FP64 GPU path on the same inputs (sketch, QR, LSQR in FP64)
+    x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    tol64 = 1e-10
+    lsq.lsq_lsqr(h, A, b, m, n, s, "f64", "f64", "f64", "f64", tol64, WL["seed"], None, x64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k64 = max(1, min(2, args.steps))
+    e0.record(stream)
+    for _ in range(k64):
+        st64, info64 = lsq.lsq_lsqr(h, A, b, m, n, s, "f64", "f64", "f64", "f64", tol64, WL["seed"],
+                                    None, x64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / k64
+    x_fp64 = x64.cpu().numpy()
+
+    # ---- end to end through the public API with host buffers
+    hA = torch.from_numpy(P.A).pin_memory()
+    hb = torch.from_numpy(P.b).pin_memory()
+    hx = torch.empty(n, dtype=torch.float64).pin_memory()
+    hr = torch.empty(m, dtype=torch.float64).pin_memory()
+    dA, db = torch.empty_like(A), torch.empty_like(b)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_e2e = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(k_e2e):
+        dA.copy_(hA, non_blocking=True)
+        db.copy_(hb, non_blocking=True)
+        solve(None, dA, db)
+        hx.copy_(x, non_blocking=True)
+        hr.copy_(r, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = barrier_max(e2.elapsed_time(e3) / k_e2e, world) / world
+
+    line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32/f64", "data": "synthetic",
+            "config": dict(WL, l2="inputs larger than L2 (A is 400 MB FP64 + 200 MB FP32 copy)",
+                           parallelism=f"replicas x{world}",
+                           u_s_rule="cheapest u_s with kappa*u_s<1 (Sec. 3.4)"),
+            "converged": bool(last["ir_converged"]),
+            "iterations": {"lsqr": last["lsqr_its"], "ir": last["ir_its"],
+                           "fgmres_total": last["gmres_its_total"], "escalated": last["escalated"]},
+            "stage_ms": last["stage_ms"], "kappa_R_est": last["kappa_R_est"],
+            "sketch": sketch, "passes": passes,
+            "fp64_path": {"tts_ms": fp64_ms, "lsqr_its": info64.lsqr_its, "tol": tol64, "status": st64,
+                          "speedup_of_mixed": fp64_ms / value},
+            "single_term_sketch": {k: {kk: vv for kk, vv in v.items() if kk not in ("x", "r")}
+                                   for k, v in single.items()},
+            "roofline": roofline,
+            "gpu_launches": int(sum(i["gpu_launches"] for i in infos)),
+            "clocks": clocks,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * m * n + 8 * m),
+                    "d2h_bytes_per_step": int(8 * n + 8 * m)}}
+
+    # ---- oracle leg (rank 0, N = 1): forward errors and the CPU baseline
+    if rank == 0 and world == 1:
+        from oracle import exact
+        t0 = time.perf_counter()
+        xstar, rstar = exact.reference_solution(P.A, P.b, maxit=4)
+        u = 2.0 ** -24
+        fe = {"mixed": exact.forward_errors(x_mixed, r_mixed, xstar, rstar),
+              "fp64_path": exact.forward_errors(x_fp64, P.b - P.A @ x_fp64, xstar, rstar)}
+        for k, v in single.items():
+            fe[f"single_{k}"] = exact.forward_errors(v["x"], v["r"], xstar, rstar)
+        line["forward_error"] = {k: {"x": v[0], "r": v[1]} for k, v in fe.items()}
+        line["forward_error"].update(bound_4u=4 * u, reference="oracle exact.reference_solution",
+                                     ref_seconds=time.perf_counter() - t0)
+        line["mixed_meets_bound"] = bool(max(fe["mixed"]) <= 4 * u)
+        line["fp64_meets_bound"] = bool(max(fe["fp64_path"]) <= 4 * u)
+        iters = {"lsqr": last["lsqr_its"], "fgmres": max(1, last["gmres_its_total"])}
+        v, detail = oracle_step(P, iters, 4000)
+        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"first 4000 rows: {WL['u_s']} sketch, FP32 QR, 4 LSQR + 4 "
+                                          "FGMRES iterations, scaled to m=1e5 and the GPU's iteration counts",
+                                "detail": detail}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

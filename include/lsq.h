@@ -48,13 +48,18 @@ extern "C" {
 #endif
 
 /* Precisions.  F16 = IEEE half (the paper's "half"), BF16 and E4M3 are the
- * GB300 tensor-core formats (sketch only), F32 = single, F64 = double. */
+ * GB300 tensor-core formats (sketch only), F32 = single, F64 = double.
+ * BF16X3 (sketch only) = single precision on BF16 tensor cores: the sketch
+ * operand is fl_bf16(G) and each scaled entry of [A | b] is split exactly into
+ * three BF16 terms hi + lo + lo2 (24 significant bits), all products
+ * accumulated in FP32; its unit roundoff is taken as 2^-24. */
 typedef enum lsq_prec {
   LSQ_F64 = 0,
   LSQ_F32 = 1,
   LSQ_F16 = 2,
   LSQ_BF16 = 3,
-  LSQ_E4M3 = 4
+  LSQ_E4M3 = 4,
+  LSQ_BF16X3 = 5
 } lsq_prec;
 
 typedef enum lsq_status {
@@ -84,8 +89,13 @@ typedef struct lsq_opts {
   int32_t gmres_maxit;    /* FGMRES cap per refinement step; 0 -> 50 (Sec. 5) */
   int32_t no_escalate;    /* 1 disables the Sec. 5 re-run with u_A=u_L=u_R=u^2 */
   int32_t no_colscale;    /* 1 disables the power-of-two column scaling (Sec. 3.2) */
-  int32_t ir_stop;        /* 0: stop when ||dx|| <= u||x|| and ||dr|| <= u||r|| */
-  int32_t reserved0;
+  int32_t ir_stop;        /* refinement stop rule, with dx_i, dr_i the corrections of step i:
+                             0: ||dx_i|| <= u||x|| and ||dr_i|| <= u||r||, or (i >= 1) the
+                                contraction estimate rho_i = ||dx_i||/||dx_{i-1}|| < 1/2 with
+                                rho_i ||dx_i|| <= u||x|| (and the same for r);
+                             1: the first test only */
+  int32_t timing;         /* 1: time every sketch GEMM and pass launch with CUDA events
+                             on the handle's stream (info->kern_ms / kern_launches) */
   double gmres_tol;       /* FGMRES relative-residual tolerance; 0 -> tol */
   double kappa_hint;      /* kappa(A) for the escalation rule; 0 -> estimate from R */
   const double* Y_in;     /* optional device sketch, s x (n+1) column-major (ld = s):
@@ -114,6 +124,12 @@ typedef struct lsq_info {
   double ir_dr_rel;         /* ||dr|| / ||r|| of the last refinement step */
   double stage_ms[8];       /* cast, sketch, qr, lsqr, residual, fgmres, update, total */
   int64_t gpu_launches;     /* kernels launched by the call */
+  double ir_dx_hist[32];    /* ||dx_i|| / ||x_{i+1}|| of each refinement step */
+  double ir_dr_hist[32];    /* ||dr_i|| / ||r_{i+1}|| of each refinement step */
+  double gmres_relres[32];  /* FGMRES relative residual reached in each refinement step */
+  double kern_ms[4];        /* with opts->timing: summed device time of the sketch GEMM,
+                               LSQR pass, FGMRES pass and residual pass launches */
+  int64_t kern_launches[4]; /* number of launches behind each kern_ms entry */
 } lsq_info;
 
 /* sizeof(lsq_opts) for which = 0, sizeof(lsq_info) for which = 1, else 0: lets

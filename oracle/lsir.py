@@ -17,8 +17,11 @@ loop is run again from (x_0, r_0) with u_A = u_L = u_R = u^2.
 
 Stopping.  The paper stops when both forward errors against the true x*, r*
 are <= 4u; ``lsir`` does exactly that when (xstar, rstar) are given.
-Otherwise it uses the computable rule of this build:
-||dx_i|| <= u ||x_{i+1}|| and ||dr_i|| <= u ||r_{i+1}||.
+Otherwise it uses the computable rule of this build: stop after step i if
+||dx_i|| <= u ||x_{i+1}|| and ||dr_i|| <= u ||r_{i+1}||, or if (i >= 1) the
+contraction estimates rho = ||d_i|| / ||d_{i-1}|| are below 1/2 and
+rho ||dx_i|| <= u ||x_{i+1}||, rho ||dr_i|| <= u ||r_{i+1}|| (the next
+correction, i.e. the remaining error, is then below u).
 
 Here u_r is the correctly rounded residual of ``exact.residual_aug`` when
 ``ur='exact'`` and plain FP64 otherwise; h_i is solved in FP64.
@@ -44,6 +47,7 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
     x = np.array(x0, np.float64, copy=True)
     r = np.array(r0, np.float64, copy=True)
     its, gm_total, converged = 0, 0, False
+    prev = None
     gm_its = []
     for _ in range(ir_maxit):
         f, g = _residual(A, b, r, x, ur)
@@ -58,8 +62,14 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
             ex, er = exact.forward_errors(x, r, xstar, rstar)
             done = ex <= 4 * u and er <= 4 * u
         else:
-            done = (np.linalg.norm(dx) <= u * np.linalg.norm(x)
-                    and np.linalg.norm(dr) <= u * np.linalg.norm(r))
+            ndx, ndr = np.linalg.norm(dx), np.linalg.norm(dr)
+            nx, nr = np.linalg.norm(x), np.linalg.norm(r)
+            done = ndx <= u * nx and ndr <= u * nr
+            if not done and prev is not None:
+                rx = ndx / prev[0] if prev[0] > 0 else 1.0
+                rr = ndr / prev[1] if prev[1] > 0 else 1.0
+                done = rx < 0.5 and rr < 0.5 and rx * ndx <= u * nx and rr * ndr <= u * nr
+            prev = (ndx, ndr)
         if done:
             converged = True
             break

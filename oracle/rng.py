@@ -161,9 +161,15 @@ FORMATS = {
     "e4m3": (3, -6, 448.0, True),
 }
 
-#: unit roundoff of each format (2^-(mantissa bits + 1))
+#: unit roundoff of each format (2^-(mantissa bits + 1)); "bf16x3" is the
+#: three-term BF16 split of A (24 significant bits) with FP32 accumulation,
+#: i.e. single precision.
 UNIT_ROUNDOFF = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "f16": 2.0 ** -11,
-                 "bf16": 2.0 ** -8, "e4m3": 2.0 ** -4}
+                 "bf16": 2.0 ** -8, "e4m3": 2.0 ** -4, "bf16x3": 2.0 ** -24}
+
+#: format of the sketch operand fl_s(G) for each sketch precision
+OPERAND_FORMAT = {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16", "e4m3": "e4m3",
+                  "bf16x3": "bf16"}
 
 
 def round_to_format(x, fmt):
@@ -196,4 +202,18 @@ def round_to_format(x, fmt):
 
 def sketch_operand(s, j0, j1, seed, fmt):
     """fl_s(G)[0:s, j0:j1] -- the sketch operand as used in precision ``fmt``."""
-    return round_to_format(gaussian_block(0, s, j0, j1, seed), fmt)
+    return round_to_format(gaussian_block(0, s, j0, j1, seed), OPERAND_FORMAT[fmt])
+
+
+def split3(x, fmt="bf16"):
+    """Three-term split x ~ hi + lo + lo2 with each term in ``fmt``.
+
+    hi = fl(x), lo = fl(x - hi), lo2 = fl(x - hi - lo); the differences are exact
+    in FP64 for BF16 terms, so the sum carries 3 x 8 significant bits of x.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    hi = round_to_format(x, fmt)
+    r1 = x - hi
+    lo = round_to_format(r1, fmt)
+    lo2 = round_to_format(r1 - lo, fmt)
+    return hi, lo, lo2

@@ -21,7 +21,7 @@ import numpy as np
 from . import rng
 
 #: power-of-two target T for the largest entry of each scaled column
-SCALE_TARGET_LOG2 = {"f64": None, "f32": None, "f16": 14, "bf16": 14, "e4m3": 7}
+SCALE_TARGET_LOG2 = {"f64": None, "f32": None, "f16": 14, "bf16": 14, "e4m3": 7, "bf16x3": 14}
 
 
 def column_scale_exponents(M, fmt):
@@ -41,11 +41,20 @@ def column_scale_exponents(M, fmt):
 
 
 def cast_scaled(A, b, fmt):
-    """Return (A_s, b_s, kA, kb): fl_s(A 2^kA), fl_s(b 2^kb) as FP64 arrays."""
+    """Return (A_s, b_s, kA, kb): fl_s(A 2^kA), fl_s(b 2^kb) as FP64 arrays.
+
+    For ``bf16x3`` (this build's split-term reading of a single-precision
+    sketch on BF16 tensor cores) A_s is the exact sum hi + lo + lo2 of the
+    three BF16 terms of ``rng.split3``.
+    """
     Ab = np.concatenate([np.asarray(A, dtype=np.float64),
                          np.asarray(b, dtype=np.float64).reshape(-1, 1)], axis=1)
     k = column_scale_exponents(Ab, fmt)
-    As = rng.round_to_format(np.ldexp(Ab, k[None, :]), fmt)
+    if fmt == "bf16x3":
+        hi, lo, lo2 = rng.split3(np.ldexp(Ab, k[None, :]), "bf16")
+        As = hi + lo + lo2
+    else:
+        As = rng.round_to_format(np.ldexp(Ab, k[None, :]), fmt)
     return As[:, :-1], As[:, -1], k[:-1], int(k[-1])
 
 

@@ -19,17 +19,21 @@ if not os.path.exists(library_path()):
 
 lib = ctypes.CDLL(library_path())
 
-PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "bf16x3": 5}
 STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RANK",
           -3: "LSQ_E_BREAKDOWN", -4: "LSQ_E_NONFINITE", -5: "LSQ_E_CUDA", -6: "LSQ_E_TIMEOUT",
           -7: "LSQ_E_NOMEM", -8: "LSQ_E_UNSUPPORTED"}
+
+
+#: kernels timed with opts.timing (order of lsq_info.kern_ms)
+KERNELS = ["sketch_gemm", "lsqr_pass", "fgmres_pass", "residual_pass"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("lda", ctypes.c_int64), ("lsqr_maxit", ctypes.c_int32),
                 ("ir_maxit", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("no_escalate", ctypes.c_int32), ("no_colscale", ctypes.c_int32),
-                ("ir_stop", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("ir_stop", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
                 ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p)]
 
@@ -43,13 +47,20 @@ class Info(ctypes.Structure):
                 ("lsqr_normr", ctypes.c_double), ("lsqr_normar", ctypes.c_double),
                 ("lsqr_normA", ctypes.c_double), ("kappa_R_est", ctypes.c_double),
                 ("ir_dx_rel", ctypes.c_double), ("ir_dr_rel", ctypes.c_double),
-                ("stage_ms", ctypes.c_double * 8), ("gpu_launches", ctypes.c_int64)]
+                ("stage_ms", ctypes.c_double * 8), ("gpu_launches", ctypes.c_int64),
+                ("ir_dx_hist", ctypes.c_double * 32), ("ir_dr_hist", ctypes.c_double * 32),
+                ("gmres_relres", ctypes.c_double * 32),
+                ("kern_ms", ctypes.c_double * 4), ("kern_launches", ctypes.c_int64 * 4)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["gmres_its"] = list(self.gmres_its)[: max(0, self.ir_its)]
+        for k in ("ir_dx_hist", "ir_dr_hist", "gmres_relres"):
+            d[k] = list(getattr(self, k))[: max(0, self.ir_its)]
         d["stage_ms"] = dict(zip(["cast", "sketch", "qr", "lsqr", "residual", "fgmres", "update",
                                   "total"], list(self.stage_ms)))
+        d["kern_ms"] = dict(zip(KERNELS, list(self.kern_ms)))
+        d["kern_launches"] = dict(zip(KERNELS, list(self.kern_launches)))
         return d
 
 

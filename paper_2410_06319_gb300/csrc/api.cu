@@ -46,8 +46,28 @@ struct Buf {
 
 }  // namespace
 
+namespace {
+// An instantiated CUDA graph of a batch of solver iterations, cached in the
+// handle by the pointers and sizes it was captured with.
+struct CachedGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  int64_t kernels = 0;  // kernel nodes
+  ~CachedGraph() {
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+}  // namespace
+
 struct lsq_handle {
-  cudaStream_t stream = nullptr;
+  cudaStream_t user_stream = nullptr;  // the caller's stream (ordering only)
+  cudaStream_t stream = nullptr;       // the handle's own non-blocking work stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::unordered_map<std::string, CachedGraph*> graphs;
+  CachedGraph* cap = nullptr;          // graph being captured
+  double kern_acc[4] = {0, 0, 0, 0};
+  int64_t kern_cnt[4] = {0, 0, 0, 0};
   int device = 0;
   int num_sms = 0;
   std::unordered_map<std::string, Buf> bufs;
@@ -112,6 +132,29 @@ struct StageTimer {
 };
 
 enum Stage { ST_CAST = 0, ST_SKETCH, ST_QR, ST_LSQR, ST_RES, ST_FGMRES, ST_UPDATE, ST_TOTAL };
+enum Kern { K_SKETCH = 0, K_LSQR_PASS, K_FGM_PASS, K_RES_PASS };
+constexpr int kKernMark = 100;   // marks with stage >= kKernMark time single kernels
+
+// Brackets one launch with events when timing is on (opts.timing).
+struct KernTimer {
+  lsq_handle* h;
+  int k;
+  bool on;
+  cudaEvent_t a{};
+  KernTimer(lsq_handle* hh, int kk, bool enabled) : h(hh), k(kk), on(enabled && !hh->cap) {
+    if (!on) return;
+    a = next_event(h);
+    CK(cudaEventRecord(a, h->stream));
+  }
+  ~KernTimer() {
+    if (!on) return;
+    try {
+      cudaEvent_t b = next_event(h);
+      if (cudaEventRecord(b, h->stream) == cudaSuccess) h->marks.push_back({kKernMark + k, a, b});
+    } catch (...) {
+    }
+  }
+};
 
 int fmt_of(lsq_prec p) {
   switch (p) {
@@ -120,6 +163,7 @@ int fmt_of(lsq_prec p) {
     case LSQ_F16: return FMT_F16;
     case LSQ_BF16: return FMT_BF16;
     case LSQ_E4M3: return FMT_E4M3;
+    case LSQ_BF16X3: return FMT_BF16X3;
   }
   return -1;
 }
@@ -131,6 +175,7 @@ double unit_roundoff(lsq_prec p) {
     case LSQ_F16: return std::ldexp(1.0, -11);
     case LSQ_BF16: return std::ldexp(1.0, -8);
     case LSQ_E4M3: return std::ldexp(1.0, -4);
+    case LSQ_BF16X3: return std::ldexp(1.0, -24);   // three BF16 terms, FP32 accumulation
   }
   return 1.0;
 }
@@ -225,6 +270,64 @@ S read_state(Ctx& c, const S* d) {
 
 double read_scalar(Ctx& c, const double* d) { return read_state<double>(c, d); }
 
+// Returns the cached graph for `key`, capturing `body` on the work stream if needed.
+CachedGraph* get_graph(Ctx& c, const std::string& key, const std::function<void()>& body) {
+  auto it = c.h->graphs.find(key);
+  if (it != c.h->graphs.end()) return it->second;
+  if (c.h->graphs.size() >= 32) {
+    for (auto& kv : c.h->graphs) delete kv.second;
+    c.h->graphs.clear();
+  }
+  auto* G = new CachedGraph();
+  const int64_t l0 = c.h->launches;
+  c.h->cap = G;
+  cudaError_t e = cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    c.h->cap = nullptr;
+    delete G;
+    throw CudaFail{e, "cudaStreamBeginCapture"};
+  }
+  try {
+    body();
+  } catch (...) {
+    c.h->cap = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(c.st, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    delete G;
+    throw;
+  }
+  c.h->cap = nullptr;
+  e = cudaStreamEndCapture(c.st, &G->g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G->e, G->g, 0);
+  if (e != cudaSuccess) {
+    delete G;
+    throw CudaFail{e, "graph capture"};
+  }
+  G->kernels = c.h->launches - l0;
+  c.h->launches = l0;
+  c.h->graphs[key] = G;
+  return G;
+}
+
+void launch_graph(Ctx& c, CachedGraph* G) {
+  CK(cudaGraphLaunch(G->e, c.st));
+  c.h->launches += G->kernels;
+}
+
+std::string graph_key(const char* tag, std::initializer_list<int64_t> vals) {
+  std::string k(tag);
+  char buf[32];
+  for (int64_t v : vals) {
+    snprintf(buf, sizeof(buf), ":%llx", (unsigned long long)v);
+    k += buf;
+  }
+  return k;
+}
+
+#define PV(p) (int64_t)(uintptr_t)(p)
+
 // -------------------------------------------------------------- stages
 // Pass 1 (column maxima and, for u_w = F32, the FP32 working copy of A).
 float* stage_cast(Ctx& c) {
@@ -242,7 +345,7 @@ void stage_sketch(Ctx& c, double* Y) {
   const int64_t ncols = c.n + 1;
   auto* cmax = static_cast<unsigned long long*>(ws(c.h, "cmax", ncols * 8));
   int* kexp = static_cast<int*>(ws(c.h, "kexp", ncols * 4));
-  if (fmt == FMT_F16 || fmt == FMT_BF16 || fmt == FMT_E4M3) {
+  if (fmt == FMT_F16 || fmt == FMT_BF16 || fmt == FMT_E4M3 || fmt == FMT_BF16X3) {
     SketchPlan p;
     if (!plan_sketch_tc(fmt, c.s, c.m, ncols, c.h->num_sms, &p)) throw StatusFail{LSQ_E_UNSUPPORTED};
     const int t = c.o.no_colscale ? -1 : (fmt == FMT_E4M3 ? 7 : 14);
@@ -253,14 +356,18 @@ void stage_sketch(Ctx& c, double* Y) {
     {
       StageTimer tt(c.h, ST_CAST);
       L(launch_scale_exps(cmax, ncols, t, kexp, c.st));
-      Bt = ws(c.h, "bt", (size_t)rows * ldb * eb);
+      Bt = ws(c.h, "bt", (size_t)p.nt * rows * ldb * eb);
       L(launch_cast_transpose(fmt, c.A, c.lda, c.b, c.m, c.n, kexp, Bt, ldb, rows, c.st));
     }
     StageTimer tt(c.h, ST_SKETCH);
     CUtensorMap tm;
-    if (!encode_bt_tmap(&tm, Bt, fmt, rows, c.m, ldb, p.bn / p.nsub)) throw StatusFail{LSQ_E_UNSUPPORTED};
+    if (!encode_bt_tmap(&tm, Bt, fmt, (int64_t)p.nt * rows, c.m, ldb, p.bn / p.nsub, p.rowb))
+      throw StatusFail{LSQ_E_UNSUPPORTED};
     float* partial = static_cast<float*>(ws(c.h, "partial", (size_t)p.splits * ncols * p.s_pad * 4));
-    L(launch_sketch_tc(p, tm, c.seed, partial, c.h->d_err, c.st));
+    {
+      KernTimer kt(c.h, K_SKETCH, c.o.timing);
+      L(launch_sketch_tc(p, tm, c.seed, partial, c.h->d_err, c.st));
+    }
     L(launch_sketch_reduce(partial, false, p.splits, ncols, c.s, p.s_pad, kexp, Y, c.st));
   } else {
     StageTimer tt(c.h, ST_SKETCH);
@@ -273,27 +380,40 @@ void stage_sketch(Ctx& c, double* Y) {
     splits = (c.m + kchunk - 1) / kchunk;
     const size_t esz = (fmt == FMT_F64) ? 8 : 4;
     void* partial = ws(c.h, "partial", (size_t)splits * ncols * c.s * esz);
-    L(launch_sketch_cc(fmt, c.A, c.lda, c.b, c.m, c.n, c.s, c.seed, (int)splits, kchunk, partial, c.s,
-                       c.st));
+    {
+      KernTimer kt(c.h, K_SKETCH, c.o.timing);
+      L(launch_sketch_cc(fmt, c.A, c.lda, c.b, c.m, c.n, c.s, c.seed, (int)splits, kchunk, partial,
+                         c.s, c.st));
+    }
     L(launch_sketch_reduce(partial, fmt == FMT_F64, (int)splits, ncols, c.s, c.s, nullptr, Y, c.st));
   }
 }
 
 struct RCopies {
-  float *R32, *L32;
-  double *R64, *L64;
+  Tri<float> f32;
+  Tri<double> f64;
   double* kappa;
+  template <typename T>
+  const Tri<T>& get() const {
+    if constexpr (sizeof(T) == 4) return f32;
+    else return f64;
+  }
 };
 
 RCopies stage_prepare_r(Ctx& c, const double* R) {
   RCopies r;
-  const size_t nn = (size_t)c.n * c.n;
-  r.R32 = static_cast<float*>(ws(c.h, "R32", nn * 4));
-  r.L32 = static_cast<float*>(ws(c.h, "L32", nn * 4));
-  r.R64 = static_cast<double*>(ws(c.h, "R64", nn * 8));
-  r.L64 = static_cast<double*>(ws(c.h, "L64", nn * 8));
+  const int64_t ld32 = tri_ld(c.n, 4), ld64 = tri_ld(c.n, 8);
+  const size_t n32 = (size_t)ld32 * c.n, n64 = (size_t)ld64 * c.n;
+  const size_t nd = (size_t)((c.n + 31) / 32) * 1024;
+  r.f32 = {static_cast<float*>(ws(c.h, "R32", n32 * 4)), static_cast<float*>(ws(c.h, "L32", n32 * 4)),
+           static_cast<float*>(ws(c.h, "DU32", nd * 4)), static_cast<float*>(ws(c.h, "DL32", nd * 4)), c.n,
+           ld32};
+  r.f64 = {static_cast<double*>(ws(c.h, "R64", n64 * 8)), static_cast<double*>(ws(c.h, "L64", n64 * 8)),
+           static_cast<double*>(ws(c.h, "DU64", nd * 8)), static_cast<double*>(ws(c.h, "DL64", nd * 8)), c.n,
+           ld64};
   r.kappa = static_cast<double*>(ws(c.h, "kappaR", 8));
-  L(launch_prepare_r(R, c.n, r.R32, r.L32, r.R64, r.L64, r.kappa, c.st));
+  L(launch_prepare_r(R, c.n, &r.f32, &r.f64, r.kappa, c.st));
+  c.h->launches += 3;
   return r;
 }
 
@@ -310,8 +430,8 @@ void stage_qr(Ctx& c, const double* Y, double* R, double* xs, RCopies* rc) {
     c.h->launches += 2;
     *rc = stage_prepare_r(c, R);
     if (xs) {
-      if (f64) L((launch_trsv<double, double, double>(true, rc->R64, c.n, cvec, 1.0, xs, nullptr, c.st)));
-      else L((launch_trsv<float, double, double>(true, rc->R32, c.n, cvec, 1.0, xs, nullptr, c.st)));
+      if (f64) L((launch_trsv<double, double, double>(true, rc->f64, cvec, 1.0, xs, nullptr, c.st)));
+      else L((launch_trsv<float, double, double>(true, rc->f32, cvec, 1.0, xs, nullptr, c.st)));
     }
   }
 }
@@ -322,7 +442,7 @@ struct LsqrOut {
 
 // Alg. 2 line 1: preconditioned LSQR in working precision W from x0 -> x.
 template <typename W>
-LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const W* Rw, const W* Lw, const double* x0,
+LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const Tri<W>& tri, const double* x0,
                      double* x) {
   StageTimer tmr(c.h, ST_LSQR);
   const int64_t n = c.n, m = c.m;
@@ -358,29 +478,42 @@ LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const W* Rw, const W* Lw,
   // u = b - A x0, A^T u  (t = -x0 so that q = A t + 1 * b)
   L((launch_axpby<double, double, W>(x0, -1.0, nullptr, 0.0, t, n, c.st)));
   L(launch_pass_lsqr_any<W>(Aw, ldw, m, n, t, bw, nullptr, 1.0, u, P, sq, c.nblk, nullptr, c.st));
-  L(launch_lsqr_beta(sq, c.nblk, dst, true, c.st));
-  L((launch_colsum<W, W>(P, c.nblk, n, &dst->us, 1.0, sv, nullptr, c.st)));
-  L((launch_trsv<W, W, W>(false, Lw, n, sv, 1.0, vt, nullptr, c.st)));
-  L(launch_lsqr_init<W>(vt, n, v, w, z, dst, c.st));
+  L(launch_lsqr_colsum<W>(P, c.nblk, n, sq, dst, true, sv, c.st));
+  L(launch_lsqr_step<W>(tri, sv, v, w, z, t, dst, true, c.st));
+  auto body = [&]() {
+    for (int k = 0; k < kBatch; ++k) {
+      const int* dn = &dst->done;
+      {
+        KernTimer kt(c.h, K_LSQR_PASS, c.o.timing);
+        L(launch_pass_lsqr_any<W>(Aw, ldw, m, n, t, u, &dst->cu, 1.0, u, P, sq, c.nblk, dn, c.st));
+      }
+      L(launch_lsqr_colsum<W>(P, c.nblk, n, sq, dst, false, sv, c.st));
+      L(launch_lsqr_step<W>(tri, sv, v, w, z, t, dst, false, c.st));
+    }
+  };
+  // CUDA events cannot be timed inside graphs: with opts.timing the batch is launched directly
+  CachedGraph* G = c.o.timing ? nullptr
+                              : get_graph(c,
+                                          graph_key(sizeof(W) == 4 ? "lsqr32" : "lsqr64",
+                                                    {PV(Aw), ldw, m, n, PV(t), PV(u), PV(P), PV(sq),
+                                                     PV(sv), PV(v), PV(w), PV(z), PV(dst), PV(tri.R),
+                                                     PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk}),
+                                          body);
   int done = 0, its = 0;
   LsqrState out{};
   while (!done) {
-    for (int k = 0; k < kBatch; ++k) {
-      const int* dn = &dst->done;
-      L((launch_trsv<W, W, W>(true, Rw, n, v, 1.0, t, dn, c.st)));
-      L(launch_pass_lsqr_any<W>(Aw, ldw, m, n, t, u, &dst->cu, 1.0, u, P, sq, c.nblk, dn, c.st));
-      L(launch_lsqr_beta(sq, c.nblk, dst, false, c.st));
-      L((launch_colsum<W, W>(P, c.nblk, n, &dst->us, 1.0, sv, dn, c.st)));
-      L((launch_trsv<W, W, W>(false, Lw, n, sv, 1.0, vt, dn, c.st)));
-      L(launch_lsqr_update<W>(vt, n, v, w, z, dst, c.st));
-    }
+    const size_t mark0 = c.h->marks.size();
+    if (G) launch_graph(c, G);
+    else body();
     out = read_state<LsqrState>(c, dst);
+    const int ran = std::min(kBatch, out.its - its);
+    if (c.o.timing) c.h->marks.resize(mark0 + ran);   // keep the passes that did work
     done = out.done;
     its = out.its;
     if (its > maxit + kBatch) break;  // defensive: the device flag ends the loop
   }
   // x = x0 + R^-1 z
-  L((launch_trsv<W, W, W>(true, Rw, n, z, 1.0, t, nullptr, c.st)));
+  L((launch_trsv<W, W, W>(true, tri, z, 1.0, t, nullptr, c.st)));
   L((launch_axpby<W, double, double>(t, 1.0, x0, 1.0, x, n, c.st)));
   return out;
 }
@@ -394,8 +527,8 @@ struct GmOut {
 // Alg. 2 line 7: FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (operator
 // products in TOP), x0 = 0; r += dr, x += dx.
 template <typename TOP>
-GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const TOP* Lop,
-                   const double* f, const double* hv, double tol, int maxit, double* r, double* x) {
+GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, const double* f,
+                   const double* hv, double tol, int maxit, double* r, double* x) {
   StageTimer tmr(c.h, ST_FGMRES);
   const int64_t m = c.m, n = c.n, ld = m + n;
   const int ldh = maxit + 1;
@@ -403,6 +536,11 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const T
   TOP* Zb = static_cast<TOP*>(ws(c.h, "gmZ", (size_t)(round_up(n, 4) + 4) * (maxit + 1) * sizeof(TOP)));
   const int64_t ldz = round_up(n, 4) + 4;
   double* wv = static_cast<double*>(ws(c.h, "gmW", ld * 8));
+  TOP* az = static_cast<TOP*>(ws(c.h, "gmAz", (m + 8) * sizeof(TOP)));
+  float* v32 = (sizeof(TOP) == 4) ? static_cast<float*>(ws(c.h, "gmV32", (m + 8) * 4)) : nullptr;
+  // coefficient vector of the pass: the FP32 copy of the current column, or the column itself
+  const TOP* vcoef = (sizeof(TOP) == 4) ? reinterpret_cast<const TOP*>(v32) : reinterpret_cast<const TOP*>(V);
+  const int64_t vstr = (sizeof(TOP) == 4) ? 0 : ld;
   TOP* P = static_cast<TOP*>(ws(c.h, "gmP", (size_t)c.nblk * n * sizeof(TOP)));
   TOP* sb = static_cast<TOP*>(ws(c.h, "gmS", (round_up(n, 4) + 4) * sizeof(TOP)));
   CK(cudaMemsetAsync(Zb, 0, (size_t)(round_up(n, 4) + 4) * (maxit + 1) * sizeof(TOP), c.st));
@@ -425,30 +563,49 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const T
   CK(cudaMemcpyAsync(gst, c.h->h_pinned + 2048, sizeof(hs), cudaMemcpyHostToDevice, c.st));
   L(launch_gm_rhs(f, hv, m, n, V, sqp, c.nblk2, c.st));
   L(launch_gm_init(sqp, c.nblk2, gst, g, c.st));
-  L(launch_gm_scale0(V, ld, gst, c.nblk2, c.st));
+  L(launch_gm_scale0(V, ld, gst, v32, m, c.nblk2, c.st));
   const int maxc = maxit + 1;
-  int j = 0;
-  GmState out{};
-  while (j < maxit) {
-    const int jend = std::min(maxit, j + kBatch);
-    for (; j < jend; ++j) {
+  auto body = [&]() {
+    for (int k = 0; k < kBatch; ++k) {
       const int* dn = &gst->done;
-      const double* vj = V + (int64_t)j * ld;
-      TOP* zj = Zb + (int64_t)j * ldz;
-      L((launch_trsv<TOP, double, TOP>(true, Rop, n, vj + m, 1.0, zj, dn, c.st)));
-      L(launch_pass_fgm<TOP>(Aop, ldop, m, n, zj, vj, nullptr, wv, P, c.nblk, dn, c.st));
+      const int* jp = &gst->j;
+      L((launch_trsv<TOP, double, TOP>(true, tri, V + m, 1.0, Zb, dn, c.st, jp, ld, ldz)));
+      {
+        KernTimer kt(c.h, K_FGM_PASS, c.o.timing);
+        L(launch_pass_fgm<TOP>(Aop, ldop, m, n, Zb, vcoef, az, P, c.nblk, dn, c.st, jp, ldz, vstr,
+                               c.h->d_err));
+      }
       L((launch_colsum<TOP, TOP>(P, c.nblk, n, nullptr, 1.0, sb, dn, c.st)));
-      L((launch_trsv<TOP, TOP, double>(false, Lop, n, sb, 1.0, wv + m, dn, c.st)));
+      L((launch_trsv<TOP, TOP, double>(false, tri, sb, 1.0, wv + m, dn, c.st)));
       for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
-        L(launch_gm_mdot(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st));
+        L(launch_gm_mdot<TOP>(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st, pass == 0 ? az : nullptr, m));
         L(launch_gm_hsum(Dp, c.nblk2, maxc, gst, hh, H, ldh, c.st));
         L(launch_gm_axpy(V, ld, hh, wv, ld, gst, pass == 1 ? sqp : nullptr, c.nblk2, c.st));
       }
       L(launch_gm_finish(sqp, c.nblk2, gst, H, ldh, cs, sn, g, c.st));
-      L(launch_gm_newcol(wv, ld, gst, V, ld, c.nblk2, c.st));
+      L(launch_gm_newcol(wv, ld, gst, V, ld, v32, m, c.nblk2, c.st));
     }
+  };
+  CachedGraph* G =
+      c.o.timing ? nullptr
+                 : get_graph(c,
+                             graph_key(sizeof(TOP) == 4 ? "fgm32" : "fgm64",
+                                       {PV(Aop), ldop, m, n, maxit, PV(V), PV(Zb), PV(wv), PV(P), PV(az), PV(v32),
+                                        PV(sb), PV(H), PV(cs), PV(sn), PV(g), PV(hh), PV(Dp), PV(sqp),
+                                        PV(gst), PV(tri.R), PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk,
+                                        c.nblk2}),
+                             body);
+  int j = 0;
+  GmState out{};
+  while (true) {
+    const size_t mark0 = c.h->marks.size();
+    if (G) launch_graph(c, G);
+    else body();
     out = read_state<GmState>(c, gst);
-    if (out.done) break;
+    const int ran = std::min(kBatch, out.j - j);
+    if (c.o.timing) c.h->marks.resize(mark0 + ran);
+    j = out.j;
+    if (out.done || j >= maxit) break;
   }
   StageTimer tu(c.h, ST_UPDATE);
   L(launch_gm_solve(gst, H, ldh, g, y, c.st));
@@ -471,8 +628,8 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const T
 
 // Steps 4-11 of Alg. 2 from (x0, r0), FGMRES products in TOP.
 template <typename TOP>
-bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const TOP* Lop,
-                  const RCopies& rc, double* x, double* r, lsq_info* info) {
+bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const RCopies& rc, double* x, double* r,
+                  lsq_info* info) {
   const int64_t m = c.m, n = c.n;
   double* f = static_cast<double*>(ws(c.h, "ir_f", m * 8));
   double* gv = static_cast<double*>(ws(c.h, "ir_g", (n + 4) * 8));
@@ -483,26 +640,46 @@ bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const TOP* Rop, const TO
   const double gtol = c.o.gmres_tol > 0 ? c.o.gmres_tol : c.tol;
   const double u = unit_roundoff(c.uw);
   bool converged = false;
+  double prev_dx = 0.0, prev_dr = 0.0;
   info->ir_its = 0;
   info->gmres_its_total = 0;
   for (int i = 0; i < irmax; ++i) {
     {
       StageTimer t(c.h, ST_RES);
-      L(launch_pass_res(c.A, c.lda, m, n, x, r, c.b, f, P, c.nblk, c.st));
+      {
+        KernTimer kt(c.h, K_RES_PASS, c.o.timing);
+        L(launch_pass_res(c.A, c.lda, m, n, x, r, c.b, f, P, c.nblk, c.st));
+      }
       L((launch_colsum<double, double>(P, c.nblk, n, nullptr, 1.0, gv, nullptr, c.st)));
-      L((launch_trsv<double, double, double>(false, rc.L64, n, gv, 1.0, hv, nullptr, c.st)));
+      L((launch_trsv<double, double, double>(false, rc.f64, gv, 1.0, hv, nullptr, c.st)));
     }
-    GmOut go = stage_fgmres<TOP>(c, Aop, ldop, Rop, Lop, f, hv, gtol, gmax, r, x);
+    GmOut go = stage_fgmres<TOP>(c, Aop, ldop, rc.get<TOP>(), f, hv, gtol, gmax, r, x);
     info->gmres_its[i] = go.its;
     info->gmres_its_total += go.its;
     info->ir_its = i + 1;
-    info->ir_dx_rel = go.x2 > 0 ? go.dx2 / go.x2 : 0.0;
-    info->ir_dr_rel = go.r2 > 0 ? go.dr2 / go.r2 : 0.0;
+    const double dxr = go.x2 > 0 ? go.dx2 / go.x2 : 0.0;
+    const double drr = go.r2 > 0 ? go.dr2 / go.r2 : 0.0;
+    info->ir_dx_rel = dxr;
+    info->ir_dr_rel = drr;
+    info->ir_dx_hist[i] = dxr;
+    info->ir_dr_hist[i] = drr;
+    info->gmres_relres[i] = go.relres;
     if (!std::isfinite(go.x2) || !std::isfinite(go.r2)) throw StatusFail{LSQ_E_NONFINITE};
     if (go.dx2 <= u * go.x2 && go.dr2 <= u * go.r2) {
       converged = true;
       break;
     }
+    if (c.o.ir_stop == 0 && i >= 1) {
+      // contraction estimate: the next correction is about rho times this one
+      const double rx = prev_dx > 0 ? go.dx2 / prev_dx : 1.0;
+      const double rr = prev_dr > 0 ? go.dr2 / prev_dr : 1.0;
+      if (rx < 0.5 && rr < 0.5 && rx * go.dx2 <= u * go.x2 && rr * go.dr2 <= u * go.r2) {
+        converged = true;
+        break;
+      }
+    }
+    prev_dx = go.dx2;
+    prev_dr = go.dr2;
   }
   return converged;
 }
@@ -511,14 +688,27 @@ void finish_timing(lsq_handle* h, lsq_info* info) {
   CK(cudaStreamSynchronize(h->stream));
   if (info) {
     for (int k = 0; k < 8; ++k) info->stage_ms[k] = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      info->kern_ms[k] = h->kern_acc[k];
+      info->kern_launches[k] = h->kern_cnt[k];
+    }
     for (auto& mk : h->marks) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, mk.a, mk.b));
-      info->stage_ms[mk.stage] += ms;
+      if (mk.stage >= kKernMark) {
+        info->kern_ms[mk.stage - kKernMark] += ms;
+        info->kern_launches[mk.stage - kKernMark] += 1;
+      } else {
+        info->stage_ms[mk.stage] += ms;
+      }
     }
   }
   h->marks.clear();
   h->next_event = 0;
+  for (int k = 0; k < 4; ++k) {
+    h->kern_acc[k] = 0.0;
+    h->kern_cnt[k] = 0;
+  }
 }
 
 lsq_status run_guarded(lsq_handle* h, lsq_info* info, const std::function<lsq_status()>& fn) {
@@ -527,9 +717,17 @@ lsq_status run_guarded(lsq_handle* h, lsq_info* info, const std::function<lsq_st
   try {
     h->marks.clear();
     h->next_event = 0;
+    for (int k = 0; k < 4; ++k) {
+      h->kern_acc[k] = 0.0;
+      h->kern_cnt[k] = 0;
+    }
+    CK(cudaEventRecord(h->ev_in, h->user_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
     st = fn();
     check_dev_error(h);
     finish_timing(h, info);
+    CK(cudaEventRecord(h->ev_out, h->stream));
+    CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
   } catch (const CudaFail& f) {
     h->last_cuda = std::string(f.what) + ": " + cudaGetErrorString(f.e);
     cudaGetLastError();
@@ -584,9 +782,9 @@ Front run_front(Ctx& c, double* x, lsq_info* info) {
   if (!(kap < INFINITY)) throw StatusFail{LSQ_E_RANK};
   if (kap * unit_roundoff(c.us) >= 1.0) info->flags |= LSQ_WARN_COND;
   if (c.uw == LSQ_F32)
-    fr.ls = stage_lsqr<float>(c, fr.a32, c.lda32, fr.rc.R32, fr.rc.L32, fr.x0, x);
+    fr.ls = stage_lsqr<float>(c, fr.a32, c.lda32, fr.rc.f32, fr.x0, x);
   else
-    fr.ls = stage_lsqr<double>(c, c.A, c.lda, fr.rc.R64, fr.rc.L64, fr.x0, x);
+    fr.ls = stage_lsqr<double>(c, c.A, c.lda, fr.rc.f64, fr.x0, x);
   info->lsqr_its = fr.ls.its;
   info->lsqr_flag = fr.ls.flag;
   info->lsqr_normr = fr.ls.normr;
@@ -639,11 +837,19 @@ lsq_status lsq_create(lsq_handle** out, void* cuda_stream) {
     delete h;
     return LSQ_E_CUDA;
   }
-  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return LSQ_E_CUDA;
+  }
   if (cudaMalloc(&h->d_err, 64) != cudaSuccess || cudaMemset(h->d_err, 0, 64) != cudaSuccess ||
       cudaMallocHost(&h->h_pinned, 4096) != cudaSuccess) {
     cudaGetLastError();
     if (h->d_err) cudaFree(h->d_err);
+    cudaStreamDestroy(h->stream);
     delete h;
     return LSQ_E_NOMEM;
   }
@@ -654,11 +860,16 @@ lsq_status lsq_create(lsq_handle** out, void* cuda_stream) {
 lsq_status lsq_destroy(lsq_handle* h) {
   if (!h) return LSQ_E_INVAL;
   cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs) delete kv.second;
+  h->graphs.clear();
   for (auto& kv : h->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (auto e : h->events) cudaEventDestroy(e);
   if (h->d_err) cudaFree(h->d_err);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return LSQ_OK;
 }
@@ -764,9 +975,9 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
     bool conv;
     if (c.uw == LSQ_F32)
-      conv = stage_refine<float>(c, fr.a32, c.lda32, fr.rc.R32, fr.rc.L32, fr.rc, x, rr, inf);
+      conv = stage_refine<float>(c, fr.a32, c.lda32, fr.rc, x, rr, inf);
     else
-      conv = stage_refine<double>(c, c.A, c.lda, fr.rc.R64, fr.rc.L64, fr.rc, x, rr, inf);
+      conv = stage_refine<double>(c, c.A, c.lda, fr.rc, x, rr, inf);
     const double kap = c.o.kappa_hint > 0 ? c.o.kappa_hint : inf->kappa_R_est;
     if (!conv && !c.o.no_escalate && kap < 1.0 / unit_roundoff(c.us) && c.uw == LSQ_F32) {
       // Sec. 5: re-run the refinement from (x0, r0) with u_A = u_L = u_R = u^2 (FP64 here)
@@ -774,7 +985,7 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
       CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
       inf->escalated = 1;
       inf->flags |= LSQ_INFO_ESCALATED;
-      conv = stage_refine<double>(c, c.A, c.lda, fr.rc.R64, fr.rc.L64, fr.rc, x, rr, inf);
+      conv = stage_refine<double>(c, c.A, c.lda, fr.rc, x, rr, inf);
     }
     inf->ir_converged = conv ? 1 : 0;
     return conv ? LSQ_OK : LSQ_NOT_CONVERGED;

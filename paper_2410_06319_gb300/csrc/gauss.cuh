@@ -12,7 +12,7 @@
 // used by a sketch in precision u_s is fl_s(G), round to nearest even.
 //
 // Evaluation on GB300: FP64 is a slow pipe, so G is first evaluated in FP32
-// (fast_*) with a relative error below 2^-21 against the FP64 definition;
+// (fast_*) with a relative error below 2^-20.4 against the FP64 definition;
 // if both ends of [g32 (1 - 2^-19), g32 (1 + 2^-19)] round to the same u_s
 // value, that value is fl_s(G) exactly.  Otherwise the FP64 definition is
 // evaluated and rounded (round-to-odd to FP32, then to u_s: a single
@@ -26,7 +26,7 @@
 
 namespace lsq {
 
-enum SFmt : int { FMT_F64 = 0, FMT_F32 = 1, FMT_F16 = 2, FMT_BF16 = 3, FMT_E4M3 = 4 };
+enum SFmt : int { FMT_F64 = 0, FMT_F32 = 1, FMT_F16 = 2, FMT_BF16 = 3, FMT_E4M3 = 4, FMT_BF16X3 = 5 };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -131,11 +131,13 @@ __device__ __forceinline__ void spec_gauss_pair(uint32_t a, uint32_t b, double& 
 }
 
 // ------------------------------------------------------------ FP32 evaluation
-// Relative error against the FP64 definition is below 2^-21 (argument: U1 or
-// 1 - U1 and r are converted with relative error 2^-24, the atanh and sin/cos
-// series are truncated below 2^-28, every other step adds a few FP32 ulps,
-// and the radius halves the relative error of ln).  kFastRelBound = 2^-19
-// leaves a factor-four margin.
+// Relative error against the FP64 definition, first order: ln U1 <= 12 ulp
+// (conversion of U1 or 1 - U1: 1 ulp, amplified <= 2.9x where |ln U1| >= 0.35;
+// the quotient z: f + 1 rounded plus a 2-ulp __fdividef; series rounding and
+// truncation < 2 ulp; e ln2 + ln f with cancellation <= 2x), so the radius is
+// within 6.5 ulp; the reduced angle is within 2.5 ulp (30-bit r converted,
+// pi/2 rounded, one product) and sin/cos within 4.5 ulp; the final product adds
+// 1 ulp.  Total 12 ulp = 2^-20.4; kFastRelBound = 2^-19 leaves a 2.6x margin.
 constexpr float kFastRelBound = 0x1p-19f;
 
 __device__ __forceinline__ float fast_ln_u1(uint32_t a) {
@@ -241,24 +243,31 @@ __device__ __forceinline__ bool round_checked(float g, uint32_t& out) {
   return lo == hi;
 }
 
+// FP32 evaluation of one (a, b) word pair; false when the FP64 definition is
+// needed for either entry (near a rounding boundary of u_s, or U1 = 1).
+template <int FMT>
+__device__ __forceinline__ bool gauss_pair_fast(uint32_t a, uint32_t b, uint32_t& be, uint32_t& bo) {
+  const float rad = __fsqrt_rn(-2.0f * fast_ln_u1(a));
+  float c, s;
+  fast_cos_sin_2pi(b, c, s);
+  const bool oke = round_checked<FMT>(rad * c, be);
+  const bool oko = round_checked<FMT>(rad * s, bo);
+  return oke && oko && a != 0xFFFFFFFFu;
+}
+
+// The FP64 definition, rounded once into u_s.
+template <int FMT>
+__device__ __forceinline__ void gauss_pair_slow(uint32_t a, uint32_t b, uint32_t& be, uint32_t& bo) {
+  double ge, go;
+  spec_gauss_pair(a, b, ge, go);
+  be = round_f64<FMT>(ge);
+  bo = round_f64<FMT>(go);
+}
+
 // fl_s(G) bits of the two entries served by one (a, b) word pair.
 template <int FMT>
 __device__ __forceinline__ void gauss_pair_bits(uint32_t a, uint32_t b, uint32_t& be, uint32_t& bo) {
-  bool ok = false;
-  if (a != 0xFFFFFFFFu) {
-    const float rad = __fsqrt_rn(-2.0f * fast_ln_u1(a));
-    float c, s;
-    fast_cos_sin_2pi(b, c, s);
-    const bool oke = round_checked<FMT>(rad * c, be);
-    const bool oko = round_checked<FMT>(rad * s, bo);
-    ok = oke && oko;
-  }
-  if (!ok) {  // rare: within the error bound of a rounding boundary, or U1 = 1
-    double ge, go;
-    spec_gauss_pair(a, b, ge, go);
-    be = round_f64<FMT>(ge);
-    bo = round_f64<FMT>(go);
-  }
+  if (!gauss_pair_fast<FMT>(a, b, be, bo)) gauss_pair_slow<FMT>(a, b, be, bo);
 }
 
 }  // namespace lsq

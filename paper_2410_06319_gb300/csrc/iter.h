@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "kernels.h"
+
 namespace lsq {
 
 // LSQR (Paige & Saunders 1982) scalars, kept on the device so that iterations
@@ -26,6 +28,12 @@ template <typename TP>
 cudaError_t launch_pass_lsqr_any(const TP* A, int64_t lda, int64_t m, int64_t n, const TP* t,
                                  const TP* u_in, const double* cu_ptr, double cu_mul, TP* u_out,
                                  TP* Pblk, double* sq, int nblk, const int* done, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lsqr_colsum(const T* P, int nblk, int64_t n, const double* sq, LsqrState* st,
+                               bool init, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lsqr_step(const Tri<T>& f, const T* s, T* v, T* w, T* z, T* t, LsqrState* st,
+                             bool init, cudaStream_t strm);
 cudaError_t launch_lsqr_beta(const double* sq, int nblk, LsqrState* st, bool init, cudaStream_t s);
 template <typename T>
 cudaError_t launch_lsqr_init(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s);
@@ -43,9 +51,12 @@ cudaError_t launch_sum_partials(const double* partial, int nblk, double* out, bo
 cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n, double* V0,
                           double* sq_partial, int nblk, cudaStream_t s);
 cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s);
-cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, int nblk, cudaStream_t s);
-cudaError_t launch_gm_mdot(const double* V, int64_t ld, const double* w, int64_t len, const GmState* st,
-                           int maxc, double* Dp, int nblk, cudaStream_t s);
+cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
+                             int nblk, cudaStream_t s);
+// Partial dots of w with V[:, 0..j]; with az, first forms w_top = V[:m, j] + az.
+template <typename TAZ>
+cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
+                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m);
 cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
                            int ldh, cudaStream_t s);
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
@@ -53,7 +64,7 @@ cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double*
 cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
                              double* cs, double* sn, double* g, cudaStream_t s);
 cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
-                             int nblk, cudaStream_t s);
+                             float* v32, int64_t m, int nblk, cudaStream_t s);
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
                             cudaStream_t s);
 template <typename TB>

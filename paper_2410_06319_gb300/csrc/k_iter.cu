@@ -8,10 +8,26 @@
 // P is reduced per CTA (fixed order) and then across CTAs by colsum, so the
 // results are deterministic.
 #include "common.cuh"
-#include "kernels.h"
 #include "iter.h"
+#include "kernels.h"
+#include "trsv.cuh"
 
 namespace lsq {
+
+// ============================================================ block helpers
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[32] = t;
+  __syncthreads();
+  return red[32];
+}
+
 
 template <typename T, int VW>
 struct VecOf;
@@ -58,11 +74,18 @@ struct PassArgs {
   T* Pblk;
   double* sq;
   const int* done;
+  const int* jp;         // FGMRES: x and v are column (*jp) of their bases
+  int64_t xstr, vstr;
 };
 
 template <typename T, int VW, int VPL, int MODE>
-__global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> p) {
+__global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
   if (p.done && *p.done) return;
+  if (p.jp) {
+    const int64_t j = *p.jp;
+    p.x += j * p.xstr;
+    p.v += j * p.vstr;
+  }
   extern __shared__ __align__(16) unsigned char pass_smem[];
   T* red = reinterpret_cast<T*>(pass_smem);          // [8 warps][nv * VW]
   __shared__ double sqred[8];
@@ -179,7 +202,225 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> p) {
   }
 }
 
-int pass_blocks(int num_sms) { return 2 * num_sms; }
+// ------------------------------------------------------------ bulk-streamed passes
+// A producer warp streams stages of 8 consecutive rows of A into a shared-memory
+// ring with cp.async.bulk (completion on an mbarrier); eight consumer warps take
+// one row of each stage.  Each CTA owns a contiguous range of rows.  The per-row
+// scalars of the next stage are loaded one stage ahead.
+//   PM_LSQR: q = A t + cu u ; u_out = q ; P = A^T q ; sq = sum q^2
+//   PM_FGM : az = A z ; P = A^T v            (v_top + az is formed by gm_mdot)
+//   PM_RES : f = b - r - A x ; P = A^T (-r)
+constexpr int kBulkRows = 8;
+constexpr int kBulkThreads = (kBulkRows + 1) * 32;
+
+template <typename T>
+struct BulkArgs {
+  const T* A;
+  int64_t lda, m;
+  int n, nv, stages;
+  int64_t rows_per_cta;
+  const T* x;                  // multiplied vector (nv * VW entries, zero padded)
+  const int* jp;               // FGM: x and v are column (*jp) of their bases
+  int64_t xstr, vstr;
+  const T* uin;                // LSQR
+  T* uout;
+  const double* cu_ptr;
+  double cu_mul;
+  const T* v;                  // FGM coefficient vector
+  T* az;
+  const double* r;             // RES
+  const double* b;
+  double* f;
+  T* Pblk;
+  double* sq;
+  const int* done;
+  int* err;
+};
+
+template <typename T, int VW, int VPL, int MODE>
+__global__ void __launch_bounds__(kBulkThreads, 1) pass_bulk_kernel(BulkArgs<T> p) {
+  if (p.done && *p.done) return;
+  if (MODE == PM_FGM && p.jp) {
+    const int64_t j = *p.jp;
+    p.x += j * p.xstr;
+    p.v += j * p.vstr;
+  }
+  extern __shared__ __align__(128) unsigned char bulk_smem[];
+  const uint32_t stage_bytes = (uint32_t)(kBulkRows * p.lda * sizeof(T));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bulk_smem + (size_t)p.stages * stage_bytes);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + p.stages);
+  __shared__ double sqred[kBulkRows];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * p.rows_per_cta;
+  const int64_t r1 = min(p.m, r0 + p.rows_per_cta);
+  const int nst = r0 < r1 ? (int)((r1 - r0 + kBulkRows - 1) / kBulkRows) : 0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < p.stages; ++k) {
+      mbar_init(full0 + 8 * k, 1);
+      mbar_init(empty0 + 8 * k, kBulkRows);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+  T acc[VPL][VW];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v)
+#pragma unroll
+    for (int k = 0; k < VW; ++k) acc[v][k] = T(0);
+  float sqacc = 0.f;
+  if (warp == kBulkRows) {
+    // ---------------- producer
+    if (lane == 0) {
+      for (int it = 0; it < nst; ++it) {
+        const int slot = it % p.stages;
+        const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+        if (!mbar_wait(empty0 + 8 * slot, ph ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) break;
+        const int64_t row0 = r0 + (int64_t)it * kBulkRows;
+        const int rows = (int)min((int64_t)kBulkRows, r1 - row0);
+        const uint32_t bytes = (uint32_t)(rows * p.lda * sizeof(T));
+        mbar_arrive_expect_tx(full0 + 8 * slot, bytes);
+        bulk_load(smem_u32(bulk_smem + (size_t)slot * stage_bytes), p.A + row0 * p.lda, bytes,
+                  full0 + 8 * slot);
+      }
+    }
+  } else {
+    // ---------------- consumers: warp `warp` takes row `warp` of every stage
+    T xv[VPL][VW];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      const int idx = lane + 32 * v;
+      if (idx < p.nv) {
+        load_vec<T, VW>(p.x + (int64_t)idx * VW, xv[v], false);
+      } else {
+        for (int k = 0; k < VW; ++k) xv[v][k] = T(0);
+      }
+    }
+    const T cu = (MODE == PM_LSQR) ? (T)((p.cu_ptr ? *p.cu_ptr : 1.0) * p.cu_mul) : T(0);
+    // per-row scalars, one stage ahead
+    auto scal = [&](int it, double& s0, double& s1) {
+      const int64_t row = r0 + (int64_t)it * kBulkRows + warp;
+      s0 = 0.0;
+      s1 = 0.0;
+      if (it < nst && row < r1) {
+        if (MODE == PM_LSQR) s0 = (double)p.uin[row];
+        if (MODE == PM_FGM) s0 = (double)p.v[row];
+        if (MODE == PM_RES) {
+          s0 = p.r[row];
+          s1 = p.b[row];
+        }
+      }
+    };
+    double n0, n1;
+    scal(0, n0, n1);
+    for (int it = 0; it < nst; ++it) {
+      const double c0 = n0, c1s = n1;
+      scal(it + 1, n0, n1);
+      const int slot = it % p.stages;
+      const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+      if (!mbar_wait(full0 + 8 * slot, ph, p.err, DEV_TIMEOUT_FULL)) break;
+      const int64_t row = r0 + (int64_t)it * kBulkRows + warp;
+      if (row < r1) {
+        const T* srow = reinterpret_cast<const T*>(bulk_smem + (size_t)slot * stage_bytes) + warp * p.lda;
+        T a[VPL][VW];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const int idx = lane + 32 * v;
+          if (idx < p.nv) {
+            load_vec<T, VW>(srow + idx * VW, a[v], false);
+          } else {
+            for (int k = 0; k < VW; ++k) a[v][k] = T(0);
+          }
+        }
+        T d = 0;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+          for (int k = 0; k < VW; ++k) d = fma(a[v][k], xv[v][k], d);
+        d = warp_sum(d);
+        T coef;
+        if (MODE == PM_LSQR) {
+          const T q = d + cu * (T)c0;
+          coef = q;
+          if (lane == 0) {
+            p.uout[row] = q;
+            sqacc = fmaf((float)q, (float)q, sqacc);
+          }
+        } else if (MODE == PM_FGM) {
+          coef = (T)c0;
+          if (lane == 0) p.az[row] = d;
+        } else {
+          coef = (T)(-c0);
+          if (lane == 0) p.f[row] = (c1s - c0) - (double)d;
+        }
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+          for (int k = 0; k < VW; ++k) acc[v][k] = fma(coef, a[v][k], acc[v][k]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+    }
+  }
+  __syncthreads();   // every stage consumed: the ring is free for the reduction
+  const int width = p.nv * VW;
+  T* red = reinterpret_cast<T*>(bulk_smem);
+  if (warp < kBulkRows) {
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      const int idx = lane + 32 * v;
+      if (idx < p.nv) {
+        for (int k = 0; k < VW; ++k) red[warp * width + idx * VW + k] = acc[v][k];
+      }
+    }
+    if (MODE == PM_LSQR && lane == 0) sqred[warp] = (double)sqacc;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < p.n; c += blockDim.x) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < kBulkRows; ++w) s += red[w * width + c];
+    p.Pblk[(int64_t)blockIdx.x * p.n + c] = s;
+  }
+  if (MODE == PM_LSQR && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kBulkRows; ++w) s += sqred[w];
+    p.sq[blockIdx.x] = s;
+  }
+}
+
+int bulk_blocks(int num_sms) { return num_sms; }
+
+template <typename T, int VW, int MODE>
+static cudaError_t dispatch_bulk(BulkArgs<T> p, int nblk, int num_sms_unused, cudaStream_t st) {
+  const int vpl = (p.nv + 31) / 32;
+  const size_t stage_bytes = (size_t)kBulkRows * p.lda * sizeof(T);
+  const size_t budget = 200 * 1024;
+  int stages = (int)(budget / stage_bytes);
+  if (stages > 12) stages = 12;
+  if (stages < 2) return cudaErrorInvalidValue;
+  p.stages = stages;
+  p.rows_per_cta = ((p.m + nblk - 1) / nblk + kBulkRows - 1) / kBulkRows * kBulkRows;
+  const size_t red_bytes = (size_t)kBulkRows * p.nv * VW * sizeof(T);
+  size_t smem = (size_t)stages * stage_bytes;
+  if (smem < red_bytes) smem = red_bytes;
+  smem += 2 * stages * 8;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nblk, kBulkThreads, smem, st>>>(p);
+    return cudaGetLastError();
+  };
+  if (vpl <= 1) return go(pass_bulk_kernel<T, VW, 1, MODE>);
+  if (vpl <= 2) return go(pass_bulk_kernel<T, VW, 2, MODE>);
+  if (vpl <= 4) return go(pass_bulk_kernel<T, VW, 4, MODE>);
+  if (vpl <= 8) return go(pass_bulk_kernel<T, VW, 8, MODE>);
+  if constexpr (VW <= 2) {
+    if (vpl <= 16) return go(pass_bulk_kernel<T, VW, 16, MODE>);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int pass_blocks(int num_sms) { return num_sms; }
 
 template <typename T, int VW, int MODE>
 static cudaError_t dispatch_pass(const PassArgs<T>& p, int nblk, cudaStream_t st) {
@@ -211,10 +452,31 @@ static int f64_vw(const double* A, int64_t lda, int64_t n) {
   return ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda % 2) == 0 && (n % 2) == 0) ? 2 : 1;
 }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 template <typename T>
 cudaError_t launch_pass_lsqr_t(const T* A, int64_t lda, int64_t m, int64_t n, const T* t,
                                const T* u_in, const double* cu_ptr, double cu_mul, T* u_out, T* Pblk,
                                double* sq, int nblk, const int* done, cudaStream_t st) {
+  int vw = 4;
+  if constexpr (sizeof(T) == 8) vw = f64_vw(A, lda, n);
+  if (aligned16(A) && (sizeof(T) == 4 || lda % 2 == 0)) {
+    BulkArgs<T> b{};
+    b.A = A; b.lda = lda; b.m = m; b.n = (int)n;
+    b.x = t; b.uin = u_in; b.uout = u_out; b.cu_ptr = cu_ptr; b.cu_mul = cu_mul;
+    b.Pblk = Pblk; b.sq = sq; b.done = done;
+    if constexpr (sizeof(T) == 4) {
+      b.nv = (int)((lda + 3) / 4);
+      return dispatch_bulk<float, 4, PM_LSQR>(b, nblk, 0, st);
+    } else {
+      if (vw == 2) {
+        b.nv = (int)(n / 2);
+        return dispatch_bulk<double, 2, PM_LSQR>(b, nblk, 0, st);
+      }
+      b.nv = (int)n;
+      return dispatch_bulk<double, 1, PM_LSQR>(b, nblk, 0, st);
+    }
+  }
   PassArgs<T> p{};
   p.A = A; p.lda = lda; p.m = m; p.n = (int)n;
   p.x = t; p.uin = u_in; p.uout = u_out; p.cu_ptr = cu_ptr; p.cu_mul = cu_mul;
@@ -223,7 +485,7 @@ cudaError_t launch_pass_lsqr_t(const T* A, int64_t lda, int64_t m, int64_t n, co
     p.nv = (int)((lda + 3) / 4);   // A32 rows are zero padded to lda (a multiple of 4)
     return dispatch_pass<float, 4, PM_LSQR>(p, nblk, st);
   } else {
-    if (f64_vw(A, lda, n) == 2) {
+    if (vw == 2) {
       p.nv = (int)(n / 2);
       return dispatch_pass<double, 2, PM_LSQR>(p, nblk, st);
     }
@@ -241,33 +503,49 @@ cudaError_t launch_pass_lsqr(const float* A32, int64_t lda32, int64_t m, int64_t
 
 template <typename TA>
 cudaError_t launch_pass_fgm(const TA* A, int64_t lda, int64_t m, int64_t n, const TA* z,
-                            const double* v, const double* vs_ptr, double* wtop, TA* Pblk, int nblk,
-                            const int* done, cudaStream_t st) {
-  PassArgs<TA> p{};
-  p.A = A; p.lda = lda; p.m = m; p.n = (int)n;
-  p.x = z; p.v = v; p.vs_ptr = vs_ptr; p.wtop = wtop; p.Pblk = Pblk; p.done = done;
+                            const TA* v, TA* az, TA* Pblk, int nblk, const int* done, cudaStream_t st,
+                            const int* jp, int64_t zs, int64_t vstr, int* err) {
+  BulkArgs<TA> b{};
+  b.A = A; b.lda = lda; b.m = m; b.n = (int)n;
+  b.x = z; b.v = v; b.az = az; b.Pblk = Pblk; b.done = done; b.err = err;
+  b.jp = jp; b.xstr = zs; b.vstr = vstr;
   if constexpr (sizeof(TA) == 4) {
-    p.nv = (int)((lda + 3) / 4);
-    return dispatch_pass<float, 4, PM_FGM>(p, nblk, st);
+    if (!aligned16(A) || (lda % 4) != 0) return cudaErrorInvalidValue;
+    b.nv = (int)((lda + 3) / 4);
+    return dispatch_bulk<float, 4, PM_FGM>(b, nblk, 0, st);
   } else {
-    if (f64_vw(A, lda, n) == 2) {
-      p.nv = (int)(n / 2);
-      return dispatch_pass<double, 2, PM_FGM>(p, nblk, st);
+    if (!aligned16(A) || (lda % 2) != 0) {
+      return cudaErrorInvalidValue;
     }
-    p.nv = (int)n;
-    return dispatch_pass<double, 1, PM_FGM>(p, nblk, st);
+    if (f64_vw(A, lda, n) == 2) {
+      b.nv = (int)(n / 2);
+      return dispatch_bulk<double, 2, PM_FGM>(b, nblk, 0, st);
+    }
+    b.nv = (int)n;
+    return dispatch_bulk<double, 1, PM_FGM>(b, nblk, 0, st);
   }
 }
 template cudaError_t launch_pass_fgm<float>(const float*, int64_t, int64_t, int64_t, const float*,
-                                            const double*, const double*, double*, float*, int,
-                                            const int*, cudaStream_t);
+                                            const float*, float*, float*, int, const int*,
+                                            cudaStream_t, const int*, int64_t, int64_t, int*);
 template cudaError_t launch_pass_fgm<double>(const double*, int64_t, int64_t, int64_t, const double*,
-                                             const double*, const double*, double*, double*, int,
-                                             const int*, cudaStream_t);
+                                             const double*, double*, double*, int, const int*,
+                                             cudaStream_t, const int*, int64_t, int64_t, int*);
 
 cudaError_t launch_pass_res(const double* A, int64_t lda, int64_t m, int64_t n, const double* x,
                             const double* r, const double* b, double* f, double* Pblk, int nblk,
                             cudaStream_t st) {
+  if (aligned16(A) && lda % 2 == 0) {
+    BulkArgs<double> q{};
+    q.A = A; q.lda = lda; q.m = m; q.n = (int)n;
+    q.x = x; q.r = r; q.b = b; q.f = f; q.Pblk = Pblk;
+    if (f64_vw(A, lda, n) == 2) {
+      q.nv = (int)(n / 2);
+      return dispatch_bulk<double, 2, PM_RES>(q, nblk, 0, st);
+    }
+    q.nv = (int)n;
+    return dispatch_bulk<double, 1, PM_RES>(q, nblk, 0, st);
+  }
   PassArgs<double> p{};
   p.A = A; p.lda = lda; p.m = m; p.n = (int)n;
   p.x = x; p.r = r; p.b = b; p.f = f; p.Pblk = Pblk;
@@ -315,20 +593,6 @@ template cudaError_t launch_colsum<double, float>(const double*, int, int64_t, c
                                                   float*, const int*, cudaStream_t);
 template cudaError_t launch_colsum<float, double>(const float*, int, int64_t, const double*, double,
                                                   double*, const int*, cudaStream_t);
-
-// ============================================================ block helpers
-__device__ __forceinline__ double block_sum_d(double v, double* red) {
-  v = warp_sum(v);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-  if (warp == 0) t = warp_sum(t);
-  if (threadIdx.x == 0) red[32] = t;
-  __syncthreads();
-  return red[32];
-}
 
 // ============================================================ LSQR kernels
 // beta = sqrt(sum sq); us = 1/beta.
@@ -463,6 +727,156 @@ template cudaError_t launch_pass_lsqr_any<double>(const double*, int64_t, int64_
                                                   const double*, const double*, double, double*,
                                                   double*, double*, int, const int*, cudaStream_t);
 
+// ------------------------------------------------------------ fused LSQR step
+// beta = ||q|| from the per-CTA sums of squares (every CTA recomputes it);
+// out[c] = (A^T q)_c / beta.  Block 0 publishes beta and 1/beta.
+template <typename TP>
+__global__ void lsqr_colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, const double* sq,
+                                   LsqrState* st, bool init, TP* __restrict__ out) {
+  if (!init && st->done) return;
+  __shared__ double part[32][33];
+  __shared__ double beta_s;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  double q = 0.0;
+  for (int b = tid; b < nblk; b += 1024) q += sq[b];
+  q = warp_sum(q);
+  if (tx == 0) part[ty][32] = q;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += part[k][32];
+    beta_s = sqrt(t);
+  }
+  __syncthreads();
+  const double beta = beta_s;
+  const double us = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (blockIdx.x == 0 && tid == 0) {
+    st->beta = beta;
+    st->us = us;
+    if (init) st->phibar = beta;
+  }
+  const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+  double sacc = 0.0;
+  if (c < n)
+    for (int b = ty; b < nblk; b += 32) sacc += (double)P[(int64_t)b * n + c];
+  part[ty][tx] = sacc;
+  __syncthreads();
+  if (ty == 0 && c < n) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += part[k][tx];
+    out[c] = (TP)(t * us);
+  }
+}
+
+// One CTA: vt = R^-T s ; (init) alpha v = vt, w = v, z = 0 ; (iteration)
+// alpha v = vt - beta v, plane rotation, z += (phi/rho) w, w = v - (theta/rho) w,
+// stopping tests ; then t = R^-1 v for the next pass.
+template <typename T>
+__global__ void __launch_bounds__(1024)
+    lsqr_step_kernel(Tri<T> f, const T* __restrict__ s, T* __restrict__ v, T* __restrict__ w,
+                     T* __restrict__ z, T* __restrict__ t, LsqrState* st, bool init) {
+  if (!init && st->done) return;
+  __shared__ T xs[1024];
+  __shared__ double red[33];
+  __shared__ double coef[3];
+  extern __shared__ __align__(16) unsigned char step_buf[];
+  const int n = (int)f.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = s[i];
+  __syncthreads();
+  block_trsv<T, false>(f.L, f.ld, f.DL, n, xs, step_buf);       // xs = R^-T s
+  const double beta = st->beta;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T vv = init ? xs[i] : xs[i] - (T)beta * v[i];
+    ss += (double)vv * (double)vv;
+  }
+  ss = block_sum_d(ss, red);
+  const double alpha = sqrt(ss);
+  if (threadIdx.x == 0) {
+    if (init) {
+      st->alpha = alpha;
+      st->rhobar = alpha;
+      st->anorm2 = 0.0;
+      st->its = 0;
+      st->normr = beta;
+      st->normar = alpha * beta;
+      st->normA = 0.0;
+      st->flag = (beta == 0.0 || alpha == 0.0) ? 3 : 0;
+      st->done = (st->flag != 0 || st->maxit <= 0) ? 1 : 0;
+      coef[0] = 0.0;
+      coef[1] = 0.0;
+    } else {
+      const double alpha_old = st->alpha;
+      const double anorm2 = st->anorm2 + alpha_old * alpha_old + beta * beta;
+      const double rhobar = st->rhobar;
+      const double rho = sqrt(rhobar * rhobar + beta * beta);
+      const double c = rhobar / rho, sn = beta / rho;
+      const double theta = sn * alpha;
+      const double phi = c * st->phibar;
+      const double phibar = sn * st->phibar;
+      coef[0] = phi / rho;
+      coef[1] = theta / rho;
+      st->rhobar = -c * alpha;
+      st->phibar = phibar;
+      st->anorm2 = anorm2;
+      st->alpha = alpha;
+      st->its += 1;
+      st->normr = fabs(phibar);
+      st->normar = fabs(phibar * alpha * c);
+      st->normA = sqrt(anorm2);
+      int flag = 0;
+      if (st->normr <= st->tol * st->normb) flag = 1;
+      else if (st->normar <= st->tol * st->normA * st->normr) flag = 2;
+      else if (beta == 0.0 || alpha == 0.0) flag = 3;
+      st->flag = flag;
+      st->done = (flag != 0 || st->its >= st->maxit) ? 1 : 0;
+    }
+    st->cu = -alpha * st->us;
+  }
+  __syncthreads();
+  const T ia = alpha > 0.0 ? (T)(1.0 / alpha) : T(0);
+  const T c0 = (T)coef[0], c1 = (T)coef[1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T vn = (init ? xs[i] : xs[i] - (T)beta * v[i]) * ia;
+    if (init) {
+      w[i] = vn;
+      z[i] = T(0);
+    } else {
+      const T wi = w[i];
+      z[i] = z[i] + c0 * wi;
+      w[i] = vn - c1 * wi;
+    }
+    v[i] = vn;
+    xs[i] = vn;
+  }
+  __syncthreads();
+  block_trsv<T, true>(f.R, f.ld, f.DU, n, xs, step_buf);        // t = R^-1 v
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = xs[i];
+}
+
+template <typename T>
+cudaError_t launch_lsqr_colsum(const T* P, int nblk, int64_t n, const double* sq, LsqrState* st,
+                               bool init, T* out, cudaStream_t s) {
+  lsqr_colsum_kernel<T><<<(unsigned)((n + 31) / 32), dim3(32, 32), 0, s>>>(P, nblk, n, sq, st, init, out);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_lsqr_step(const Tri<T>& f, const T* s, T* v, T* w, T* z, T* t, LsqrState* st,
+                             bool init, cudaStream_t strm) {
+  if (f.n > 1024) return cudaErrorInvalidValue;
+  const size_t smem = TrsvSmem<T>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(lsqr_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  lsqr_step_kernel<T><<<1, 1024, smem, strm>>>(f, s, v, w, z, t, st, init);
+  return cudaGetLastError();
+}
+template cudaError_t launch_lsqr_colsum<float>(const float*, int, int64_t, const double*, LsqrState*, bool, float*, cudaStream_t);
+template cudaError_t launch_lsqr_colsum<double>(const double*, int, int64_t, const double*, LsqrState*, bool, double*, cudaStream_t);
+template cudaError_t launch_lsqr_step<float>(const Tri<float>&, const float*, float*, float*, float*, float*, LsqrState*, bool, cudaStream_t);
+template cudaError_t launch_lsqr_step<double>(const Tri<double>&, const double*, double*, double*, double*, double*, LsqrState*, bool, cudaStream_t);
+
 // ============================================================ vector kernels
 // out[i] = x[i] * a + y[i] * b  (types converted), i < len
 template <typename TX, typename TY, typename TO>
@@ -535,34 +949,53 @@ __global__ void gm_init_kernel(const double* sq_partial, int nblk, GmState* st, 
   }
 }
 
-// partial dots of w with V[:, 0..j] over a row range: Dp[b][c]
-__global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
-                               int64_t len, const GmState* st, int maxc, double* Dp) {
+// partial dots of w with V[:, 0..j] over a row range: Dp[b][c]; one warp per
+// column (no block-wide barrier per column), w's range cached in L1.
+template <typename TAZ>
+__global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, double* __restrict__ w,
+                               int64_t len, const GmState* st, int maxc, double* Dp,
+                               const TAZ* __restrict__ az, int64_t m) {
   if (st->done) return;
-  __shared__ double red[33];
   const int ncols = st->j + 1;
   const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(len, r0 + chunk);
-  for (int c = 0; c < ncols; ++c) {
-    double s = 0.0;
+  if (az) {  // w_top = v_top + A z for this block's rows (the pass left A z in az)
+    const double* vj = V + (int64_t)(ncols - 1) * ld;
+    for (int64_t i = r0 + threadIdx.x; i < min(r1, m); i += blockDim.x) w[i] = vj[i] + (double)az[i];
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncols; c += nw) {
     const double* vc = V + (int64_t)c * ld;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) s += vc[i] * w[i];
-    s = block_sum_d(s, red);
-    if (threadIdx.x == 0) Dp[(int64_t)blockIdx.x * maxc + c] = s;
+    double s = 0.0;
+    for (int64_t i = r0 + lane; i < r1; i += 32) s += vc[i] * w[i];
+    s = warp_sum(s);
+    if (lane == 0) Dp[(int64_t)blockIdx.x * maxc + c] = s;
   }
 }
 
-// h[c] = sum_b Dp[b][c] ; H[c][j] += h[c]
+// h[c] = sum_b Dp[b][c] ; H[c][j] += h[c]   (one 32 x 32 block, fixed order)
 __global__ void gm_hsum_kernel(const double* Dp, int nblk, int maxc, GmState* st, double* h,
                                double* H, int ldh) {
   if (st->done) return;
+  __shared__ double part[32][33];
   const int ncols = st->j + 1;
-  const int c = threadIdx.x;
-  if (c >= ncols) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += Dp[(int64_t)b * maxc + c];
-  h[c] = s;
-  H[(int64_t)st->j * ldh + c] += s;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int c0 = 0; c0 < ncols; c0 += 32) {
+    const int c = c0 + tx;
+    double s = 0.0;
+    if (c < ncols)
+      for (int b = ty; b < nblk; b += 32) s += Dp[(int64_t)b * maxc + c];
+    part[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && c < ncols) {
+      double t = 0.0;
+      for (int k = 0; k < 32; ++k) t += part[k][tx];
+      h[c] = t;
+      H[(int64_t)st->j * ldh + c] += t;
+    }
+    __syncthreads();
+  }
 }
 
 // w[i] -= sum_c V[c][i] h[c] ; optional partial ||w||^2
@@ -594,51 +1027,70 @@ __global__ void gm_finish_kernel(const double* sq_partial, int nblk, GmState* st
                                  double* cs, double* sn, double* g) {
   if (st->done) return;
   __shared__ double red[33];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
-  s = block_sum_d(s, red);
-  if (threadIdx.x != 0) return;
+  __shared__ double hcs[130], css[130], sns[130];
   const int j = st->j;
   double* hc = H + (int64_t)j * ldh;
-  const double hn = sqrt(s);
-  hc[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
-    hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-    hc[i] = t;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    hcs[i] = hc[i];
+    css[i] = cs[i];
+    sns[i] = sn[i];
   }
-  const double den = hypot(hc[j], hc[j + 1]);
-  cs[j] = den > 0.0 ? hc[j] / den : 1.0;
-  sn[j] = den > 0.0 ? hc[j + 1] / den : 0.0;
-  hc[j] = den;
-  hc[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  st->relres = fabs(g[j + 1]) / st->beta0;
-  st->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
-  st->j = j + 1;
-  st->done = (st->relres <= st->tol || st->j >= st->maxit || hn == 0.0) ? 1 : 0;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
+  s = block_sum_d(s, red);   // contains the barriers that publish hcs/css/sns
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(s);
+    hcs[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = css[i] * hcs[i] + sns[i] * hcs[i + 1];
+      hcs[i + 1] = -sns[i] * hcs[i] + css[i] * hcs[i + 1];
+      hcs[i] = t;
+    }
+    const double den = hypot(hcs[j], hcs[j + 1]);
+    cs[j] = den > 0.0 ? hcs[j] / den : 1.0;
+    sn[j] = den > 0.0 ? hcs[j + 1] / den : 0.0;
+    hcs[j] = den;
+    hcs[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    st->relres = fabs(g[j + 1]) / st->beta0;
+    st->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
+    st->j = j + 1;
+    st->done = (st->relres <= st->tol || st->j >= st->maxit || hn == 0.0) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = hcs[i];
 }
 
 // V[:, j] = w * inv_h  (j read after gm_finish incremented it)
 __global__ void gm_newcol_kernel(const double* __restrict__ w, int64_t len, const GmState* st,
-                                 double* __restrict__ V, int64_t ld) {
+                                 double* __restrict__ V, int64_t ld, float* __restrict__ v32, int64_t m) {
   if (st->done) return;
   const double s = st->inv_h;
   double* vc = V + (int64_t)st->j * ld;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x)
-    vc[i] = w[i] * s;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[i] * s;
+    vc[i] = v;
+    if (v32 && i < m) v32[i] = (float)v;
+  }
 }
 
-// y = H[:k,:k]^-1 g[:k]  (k = st->j)
+// y = H[:k,:k]^-1 g[:k]  (k = st->j): one warp, column-oriented back substitution
 __global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, const double* g, double* y) {
-  if (threadIdx.x != 0) return;
-  const int k = st->j;
+  extern __shared__ double hs[];   // k x k, column-major
+  __shared__ double rhs[130];
+  const int k = st->j, lane = threadIdx.x;
+  for (int c = 0; c < k; ++c)
+    for (int i = lane; i <= c; i += 32) hs[c * k + i] = H[(int64_t)c * ldh + i];
+  for (int i = lane; i < k; i += 32) rhs[i] = g[i];
+  __syncwarp();
   for (int i = k - 1; i >= 0; --i) {
-    double t = g[i];
-    for (int c = i + 1; c < k; ++c) t -= H[(int64_t)c * ldh + i] * y[c];
-    y[i] = t / H[(int64_t)i * ldh + i];
+    const double yi = rhs[i] / hs[i * k + i];
+    __syncwarp();
+    for (int l = lane; l < i; l += 32) rhs[l] -= hs[i * k + l] * yi;
+    if (lane == 0) y[i] = yi;
+    __syncwarp();
   }
 }
 
@@ -675,14 +1127,19 @@ cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, doub
   gm_init_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, st, g);
   return cudaGetLastError();
 }
-cudaError_t launch_gm_mdot(const double* V, int64_t ld, const double* w, int64_t len, const GmState* st,
-                           int maxc, double* Dp, int nblk, cudaStream_t s) {
-  gm_mdot_kernel<<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp);
+template <typename TAZ>
+cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
+                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m) {
+  gm_mdot_kernel<TAZ><<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp, az, m);
   return cudaGetLastError();
 }
+template cudaError_t launch_gm_mdot<float>(const double*, int64_t, double*, int64_t, const GmState*, int,
+                                           double*, int, cudaStream_t, const float*, int64_t);
+template cudaError_t launch_gm_mdot<double>(const double*, int64_t, double*, int64_t, const GmState*, int,
+                                            double*, int, cudaStream_t, const double*, int64_t);
 cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
                            int ldh, cudaStream_t s) {
-  gm_hsum_kernel<<<1, 128, 0, s>>>(Dp, nblk, maxc, st, h, H, ldh);
+  gm_hsum_kernel<<<1, dim3(32, 32), 0, s>>>(Dp, nblk, maxc, st, h, H, ldh);
   return cudaGetLastError();
 }
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
@@ -696,13 +1153,19 @@ cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, do
   return cudaGetLastError();
 }
 cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
-                             int nblk, cudaStream_t s) {
-  gm_newcol_kernel<<<nblk, 256, 0, s>>>(w, len, st, V, ld);
+                             float* v32, int64_t m, int nblk, cudaStream_t s) {
+  gm_newcol_kernel<<<nblk, 256, 0, s>>>(w, len, st, V, ld, v32, m);
   return cudaGetLastError();
 }
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
                             cudaStream_t s) {
-  gm_solve_kernel<<<1, 32, 0, s>>>(st, H, ldh, g, y);
+  const size_t smem = (size_t)(ldh - 1) * (ldh - 1) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gm_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  gm_solve_kernel<<<1, 32, smem, s>>>(st, H, ldh, g, y);
   return cudaGetLastError();
 }
 template <typename TB>
@@ -744,14 +1207,18 @@ cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n
 }
 
 // V[:, 0] *= inv_h (after gm_init)
-__global__ void gm_scale0_kernel(double* V0, int64_t len, const GmState* st) {
+__global__ void gm_scale0_kernel(double* V0, int64_t len, const GmState* st, float* v32, int64_t m) {
   const double s = st->inv_h;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x)
-    V0[i] *= s;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = V0[i] * s;
+    V0[i] = v;
+    if (v32 && i < m) v32[i] = (float)v;
+  }
 }
-cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, int nblk, cudaStream_t s) {
-  gm_scale0_kernel<<<nblk, 256, 0, s>>>(V0, len, st);
+cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
+                             int nblk, cudaStream_t s) {
+  gm_scale0_kernel<<<nblk, 256, 0, s>>>(V0, len, st, v32, m);
   return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t 
     case FMT_F16: omega_kernel<FMT_F16><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
     case FMT_BF16: omega_kernel<FMT_BF16><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
     case FMT_E4M3: omega_kernel<FMT_E4M3><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
+    case FMT_BF16X3: omega_kernel<FMT_BF16><<<blocks, threads, 0, st>>>(s, j0, cols, k0, k1, out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -133,7 +134,7 @@ template <int FMT>
 __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
                                       const double* __restrict__ b, int64_t m, int64_t n,
                                       const int* __restrict__ kexp, void* __restrict__ Bt,
-                                      int64_t ldb) {
+                                      int64_t ldb, int64_t plane_rows) {
   __shared__ double tile[32][33];
   const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += 8) {
@@ -152,6 +153,16 @@ __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
       const double v = ldexp(tile[threadIdx.x][r], kexp[c]);
       if constexpr (FMT == FMT_F32) {
         reinterpret_cast<float*>(Bt)[c * ldb + j] = __double2float_rn(v);
+      } else if constexpr (FMT == FMT_BF16X3) {
+        // three BF16 terms hi + lo + lo2 (differences exact in FP64), one plane each
+        uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
+        const uint32_t hi = round_f64<FMT_BF16>(v);
+        const double r1 = v - bits_to_double<FMT_BF16>(hi);
+        const uint32_t lo = round_f64<FMT_BF16>(r1);
+        const uint32_t lo2 = round_f64<FMT_BF16>(r1 - bits_to_double<FMT_BF16>(lo));
+        P[c * ldb + j] = (uint16_t)hi;
+        P[(plane_rows + c) * ldb + j] = (uint16_t)lo;
+        P[(2 * plane_rows + c) * ldb + j] = (uint16_t)lo2;
       } else if constexpr (FMT == FMT_E4M3) {
         reinterpret_cast<uint8_t*>(Bt)[c * ldb + j] = (uint8_t)round_f64<FMT>(v);
       } else {
@@ -165,18 +176,23 @@ cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const d
                                   int64_t n, const int* kexp, void* Bt, int64_t ldb,
                                   int64_t nrows_pad, cudaStream_t st) {
   const int esz = (fmt == FMT_E4M3) ? 1 : (fmt == FMT_F32 ? 4 : 2);
+  const int planes = (fmt == FMT_BF16X3) ? 3 : 1;
   if (nrows_pad > n + 1) {
-    cudaError_t e = cudaMemsetAsync(static_cast<uint8_t*>(Bt) + (size_t)(n + 1) * ldb * esz, 0,
-                                    (size_t)(nrows_pad - n - 1) * ldb * esz, st);
-    if (e != cudaSuccess) return e;
+    for (int pl = 0; pl < planes; ++pl) {
+      cudaError_t e = cudaMemsetAsync(
+          static_cast<uint8_t*>(Bt) + ((size_t)pl * nrows_pad + (size_t)(n + 1)) * ldb * esz, 0,
+          (size_t)(nrows_pad - n - 1) * ldb * esz, st);
+      if (e != cudaSuccess) return e;
+    }
   }
   dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 1 + 31) / 32));
   dim3 block(32, 8);
   switch (fmt) {
-    case FMT_F16: cast_transpose_kernel<FMT_F16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
-    case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
-    case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
-    case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb); break;
+    case FMT_F16: cast_transpose_kernel<FMT_F16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
+    case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
+    case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
+    case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
+    case FMT_BF16X3: cast_transpose_kernel<FMT_BF16X3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -184,29 +200,64 @@ cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const d
 
 // ============================================================ tcgen05 sketch
 constexpr int kSkGenWarps = 16;
+constexpr int kSkGenThreads = kSkGenWarps * 32;
 constexpr int kSkThreads = (2 + kSkGenWarps) * 32;
-constexpr uint32_t kSkSBytes = 128u * 128u;  // one 128 x 128-byte sketch tile
+constexpr int kSkQMax = 256;                 // FP64 fallbacks queued per stage
 
 struct SketchTcArgs {
   int64_t s, m, ncols, kchunk, s_pad;
-  int bn, nsub, tmem_cols;
+  int bn, nsub, tmem_cols, rows_per_plane;
   uint32_t k0, k1;
   float* partial;
   int* err;
 };
 
-template <int FMT, int STAGES>
+__device__ __forceinline__ void gen_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kSkGenThreads) : "memory");
+}
+
+// Smem descriptor for a K-major operand whose rows are ROWB bytes (128: 128-byte
+// swizzle; 64: 64-byte swizzle), 8-row core groups 8 * ROWB bytes apart.
+template <int ROWB>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)((8u * ROWB) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(ROWB == 128 ? 2 : 4) << 61;
+  return d;
+}
+
+// Byte offset of 16-byte chunk kc of row `row` in a swizzled K-major tile.
+template <int ROWB>
+__device__ __forceinline__ uint32_t swz_chunk(int row, int kc) {
+  const int sw = (ROWB == 128) ? (row & 7) : ((row >> 1) & 3);
+  return (uint32_t)(row * ROWB + ((kc ^ sw) << 4));
+}
+
+// Y partial = fl_s(G)[128 rows] x (sum over NT planes of Bt)[bn columns] over one split of m.
+template <int FMT, int STAGES, int ROWB, int NT>
 __global__ void __launch_bounds__(kSkThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap tmB, const SketchTcArgs a) {
-  constexpr int EB = (FMT == FMT_E4M3) ? 1 : 2;   // bytes per element
-  constexpr int BK = 128 / EB;                    // K elements per stage (one 128-byte row)
-  constexpr int EPC = 16 / EB;                    // elements per 16-byte chunk
+  constexpr int GF = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;   // format of the sketch operand
+  constexpr int EB = (GF == FMT_E4M3) ? 1 : 2;                // bytes per element
+  constexpr int BK = ROWB / EB;                               // K elements per stage
+  constexpr int EPC = 16 / EB;                                // elements per 16-byte chunk
+  constexpr int CPR = ROWB / 16;                              // chunks per row
+  constexpr int NCHUNK = 128 * CPR;                           // chunks per sketch tile
+  constexpr int PPC = EPC / 2;                                // (a, b) pairs per chunk
+  constexpr uint32_t S_BYTES = 128u * ROWB;
+  constexpr int KSLICES = ROWB / 32;                          // MMA K slices (32 bytes) per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  const uint32_t stage_bytes = kSkSBytes + (uint32_t)a.bn * 128u;
+  const uint32_t b_bytes = (uint32_t)a.bn * ROWB;              // one plane of Bt per stage
+  const uint32_t stage_bytes = S_BYTES + NT * b_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint32_t* qcnt = tslot + 4;                                 // [STAGES]
+  uint32_t* qbuf = qcnt + 4;                                  // [STAGES][kSkQMax][3]
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t done_bar = smem_u32(bars + 2 * STAGES);
 
@@ -221,6 +272,7 @@ __global__ void __launch_bounds__(kSkThreads, 1)
     for (int st = 0; st < STAGES; ++st) {
       mbar_init(full0 + 8 * st, kSkGenWarps + 1);
       mbar_init(empty0 + 8 * st, 1);
+      qcnt[st] = 0;
     }
     mbar_init(done_bar, 1);
     fence_barrier_init();
@@ -235,42 +287,47 @@ __global__ void __launch_bounds__(kSkThreads, 1)
   const uint32_t tmem_base = *tslot;
 
   if (warp == 0) {
-    // ---------------- TMA producer: Bt tiles [chunk rows x 128 bytes] per N-chunk
+    // ---------------- TMA producer: NT planes x nsub boxes of [chunk rows x ROWB bytes]
     if (lane == 0) {
       prefetch_tmap(&tmB);
       for (int ks = 0; ks < nk; ++ks) {
         const int st = ks % STAGES;
         const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
         if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
-        mbar_arrive_expect_tx(full0 + 8 * st, (uint32_t)a.bn * 128u);
-        const uint32_t sb = smem_u32(smem + st * stage_bytes + kSkSBytes);
+        mbar_arrive_expect_tx(full0 + 8 * st, (uint32_t)NT * b_bytes);
+        const uint32_t sb = smem_u32(smem + st * stage_bytes + S_BYTES);
         const int32_t kx = (int32_t)(k_begin + (int64_t)ks * BK);
-        for (int c = 0; c < a.nsub; ++c)
-          tma_load_2d(sb + (uint32_t)(c * chunk * 128), &tmB, kx, (int32_t)(ng * a.bn + c * chunk),
-                      full0 + 8 * st);
+        for (int t = 0; t < NT; ++t)
+          for (int c = 0; c < a.nsub; ++c)
+            tma_load_2d(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB), &tmB, kx,
+                        (int32_t)(t * a.rows_per_plane + ng * a.bn + c * chunk), full0 + 8 * st);
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(FMT == FMT_BF16 ? 1u : 0u, 128u, (uint32_t)chunk);
+      const uint32_t idesc = make_idesc(GF == FMT_BF16 ? 1u : 0u, 128u, (uint32_t)chunk);
       for (int ks = 0; ks < nk; ++ks) {
         const int st = ks % STAGES;
         const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
         if (!mbar_wait(full0 + 8 * st, ph, a.err, DEV_TIMEOUT_FULL)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + st * stage_bytes);
-        const uint32_t sb = sa + kSkSBytes;
+        const uint32_t sb = sa + S_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {  // 4 x 32-byte K slices per 128-byte row
-          const uint64_t ad = sw128_desc(sa + kk * 32);
+        for (int kk = 0; kk < KSLICES; ++kk) {
+          const uint64_t ad = kmajor_desc<ROWB>(sa + kk * 32);
           for (int c = 0; c < a.nsub; ++c) {
-            const uint64_t bd = sw128_desc(sb + (uint32_t)(c * chunk * 128) + kk * 32);
-            const uint32_t acc = (ks | kk) != 0 ? 1u : 0u;
-            if constexpr (FMT == FMT_E4M3)
-              mma_f8(tmem_base + (uint32_t)(c * chunk), ad, bd, idesc, acc);
-            else
-              mma_f16(tmem_base + (uint32_t)(c * chunk), ad, bd, idesc, acc);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+              const uint64_t bd =
+                  kmajor_desc<ROWB>(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB) + kk * 32);
+              const uint32_t acc = (ks | kk | t) != 0 ? 1u : 0u;
+              if constexpr (GF == FMT_E4M3)
+                mma_f8(tmem_base + (uint32_t)(c * chunk), ad, bd, idesc, acc);
+              else
+                mma_f16(tmem_base + (uint32_t)(c * chunk), ad, bd, idesc, acc);
+            }
           }
         }
         tc_commit(empty0 + 8 * st);
@@ -285,35 +342,61 @@ __global__ void __launch_bounds__(kSkThreads, 1)
       const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
       if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
       uint8_t* S = smem + st * stage_bytes;
+      uint32_t* qb = qbuf + st * (kSkQMax * 3);
       const int64_t kbase = k_begin + (int64_t)ks * BK;
-      for (int c = g; c < 1024; c += kSkGenWarps * 32) {
-        const int row = c >> 3, kc = c & 7;
+      for (int c = g; c < NCHUNK; c += kSkGenThreads) {
+        const int row = c / CPR, kc = c % CPR;
         const uint32_t i = (uint32_t)(mt * 128 + row);
         const uint64_t q0 = (uint64_t)(kbase + kc * EPC) >> 2;
         uint32_t w[4];
-        if constexpr (EB == 2) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint4 x = philox4x32_10(gauss_counter(q0 + h, i), a.k0, a.k1);
-            uint32_t e0, o0, e1, o1;
-            gauss_pair_bits<FMT>(x.x, x.y, e0, o0);
-            gauss_pair_bits<FMT>(x.z, x.w, e1, o1);
+        for (int h = 0; h < EPC / 4; ++h) {
+          const uint4 x = philox4x32_10(gauss_counter(q0 + h, i), a.k0, a.k1);
+          uint32_t e0, o0, e1, o1;
+          const bool ok0 = gauss_pair_fast<GF>(x.x, x.y, e0, o0);
+          const bool ok1 = gauss_pair_fast<GF>(x.z, x.w, e1, o1);
+          if (!ok0 || !ok1) {
+#pragma unroll
+            for (int p2 = 0; p2 < 2; ++p2) {
+              if (p2 == 0 ? ok0 : ok1) continue;
+              const uint32_t pa = p2 == 0 ? x.x : x.z, pb = p2 == 0 ? x.y : x.w;
+              const uint32_t slot = atomicAdd(qcnt + st, 1u);
+              if (slot < (uint32_t)kSkQMax) {
+                qb[slot * 3 + 0] = ((uint32_t)row << 8) | ((uint32_t)kc << 4) | (uint32_t)(2 * h + p2);
+                qb[slot * 3 + 1] = pa;
+                qb[slot * 3 + 2] = pb;
+              } else if (p2 == 0) {
+                gauss_pair_slow<GF>(pa, pb, e0, o0);   // queue full: resolve in place
+              } else {
+                gauss_pair_slow<GF>(pa, pb, e1, o1);
+              }
+            }
+          }
+          if constexpr (EB == 2) {
             w[2 * h] = e0 | (o0 << 16);
             w[2 * h + 1] = e1 | (o1 << 16);
-          }
-        } else {
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const uint4 x = philox4x32_10(gauss_counter(q0 + h, i), a.k0, a.k1);
-            uint32_t e0, o0, e1, o1;
-            gauss_pair_bits<FMT>(x.x, x.y, e0, o0);
-            gauss_pair_bits<FMT>(x.z, x.w, e1, o1);
+          } else {
             w[h] = e0 | (o0 << 8) | (e1 << 16) | (o1 << 24);
           }
         }
-        *reinterpret_cast<uint4*>(S + (row >> 3) * 1024 + (row & 7) * 128 + ((kc ^ (row & 7)) << 4)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(S + swz_chunk<ROWB>(row, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
+      gen_barrier();
+      // FP64 fallbacks of this stage, spread over all generator threads
+      const uint32_t nq = min(qcnt[st], (uint32_t)kSkQMax);
+      for (uint32_t qi = g; qi < nq; qi += kSkGenThreads) {
+        const uint32_t pos = qb[qi * 3];
+        uint32_t be, bo;
+        gauss_pair_slow<GF>(qb[qi * 3 + 1], qb[qi * 3 + 2], be, bo);
+        const int row = (int)(pos >> 8), kc = (int)((pos >> 4) & 15), pi = (int)(pos & 15);
+        uint8_t* cp = S + swz_chunk<ROWB>(row, kc);
+        if constexpr (EB == 2)
+          *reinterpret_cast<uint32_t*>(cp + 4 * pi) = be | (bo << 16);
+        else
+          *reinterpret_cast<uint16_t*>(cp + 2 * pi) = (uint16_t)(be | (bo << 8));
+      }
+      gen_barrier();
+      if (g == 0) qcnt[st] = 0;
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(full0 + 8 * st);
@@ -351,9 +434,11 @@ __global__ void __launch_bounds__(kSkThreads, 1)
 static int round_up_int(int64_t v, int64_t q) { return (int)(((v + q - 1) / q) * q); }
 
 bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p) {
-  if (fmt != FMT_F16 && fmt != FMT_BF16 && fmt != FMT_E4M3) return false;
+  if (fmt != FMT_F16 && fmt != FMT_BF16 && fmt != FMT_E4M3 && fmt != FMT_BF16X3) return false;
   const int EB = (fmt == FMT_E4M3) ? 1 : 2;
-  const int BK = 128 / EB;
+  p->nt = (fmt == FMT_BF16X3) ? 3 : 1;
+  p->rowb = (p->nt == 3) ? 64 : 128;
+  const int BK = p->rowb / EB;
   p->fmt = fmt;
   p->s = s;
   p->m = m;
@@ -368,8 +453,9 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
   }
   p->bn = bn;
   p->mtiles = (int)((s + 127) / 128);
-  p->stages = (bn > 256) ? 2 : 4;
-  p->smem = 1024 + (size_t)p->stages * (kSkSBytes + (size_t)bn * 128) + 256;
+  const size_t stage = (size_t)128 * p->rowb + (size_t)p->nt * bn * p->rowb;
+  p->stages = (4 * stage + 1024 + 256 + 16 + 4 * kSkQMax * 12 <= 232448) ? 4 : 2;
+  p->smem = 1024 + (size_t)p->stages * stage + 256 + 16 + (size_t)p->stages * kSkQMax * 12;
   if (p->smem > 232448) return false;
   const int64_t base = (int64_t)p->mtiles * p->ngroups;
   const int64_t ksteps = (m + BK - 1) / BK;
@@ -384,7 +470,7 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
 }
 
 bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
-                    int box_rows) {
+                    int box_rows, int rowb) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -398,19 +484,20 @@ bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int6
   const int EB = (fmt == FMT_E4M3) ? 1 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ldb * EB)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / EB), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(rowb / EB), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(tm, EB == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
                   const_cast<void*>(Bt), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int FMT, int STAGES>
+template <int FMT, int STAGES, int ROWB, int NT>
 static cudaError_t launch_tc_inst(const SketchPlan& p, const CUtensorMap& tm, const SketchTcArgs& a,
                                   cudaStream_t st) {
-  auto kern = sketch_tc_kernel<FMT, STAGES>;
+  auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
@@ -428,6 +515,7 @@ cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_
   a.s_pad = p.s_pad;
   a.bn = p.bn;
   a.nsub = p.nsub;
+  a.rows_per_plane = p.ngroups * p.bn;
   int tc = 32;
   while (tc < p.bn) tc <<= 1;
   a.tmem_cols = tc;
@@ -435,18 +523,16 @@ cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_
   a.k1 = (uint32_t)(seed >> 32);
   a.partial = partial;
   a.err = err;
-  if (p.stages == 2) {
-    switch (p.fmt) {
-      case FMT_F16: return launch_tc_inst<FMT_F16, 2>(p, tm, a, st);
-      case FMT_BF16: return launch_tc_inst<FMT_BF16, 2>(p, tm, a, st);
-      case FMT_E4M3: return launch_tc_inst<FMT_E4M3, 2>(p, tm, a, st);
-    }
-  } else {
-    switch (p.fmt) {
-      case FMT_F16: return launch_tc_inst<FMT_F16, 4>(p, tm, a, st);
-      case FMT_BF16: return launch_tc_inst<FMT_BF16, 4>(p, tm, a, st);
-      case FMT_E4M3: return launch_tc_inst<FMT_E4M3, 4>(p, tm, a, st);
-    }
+  const bool four = p.stages == 4;
+  switch (p.fmt) {
+    case FMT_F16: return four ? launch_tc_inst<FMT_F16, 4, 128, 1>(p, tm, a, st)
+                              : launch_tc_inst<FMT_F16, 2, 128, 1>(p, tm, a, st);
+    case FMT_BF16: return four ? launch_tc_inst<FMT_BF16, 4, 128, 1>(p, tm, a, st)
+                               : launch_tc_inst<FMT_BF16, 2, 128, 1>(p, tm, a, st);
+    case FMT_E4M3: return four ? launch_tc_inst<FMT_E4M3, 4, 128, 1>(p, tm, a, st)
+                               : launch_tc_inst<FMT_E4M3, 2, 128, 1>(p, tm, a, st);
+    case FMT_BF16X3: return four ? launch_tc_inst<FMT_BF16X3, 4, 64, 3>(p, tm, a, st)
+                                 : launch_tc_inst<FMT_BF16X3, 2, 64, 3>(p, tm, a, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -20,7 +20,8 @@ cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int
 cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols, int t, int* kexp,
                               cudaStream_t st);
 // Pass 2 over A: Bt[c][j] = fl_s(2^k_c [A | b][j][c]) (K-major operand), rows c in
-// [n+1, nrows_pad) zeroed.  fmt in {F16, BF16, E4M3, F32}; element size 2, 2, 1, 4.
+// [n+1, nrows_pad) zeroed.  fmt in {F16, BF16, E4M3, F32, BF16X3}; element size
+// 2, 2, 1, 4, 2.  BF16X3 writes three planes of nrows_pad rows (hi, lo, lo2).
 cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
                                   int64_t n, const int* kexp, void* Bt, int64_t ldb,
                                   int64_t nrows_pad, cudaStream_t st);
@@ -36,6 +37,8 @@ struct SketchPlan {
   int64_t kchunk;      // K extent per split (multiple of the K step)
   int64_t s_pad;       // rows of the partial buffers
   int stages;
+  int nt;              // B planes (1, or 3 for the split-term BF16 sketch)
+  int rowb;            // bytes per K-major row of a stage (128 or 64)
   size_t smem;
 };
 
@@ -43,7 +46,7 @@ struct SketchPlan {
 bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p);
 // Encodes the TMA descriptor of the K-major operand Bt (rows x m, row stride ldb elements).
 bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
-                    int box_rows);
+                    int box_rows, int rowb);
 cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_t seed,
                              float* partial, int* err, cudaStream_t st);
 // CUDA-core sketch in FP64 (fmt F64) or FP32 (fmt F32) from the FP64 data.
@@ -63,16 +66,35 @@ cudaError_t launch_qr(bool fp64, const double* Y, int64_t s, int64_t n, void* wo
                       unsigned* bar, double* R, double* c, int* err, int num_sms, cudaStream_t st);
 
 // ---------------------------------------------------------------- TRSV
-// x = R^-1 y (upper, col-major U) or x = L^-1 y with L = R^T stored col-major.
-// T in {float, double}; TIN/TOUT any of float/double.  Skips when *done != 0.
-template <typename T, typename TIN, typename TOUT>
-cudaError_t launch_trsv(bool upper, const T* M, int64_t n, const TIN* y, double yscale, TOUT* x,
-                        const int* done, cudaStream_t st);
+// R (upper) and L = R^T, both column-major n x n with leading dimension ld
+// (n rounded up to 16 bytes; padding rows are zero), with the inverses of their
+// 32 x 32 diagonal blocks (DU for R, DL for L; 1024 entries per block).
+template <typename T>
+struct Tri {
+  const T* R;
+  const T* L;
+  const T* DU;
+  const T* DL;
+  int64_t n;
+  int64_t ld;
+};
+inline int64_t tri_ld(int64_t n, int elem_bytes) {
+  const int64_t q = 16 / elem_bytes;
+  return (n + q - 1) / q * q;
+}
 
-// Converts R (FP64, col-major) into FP32/FP64 copies of R and R^T; writes the
-// diagonal ratio max|r_ii| / min|r_ii| to *kappa_est.
-cudaError_t launch_prepare_r(const double* R, int64_t n, float* R32, float* L32, double* R64,
-                             double* L64, double* kappa_est, cudaStream_t st);
+// x = R^-1 y (upper) or x = R^-T y (lower), n <= 1024.  T in {float, double};
+// TIN/TOUT any of float/double.  Skips when *done != 0.  With jp, y and x are
+// offset on the device by (*jp) * ys and (*jp) * xstr elements.
+template <typename T, typename TIN, typename TOUT>
+cudaError_t launch_trsv(bool upper, const Tri<T>& f, const TIN* y, double yscale, TOUT* x,
+                        const int* done, cudaStream_t st, const int* jp = nullptr, int64_t ys = 0,
+                        int64_t xstr = 0);
+
+// Converts R (FP64, col-major) into the FP32 and FP64 factors (R, R^T and the
+// diagonal-block inverses); writes max|r_ii| / min|r_ii| to *kappa_est.
+cudaError_t launch_prepare_r(const double* R, int64_t n, Tri<float>* f32, Tri<double>* f64,
+                             double* kappa_est, cudaStream_t st);
 
 // ---------------------------------------------------------------- passes
 int pass_blocks(int num_sms);
@@ -81,11 +103,13 @@ int pass_blocks(int num_sms);
 cudaError_t launch_pass_lsqr(const float* A32, int64_t lda32, int64_t m, int64_t n, const float* t,
                              const float* u_in, const double* cu_ptr, double cu_mul, float* u_out,
                              float* Pblk, double* sq, int nblk, const int* done, cudaStream_t st);
-// FGMRES pass: w_top_i = vs v_i + (A z)_i ; Pblk = block sums of (vs v_i) A_i.
+// FGMRES pass: az = A z ; Pblk = block sums of v_i A_i (rows of A streamed with
+// cp.async.bulk).  With jp, z and v are offset on the device by (*jp) * zs and
+// (*jp) * vstr.  Requires A 16-byte aligned with 16-byte rows.
 template <typename TA>
 cudaError_t launch_pass_fgm(const TA* A, int64_t lda, int64_t m, int64_t n, const TA* z,
-                            const double* v, const double* vs_ptr, double* wtop, TA* Pblk, int nblk,
-                            const int* done, cudaStream_t st);
+                            const TA* v, TA* az, TA* Pblk, int nblk, const int* done, cudaStream_t st,
+                            const int* jp, int64_t zs, int64_t vstr, int* err);
 // Residual pass (FP64): f_i = b_i - r_i - (A x)_i ; Pblk = block sums of -r_i A_i.
 cudaError_t launch_pass_res(const double* A, int64_t lda, int64_t m, int64_t n, const double* x,
                             const double* r, const double* b, double* f, double* Pblk, int nblk,

@@ -11,7 +11,7 @@ CASES = [(64, 0, 4096, 0), (33, 5, 1001, 12345), (8, 2 ** 32 - 6, 64, 2 ** 40 + 
          (5, 2 ** 34 + 1, 17, 7), (1, 3, 1, 99)]
 
 
-@pytest.mark.parametrize("fmt", ["f16", "bf16", "e4m3", "f32", "f64"])
+@pytest.mark.parametrize("fmt", ["f16", "bf16", "e4m3", "bf16x3", "f32", "f64"])
 def test_omega_bit_exact(lsq, handle, fmt):
     for s, j0, cols, seed in CASES:
         out = torch.full((s * cols,), float("nan"), dtype=torch.float64, device="cuda")

@@ -9,7 +9,7 @@ from oracle import rng, sketch
 
 pytestmark = pytest.mark.gpu
 
-FMTS = ["f16", "bf16", "e4m3", "f32", "f64"]
+FMTS = ["f16", "bf16", "e4m3", "bf16x3", "f32", "f64"]
 
 
 def gpu_sketch(lsq, handle, A, b, s, fmt, seed, **opts):
@@ -68,14 +68,15 @@ def test_sketch_full_size_sampled_entries(lsq, handle):
     """The bench workload (m=1e5, n=500, s=4n, BF16 and FP16): sampled entries vs the oracle."""
     m, n, s = 100000, 500, 2000
     P = randsvd_problem(m, n, 1e6, rho=1e-3, seed=1)
-    for fmt in ("bf16", "f16"):
+    for fmt in ("bf16", "f16", "bf16x3"):
         got = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 0)
         As, bs, kA, kb = sketch.cast_scaled(P.A, P.b, fmt)
         Ab = np.column_stack([As, bs])
         k = np.concatenate([kA, [kb]])
         r = np.random.default_rng(5)
         for i in r.choice(s, 6, replace=False):
-            g = rng.round_to_format(rng.gaussian_block(int(i), int(i) + 1, 0, m, 0), fmt)
+            g = rng.round_to_format(rng.gaussian_block(int(i), int(i) + 1, 0, m, 0),
+                                    rng.OPERAND_FORMAT[fmt])
             row = (g @ Ab)[0] / np.sqrt(s)
             ref = np.ldexp(row, -k)
             mag = np.ldexp((np.abs(g) @ np.abs(Ab))[0] / np.sqrt(s), -k)

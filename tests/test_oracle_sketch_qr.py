@@ -146,3 +146,26 @@ def test_low_precision_sketch_degrades_as_paper_predicts():
     # Corollary bound of Sec. 3.4: ||(A R_s^-1)^+|| <= (1 + sqrt(n) u_s kappa) ||Omega||
     Om = _explicit_omega(400, 1000, 1, "bf16")
     assert out["bf16"] <= (1 + np.sqrt(100) * 2.0 ** -8 * 1e6) * np.linalg.norm(Om, 2)
+
+
+def test_split3_carries_single_precision():
+    r = np.random.default_rng(11)
+    x = r.standard_normal(20000) * np.exp(r.uniform(-20, 20, 20000))
+    hi, lo, lo2 = rng.split3(x, "bf16")
+    for t in (hi, lo, lo2):
+        assert np.array_equal(rng.round_to_format(t, "bf16"), t)      # each term is a BF16 value
+    assert np.all(np.abs(x - (hi + lo + lo2)) <= 2.0 ** -24 * np.abs(x))
+    assert np.all(np.abs(lo) <= 2.0 ** -8 * np.abs(hi) + 1e-300)
+
+
+def test_split_sketch_restores_the_good_regime():
+    """Sec. 3.4: with the single-precision split sketch kappa(A R^-1) stays ~3 at kappa(A) = 1e6."""
+    P = paper_problem(1e6, seed=2)
+    Y = sketch.sketch(P.A, P.b, 400, 2, "bf16x3")
+    R, _ = qr.householder_qr(Y, 100)
+    sv = np.linalg.svd(P.A @ np.linalg.inv(R), compute_uv=False)
+    assert sv[0] / sv[-1] < 1.2 * theory.mp_limits(100, 400)[2]
+    Yb = sketch.sketch(P.A, P.b, 400, 2, "bf16")
+    Rb, _ = qr.householder_qr(Yb, 100)
+    svb = np.linalg.svd(P.A @ np.linalg.inv(Rb), compute_uv=False)
+    assert svb[0] / svb[-1] > 10 * sv[0] / sv[-1]
