@@ -96,6 +96,9 @@ typedef struct lsq_opts {
                              1: the first test only */
   int32_t timing;         /* 1: time every sketch GEMM and pass launch with CUDA events
                              on the handle's stream (info->kern_ms / kern_launches) */
+  int32_t no_graph;       /* 1: launch LSQR / FGMRES iteration batches directly instead of
+                             replaying cached CUDA graphs (same arithmetic) */
+  int32_t reserved1;
   double gmres_tol;       /* FGMRES relative-residual tolerance; 0 -> tol */
   double kappa_hint;      /* kappa(A) for the escalation rule; 0 -> estimate from R */
   const double* Y_in;     /* optional device sketch, s x (n+1) column-major (ld = s):
@@ -203,6 +206,30 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
                     int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
                     double tol, uint64_t seed, const lsq_opts* opts, double* x, double* r,
                     lsq_info* info);
+
+/* One problem of a batch (all pointers are device pointers owned by the caller). */
+typedef struct lsq_problem {
+  const double* A;   /* m x n row-major FP64, row stride lda (0 -> n) */
+  const double* b;   /* m */
+  int64_t m, n, s, lda;
+  uint64_t seed;     /* key of the problem's sketch matrix */
+  double* x;         /* out: n */
+  double* r;         /* out: m (may be NULL) */
+} lsq_problem;
+
+/*
+ * lsq_lsir_batched -- lsq_lsir on nprob independent problems of uneven sizes
+ * (probs is a HOST array of descriptors).  The problems run concurrently on
+ * up to four internal streams (one worker thread and one workspace per
+ * stream, created on first use and owned by the handle); problems with
+ * m * n < 2^26 launch their iteration batches directly instead of capturing
+ * CUDA graphs.  Each problem's result equals that of lsq_lsir on it alone.  statuses[i] and infos[i] (either
+ * may be NULL) receive each problem's outcome.  Returns LSQ_OK if every problem
+ * converged, LSQ_NOT_CONVERGED if some did not, or the first error status.
+ */
+lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* probs, lsq_prec u_s,
+                            lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol,
+                            const lsq_opts* opts, int32_t* statuses, lsq_info* infos);
 
 /*
  * lsq_omega -- the sketch operand fl_s(G)[i, j] for i in [0, s) and

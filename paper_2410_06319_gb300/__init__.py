@@ -11,6 +11,6 @@ kernels do all the work.  Importing this module fails loudly if the CUDA
 library has not been built; there is no fallback.
 """
 from ._lib import (  # noqa: F401
-    KERNELS, PREC, STATUS, Handle, Info, LsqError, Opts, lib, lsq_lsir, lsq_lsqr, lsq_omega, lsq_qr_r,
-    lsq_sketch, library_path, declared_functions,
+    KERNELS, PREC, STATUS, Handle, Info, LsqError, Opts, Problem, lib, lsq_lsir, lsq_lsir_batched,
+    lsq_lsqr, lsq_omega, lsq_qr_r, lsq_sketch, library_path, declared_functions,
 )

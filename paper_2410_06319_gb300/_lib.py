@@ -34,6 +34,7 @@ class Opts(ctypes.Structure):
                 ("ir_maxit", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("no_escalate", ctypes.c_int32), ("no_colscale", ctypes.c_int32),
                 ("ir_stop", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("no_graph", ctypes.c_int32), ("reserved1", ctypes.c_int32),
                 ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
                 ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p)]
 
@@ -64,6 +65,12 @@ class Info(ctypes.Structure):
         return d
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("s", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("x", ctypes.c_void_p), ("r", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _TUPLE = [_P, _P, _P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -82,8 +89,11 @@ lib.lsq_qr_r.argtypes = _TUPLE + [_P, _P]
 lib.lsq_lsqr.argtypes = _TUPLE + [_P, ctypes.POINTER(Info)]
 lib.lsq_lsir.argtypes = _TUPLE + [_P, _P, ctypes.POINTER(Info)]
 lib.lsq_omega.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_uint64, _P]
+lib.lsq_lsir_batched.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
 for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir",
-           "lsq_omega"):
+           "lsq_omega", "lsq_lsir_batched"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -195,6 +205,24 @@ def lsq_lsir(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, x, r, info=N
     info = info if info is not None else Info()
     st = _check(h, lib.lsq_lsir(*args, _ptr(x), _ptr(r), ctypes.byref(info)), "lsq_lsir")
     return st, info
+
+
+def lsq_lsir_batched(h, problems, u_s, u_p, u_w, u_r, tol, opts=None):
+    """problems: list of dicts with A, b, m, n, s, seed, x, r (tensors or pointers), optional lda.
+
+    Returns (aggregate status, per-problem statuses, per-problem Info)."""
+    k = len(problems)
+    arr = (Problem * max(1, k))()
+    for i, pr in enumerate(problems):
+        arr[i] = Problem(_ptr(pr["A"]), _ptr(pr["b"]), pr["m"], pr["n"], pr["s"], pr.get("lda", 0),
+                         int(pr.get("seed", 0)), _ptr(pr["x"]), _ptr(pr.get("r")))
+    sts = (ctypes.c_int32 * max(1, k))()
+    infos = (Info * max(1, k))()
+    o = _opts(opts)
+    st = lib.lsq_lsir_batched(h.ptr, k, arr, _prec(u_s), _prec(u_p), _prec(u_w), _prec(u_r),
+                              float(tol), ctypes.byref(o), sts, infos)
+    _check(h, st, "lsq_lsir_batched")
+    return st, list(sts)[:k], list(infos)[:k]
 
 
 def lsq_omega(h, s, j0, cols, u_s, seed, out):

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <functional>
+#include <thread>
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
@@ -82,6 +84,7 @@ struct lsq_handle {
     cudaEvent_t a, b;
   };
   std::vector<Mark> marks;
+  std::vector<lsq_handle*> workers;    // sub-handles of lsq_lsir_batched (own streams)
 };
 
 namespace {
@@ -423,7 +426,7 @@ void stage_qr(Ctx& c, const double* Y, double* R, double* xs, RCopies* rc) {
     StageTimer t(c.h, ST_QR);
     const bool f64 = (c.up == LSQ_F64);
     void* work = ws(c.h, "qrwork", (size_t)c.s * (c.n + 1) * (f64 ? 8 : 4));
-    double* aux = static_cast<double*>(ws(c.h, "qraux", (2 * c.n + 8) * 8));
+    double* aux = static_cast<double*>(ws(c.h, "qraux", (2 * c.n + 8) * 8 + (32 + 32 * 32) * 8));
     unsigned* bar = static_cast<unsigned*>(ws(c.h, "qrbar", 64));
     double* cvec = static_cast<double*>(ws(c.h, "qrc", c.n * 8));
     L(launch_qr(f64, Y, c.s, c.n, work, aux, bar, R, cvec, c.h->d_err, c.h->num_sms, c.st));
@@ -492,8 +495,9 @@ LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const Tri<W>& tri, const 
     }
   };
   // CUDA events cannot be timed inside graphs: with opts.timing the batch is launched directly
-  CachedGraph* G = c.o.timing ? nullptr
-                              : get_graph(c,
+  CachedGraph* G = (c.o.timing || c.o.no_graph)
+                      ? nullptr
+                      : get_graph(c,
                                           graph_key(sizeof(W) == 4 ? "lsqr32" : "lsqr64",
                                                     {PV(Aw), ldw, m, n, PV(t), PV(u), PV(P), PV(sq),
                                                      PV(sv), PV(v), PV(w), PV(z), PV(dst), PV(tri.R),
@@ -577,18 +581,23 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
       }
       L((launch_colsum<TOP, TOP>(P, c.nblk, n, nullptr, 1.0, sb, dn, c.st)));
       L((launch_trsv<TOP, TOP, double>(false, tri, sb, 1.0, wv + m, dn, c.st)));
-      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
-        L(launch_gm_mdot<TOP>(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st, pass == 0 ? az : nullptr, m));
-        L(launch_gm_hsum(Dp, c.nblk2, maxc, gst, hh, H, ldh, c.st));
-        L(launch_gm_axpy(V, ld, hh, wv, ld, gst, pass == 1 ? sqp : nullptr, c.nblk2, c.st));
-      }
+      // classical Gram-Schmidt; the second pass runs only when the first one lost
+      // more than half of ||w||^2 ("twice is enough")
+      L(launch_gm_mdot<TOP>(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st, az, m));
+      L(launch_gm_hsum(Dp, c.nblk2, maxc, gst, hh, H, ldh, c.st));
+      L(launch_gm_axpy(V, ld, hh, wv, ld, gst, sqp, c.nblk2, c.st));
+      L(launch_gm_reorth_test(sqp, c.nblk2, hh, gst, c.st));
+      L(launch_gm_mdot<TOP>(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st, nullptr, m, true));
+      L(launch_gm_hsum(Dp, c.nblk2, maxc, gst, hh, H, ldh, c.st, true));
+      L(launch_gm_axpy(V, ld, hh, wv, ld, gst, sqp, c.nblk2, c.st, true));
       L(launch_gm_finish(sqp, c.nblk2, gst, H, ldh, cs, sn, g, c.st));
       L(launch_gm_newcol(wv, ld, gst, V, ld, v32, m, c.nblk2, c.st));
     }
   };
   CachedGraph* G =
-      c.o.timing ? nullptr
-                 : get_graph(c,
+      (c.o.timing || c.o.no_graph)
+          ? nullptr
+          : get_graph(c,
                              graph_key(sizeof(TOP) == 4 ? "fgm32" : "fgm64",
                                        {PV(Aop), ldop, m, n, maxit, PV(V), PV(Zb), PV(wv), PV(P), PV(az), PV(v32),
                                         PV(sb), PV(H), PV(cs), PV(sn), PV(g), PV(hh), PV(Dp), PV(sqp),
@@ -860,6 +869,8 @@ lsq_status lsq_create(lsq_handle** out, void* cuda_stream) {
 lsq_status lsq_destroy(lsq_handle* h) {
   if (!h) return LSQ_E_INVAL;
   cudaStreamSynchronize(h->stream);
+  for (auto* w : h->workers) lsq_destroy(w);
+  h->workers.clear();
   for (auto& kv : h->graphs) delete kv.second;
   h->graphs.clear();
   for (auto& kv : h->bufs)
@@ -990,6 +1001,58 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     inf->ir_converged = conv ? 1 : 0;
     return conv ? LSQ_OK : LSQ_NOT_CONVERGED;
   });
+}
+
+lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* probs, lsq_prec u_s,
+                            lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol,
+                            const lsq_opts* opts, int32_t* statuses, lsq_info* infos) {
+  if (!h || nprob < 0 || (nprob > 0 && !probs)) return LSQ_E_INVAL;
+  for (int32_t i = 0; i < nprob; ++i) {   // validate everything before any launch
+    lsq_opts o;
+    if (opts) o = *opts;
+    else std::memset(&o, 0, sizeof(o));
+    o.lda = probs[i].lda;
+    Ctx c = make_ctx(h, probs[i].A, probs[i].b, probs[i].m, probs[i].n, probs[i].s, u_s, u_p, u_w, u_r,
+                     tol, probs[i].seed, &o);
+    if (validate(c, true) != LSQ_OK || !probs[i].x) return LSQ_E_INVAL;
+  }
+  if (nprob == 0) return LSQ_OK;
+  const int nw = std::min<int32_t>(nprob, 4);
+  while ((int)h->workers.size() < nw) {
+    lsq_handle* w = nullptr;
+    const lsq_status st = lsq_create(&w, h->user_stream);
+    if (st != LSQ_OK) return st;
+    h->workers.push_back(w);
+  }
+  std::atomic<int32_t> next{0};
+  std::vector<lsq_status> sts((size_t)nprob, LSQ_OK);
+  auto work = [&](lsq_handle* w) {
+    cudaSetDevice(h->device);
+    for (;;) {
+      const int32_t i = next.fetch_add(1);
+      if (i >= nprob) break;
+      lsq_opts o;
+      if (opts) o = *opts;
+      else std::memset(&o, 0, sizeof(o));
+      o.lda = probs[i].lda;
+      if ((double)probs[i].m * (double)probs[i].n < 67108864.0) o.no_graph = 1;
+      lsq_info local;
+      lsq_info* inf = infos ? &infos[i] : &local;
+      sts[(size_t)i] = lsq_lsir(w, probs[i].A, probs[i].b, probs[i].m, probs[i].n, probs[i].s, u_s, u_p,
+                                u_w, u_r, tol, probs[i].seed, &o, probs[i].x, probs[i].r, inf);
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int k = 1; k < nw; ++k) threads.emplace_back(work, h->workers[(size_t)k]);
+  work(h->workers[0]);
+  for (auto& t : threads) t.join();
+  lsq_status agg = LSQ_OK;
+  for (int32_t i = 0; i < nprob; ++i) {
+    if (statuses) statuses[i] = sts[(size_t)i];
+    if (sts[(size_t)i] < 0 && agg >= 0) agg = sts[(size_t)i];
+    else if (sts[(size_t)i] == LSQ_NOT_CONVERGED && agg == LSQ_OK) agg = LSQ_NOT_CONVERGED;
+  }
+  return agg;
 }
 
 lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_prec u_s, uint64_t seed,

@@ -22,6 +22,8 @@ struct LsqrState {
 struct GmState {
   double beta0, relres, tol, inv_h;
   int j, done, maxit, pad;
+  int reorth;     // 1: the current Arnoldi step needs the second Gram-Schmidt pass
+  int nreorth;    // second passes run so far
 };
 
 template <typename TP>
@@ -56,11 +58,16 @@ cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* 
 // Partial dots of w with V[:, 0..j]; with az, first forms w_top = V[:m, j] + az.
 template <typename TAZ>
 cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
-                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m);
+                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m,
+                           bool second = false);
 cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
-                           int ldh, cudaStream_t s);
+                           int ldh, cudaStream_t s, bool second = false);
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
-                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s);
+                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s,
+                           bool second = false);
+// Second-pass test: reorthogonalise iff ||w'||^2 < (||w'||^2 + ||h||^2) / 2.
+cudaError_t launch_gm_reorth_test(const double* sq_partial, int nblk, const double* h, GmState* st,
+                                  cudaStream_t s);
 cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
                              double* cs, double* sn, double* g, cudaStream_t s);
 cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,

@@ -7,6 +7,8 @@
 //   residual (line 5, u_r):  f = b - r - A x ; P = A^T (-r)
 // P is reduced per CTA (fixed order) and then across CTAs by colsum, so the
 // results are deterministic.
+#include <type_traits>
+
 #include "common.cuh"
 #include "iter.h"
 #include "kernels.h"
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
 //   PM_LSQR: q = A t + cu u ; u_out = q ; P = A^T q ; sq = sum q^2
 //   PM_FGM : az = A z ; P = A^T v            (v_top + az is formed by gm_mdot)
 //   PM_RES : f = b - r - A x ; P = A^T (-r)
-constexpr int kBulkRows = 8;
+constexpr int kBulkRows = 16;
 constexpr int kBulkThreads = (kBulkRows + 1) * 32;
 
 template <typename T>
@@ -296,25 +298,35 @@ __global__ void __launch_bounds__(kBulkThreads, 1) pass_bulk_kernel(BulkArgs<T> 
       }
     }
     const T cu = (MODE == PM_LSQR) ? (T)((p.cu_ptr ? *p.cu_ptr : 1.0) * p.cu_mul) : T(0);
-    // per-row scalars, one stage ahead
-    auto scal = [&](int it, double& s0, double& s1) {
+    // per-row scalars for a window of 32 stages: lane l holds the scalars of stage
+    // base + l; the next window is loaded while the current one is consumed
+    // scalars in the pass precision (no FP64 conversions in the FP32 passes)
+    using S = typename std::conditional<MODE == PM_RES, double, T>::type;
+    auto load_window = [&](int base, S& s0, S& s1) {
+      const int it = base + lane;
       const int64_t row = r0 + (int64_t)it * kBulkRows + warp;
-      s0 = 0.0;
-      s1 = 0.0;
+      s0 = S(0);
+      s1 = S(0);
       if (it < nst && row < r1) {
-        if (MODE == PM_LSQR) s0 = (double)p.uin[row];
-        if (MODE == PM_FGM) s0 = (double)p.v[row];
-        if (MODE == PM_RES) {
+        if constexpr (MODE == PM_LSQR) s0 = p.uin[row];
+        if constexpr (MODE == PM_FGM) s0 = p.v[row];
+        if constexpr (MODE == PM_RES) {
           s0 = p.r[row];
           s1 = p.b[row];
         }
       }
     };
-    double n0, n1;
-    scal(0, n0, n1);
+    S w0, w1, x0n, x1n;
+    load_window(0, w0, w1);
+    load_window(32, x0n, x1n);
     for (int it = 0; it < nst; ++it) {
-      const double c0 = n0, c1s = n1;
-      scal(it + 1, n0, n1);
+      if ((it & 31) == 0 && it > 0) {
+        w0 = x0n;
+        w1 = x1n;
+        load_window(it + 32, x0n, x1n);
+      }
+      const S c0 = __shfl_sync(0xffffffffu, w0, it & 31);
+      const S c1s = (MODE == PM_RES) ? __shfl_sync(0xffffffffu, w1, it & 31) : S(0);
       const int slot = it % p.stages;
       const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
       if (!mbar_wait(full0 + 8 * slot, ph, p.err, DEV_TIMEOUT_FULL)) break;
@@ -954,8 +966,8 @@ __global__ void gm_init_kernel(const double* sq_partial, int nblk, GmState* st, 
 template <typename TAZ>
 __global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, double* __restrict__ w,
                                int64_t len, const GmState* st, int maxc, double* Dp,
-                               const TAZ* __restrict__ az, int64_t m) {
-  if (st->done) return;
+                               const TAZ* __restrict__ az, int64_t m, bool second) {
+  if (st->done || (second && !st->reorth)) return;
   const int ncols = st->j + 1;
   const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(len, r0 + chunk);
@@ -976,8 +988,8 @@ __global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, double*
 
 // h[c] = sum_b Dp[b][c] ; H[c][j] += h[c]   (one 32 x 32 block, fixed order)
 __global__ void gm_hsum_kernel(const double* Dp, int nblk, int maxc, GmState* st, double* h,
-                               double* H, int ldh) {
-  if (st->done) return;
+                               double* H, int ldh, bool second) {
+  if (st->done || (second && !st->reorth)) return;
   __shared__ double part[32][33];
   const int ncols = st->j + 1;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -1001,8 +1013,8 @@ __global__ void gm_hsum_kernel(const double* Dp, int nblk, int maxc, GmState* st
 // w[i] -= sum_c V[c][i] h[c] ; optional partial ||w||^2
 __global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
                                double* __restrict__ w, int64_t len, const GmState* st,
-                               double* sq_partial) {
-  if (st->done) return;
+                               double* sq_partial, bool second) {
+  if (st->done || (second && !st->reorth)) return;
   __shared__ double hs[128];
   __shared__ double red[33];
   const int ncols = st->j + 1;
@@ -1020,6 +1032,28 @@ __global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const d
     s = block_sum_d(s, red);
     if (threadIdx.x == 0) sq_partial[blockIdx.x] = s;
   }
+}
+
+// Kahan's "twice is enough" test after the first Gram-Schmidt pass.
+__global__ void gm_reorth_test_kernel(const double* sq_partial, int nblk, const double* h, GmState* st) {
+  if (st->done) return;
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
+  s = block_sum_d(s, red);
+  double hh = 0.0;
+  for (int c = threadIdx.x; c <= st->j; c += blockDim.x) hh += h[c] * h[c];
+  hh = block_sum_d(hh, red);
+  if (threadIdx.x == 0) {
+    const int need = (s < 0.5 * (s + hh)) ? 1 : 0;
+    st->reorth = need;
+    st->nreorth += need;
+  }
+}
+cudaError_t launch_gm_reorth_test(const double* sq_partial, int nblk, const double* h, GmState* st,
+                                  cudaStream_t s) {
+  gm_reorth_test_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, h, st);
+  return cudaGetLastError();
 }
 
 // h_{j+1,j} = ||w|| ; Givens rotations on column j ; residual estimate ; j++.
@@ -1129,22 +1163,23 @@ cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, doub
 }
 template <typename TAZ>
 cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
-                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m) {
-  gm_mdot_kernel<TAZ><<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp, az, m);
+                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m,
+                           bool second) {
+  gm_mdot_kernel<TAZ><<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp, az, m, second);
   return cudaGetLastError();
 }
 template cudaError_t launch_gm_mdot<float>(const double*, int64_t, double*, int64_t, const GmState*, int,
-                                           double*, int, cudaStream_t, const float*, int64_t);
+                                           double*, int, cudaStream_t, const float*, int64_t, bool);
 template cudaError_t launch_gm_mdot<double>(const double*, int64_t, double*, int64_t, const GmState*, int,
-                                            double*, int, cudaStream_t, const double*, int64_t);
+                                            double*, int, cudaStream_t, const double*, int64_t, bool);
 cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
-                           int ldh, cudaStream_t s) {
-  gm_hsum_kernel<<<1, dim3(32, 32), 0, s>>>(Dp, nblk, maxc, st, h, H, ldh);
+                           int ldh, cudaStream_t s, bool second) {
+  gm_hsum_kernel<<<1, dim3(32, 32), 0, s>>>(Dp, nblk, maxc, st, h, H, ldh, second);
   return cudaGetLastError();
 }
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
-                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s) {
-  gm_axpy_kernel<<<nblk, 256, 0, s>>>(V, ld, h, w, len, st, sq_partial);
+                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second) {
+  gm_axpy_kernel<<<nblk, 256, 0, s>>>(V, ld, h, w, len, st, sq_partial, second);
   return cudaGetLastError();
 }
 cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,

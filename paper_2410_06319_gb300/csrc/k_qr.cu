@@ -9,6 +9,7 @@
 // shared memory, each block updates whole trailing columns (block-wide
 // reductions), the block owning column k+1 also leaves its squared norm for
 // the next step, and a bounded grid barrier separates the steps.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -98,6 +99,179 @@ __global__ void qr_finalize_kernel(const T* __restrict__ W, int64_t s, int64_t n
   }
 }
 
+// ------------------------------------------------------------ blocked variant
+// Panels of NB columns: one CTA factors the panel W[p:s, p:p+kb] in shared
+// memory (column Householder steps with block reductions), leaving the vectors
+// v_j below the diagonal, tau_j = 1 / (alpha (alpha + |x_1|)) and the compact-WY
+// factor T (Q_panel = I - V T V^T, T upper triangular, Schreiber-Van Loan
+// recurrence); then every trailing column y (including the right-hand side) is
+// updated as y -= V (T^T (V^T y)) by a grid of CTAs.  Same reflectors and the
+// same arithmetic order per column as the unblocked kernel, blocked.
+constexpr int kQrPanelThreads = 1024;
+
+template <typename T>
+__device__ __forceinline__ T block_sum_1024(T v, T* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T t = (threadIdx.x < 32) ? red[threadIdx.x] : T(0);
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[32] = t;
+  __syncthreads();
+  return red[32];
+}
+
+// Block-wide sums of NB per-thread values (entries c < lo are ignored).
+template <typename T, int NB>
+__device__ __forceinline__ void block_vsum(T (&pd)[NB], int lo, T (*red)[NB + 1], T* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (c >= lo) {
+      const T v = warp_sum(pd[c]);
+      if (lane == 0) red[warp][c] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NB && (int)threadIdx.x >= lo) {
+    T t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kQrPanelThreads)
+    qr_panel_kernel(T* __restrict__ W, int64_t s, int64_t p, int kb, double* __restrict__ diagR,
+                    T* __restrict__ tau, T* __restrict__ Tm) {
+  extern __shared__ __align__(16) unsigned char qp_smem[];
+  T* P = reinterpret_cast<T*>(qp_smem);        // [kb][len] panel, column-major
+  __shared__ T red[32][NB + 1];
+  __shared__ T wv[NB];
+  __shared__ T tj_s;
+  const int64_t len = s - p;
+  for (int c = 0; c < kb; ++c)
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) P[c * len + t] = W[(p + c) * s + p + t];
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    T* x = P + j * len;
+    T pd[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) pd[c] = 0;
+    for (int64_t t = j + threadIdx.x; t < len; t += blockDim.x) pd[0] += x[t] * x[t];
+    block_vsum<T, NB>(pd, 0, red, wv);
+    if (threadIdx.x == 0) {
+      const T alpha = sqrt(wv[0]);
+      const T x0 = x[j];
+      const T sgn = (x0 >= T(0)) ? T(1) : T(-1);
+      const T tj = (alpha > T(0)) ? T(1) / (alpha * (alpha + fabs(x0))) : T(0);
+      x[j] = x0 + sgn * alpha;               // v_j lives in rows j.. of panel column j
+      diagR[p + j] = (double)(-sgn * alpha);
+      tau[j] = tj;
+      tj_s = tj;
+    }
+    __syncthreads();
+    const T tj = tj_s;
+    // w_c = tau_j v_j^T y_c for all remaining panel columns at once, then y_c -= w_c v_j
+#pragma unroll
+    for (int c = 0; c < NB; ++c) pd[c] = 0;
+    for (int64_t t = j + threadIdx.x; t < len; t += blockDim.x) {
+      const T xv = x[t];
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c > j && c < kb) pd[c] += xv * P[c * len + t];
+    }
+    block_vsum<T, NB>(pd, j + 1, red, wv);
+    for (int64_t t = j + threadIdx.x; t < len; t += blockDim.x) {
+      const T xv = x[t];
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c > j && c < kb) P[c * len + t] -= (wv[c] * tj) * xv;
+    }
+    __syncthreads();
+  }
+  // T factor: T_jj = tau_j ; T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j)
+  if ((int)threadIdx.x < kb) Tm[threadIdx.x * NB + threadIdx.x] = tau[threadIdx.x];
+  __syncthreads();
+  for (int j = 1; j < kb; ++j) {
+    const T* vj = P + j * len;
+    T pd[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) pd[c] = 0;
+    for (int64_t t = j + threadIdx.x; t < len; t += blockDim.x) {   // v_j is zero above row j
+      const T vv = vj[t];
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < j) pd[c] += P[c * len + t] * vv;
+    }
+    block_vsum<T, NB>(pd, 0, red, wv);
+    if (threadIdx.x == 0) {
+      const T tjj = tau[j];
+      for (int i = 0; i < j; ++i) {
+        T acc = 0;
+        for (int l = i; l < j; ++l) acc += Tm[l * NB + i] * wv[l];
+        Tm[j * NB + i] = -tjj * acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    for (int i = 0; i < NB; ++i)
+      if (i > j || j >= kb) Tm[j * NB + i] = T(0);
+  }
+  // write back: rows 0..j-1 of column j are R entries, rows j.. hold v_j
+  for (int c = 0; c < kb; ++c)
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) W[(p + c) * s + p + t] = P[c * len + t];
+}
+
+// y -= V T^T V^T y for trailing columns c in [p + kb, n] (column n = Omega b).
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+    qr_trail_kernel(T* __restrict__ W, int64_t s, int64_t n, int64_t p, int kb,
+                    const T* __restrict__ Tm) {
+  __shared__ T red[NB][9];
+  __shared__ T wv[NB];
+  const int64_t len = s - p;
+  const T* V = W + p * s + p;                  // column j of V at V + j * s (rows j.. are valid)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t col = p + kb + blockIdx.x; col <= n; col += gridDim.x) {
+    T* y = W + col * s + p;
+    // w = V^T y (v_j has an implicit zero above row j)
+    for (int j = warp; j < kb; j += 8) {
+      const T* vj = V + (int64_t)j * s;
+      T pd = 0;
+      for (int64_t t = j + lane; t < len; t += 32) pd += vj[t] * y[t];
+      pd = warp_sum(pd);
+      if (lane == 0) wv[j] = pd;
+    }
+    __syncthreads();
+    // w2 = T^T w (T upper triangular): w2_j = sum_{i <= j} T(i, j) w_i
+    if (threadIdx.x < kb) {
+      const int j = threadIdx.x;
+      T acc = 0;
+      for (int i = 0; i <= j; ++i) acc += Tm[j * NB + i] * wv[i];
+      red[j][0] = acc;
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+      T acc = 0;
+      const int jmax = (t < kb - 1) ? (int)t : kb - 1;
+      for (int j = 0; j <= jmax; ++j) acc += V[(int64_t)j * s + t] * red[j][0];
+      y[t] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+static bool qr_blocked_fits(int64_t s, int nb) {
+  return (size_t)s * nb * sizeof(T) <= 200 * 1024;
+}
+
 template <typename T>
 static cudaError_t run_qr(const double* Y, int64_t s, int64_t n, T* W, double* aux, unsigned* bar,
                           double* R, double* c, int* err, int num_sms, cudaStream_t st) {
@@ -131,8 +305,39 @@ static cudaError_t run_qr(const double* Y, int64_t s, int64_t n, T* W, double* a
   return cudaGetLastError();
 }
 
+template <typename T, int NB>
+static cudaError_t run_qr_blocked(const double* Y, int64_t s, int64_t n, T* W, double* aux, double* R,
+                                  double* c, int num_sms, cudaStream_t st) {
+  const int64_t total = s * (n + 1);
+  convert_y_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Y, W, total);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double* diagR = aux + n;
+  T* tau = reinterpret_cast<T*>(aux + 2 * n + 8);
+  T* Tm = tau + NB;
+  const size_t smem = (size_t)s * NB * sizeof(T);
+  e = cudaFuncSetAttribute(qr_panel_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t p = 0; p < n; p += NB) {
+    const int kb = (int)std::min<int64_t>(NB, n - p);
+    qr_panel_kernel<T, NB><<<1, kQrPanelThreads, (size_t)(s - p) * kb * sizeof(T), st>>>(W, s, p, kb, diagR,
+                                                                                        tau, Tm);
+    const int64_t ncols = n + 1 - (p + kb);
+    if (ncols > 0) {
+      const unsigned grid = (unsigned)std::min<int64_t>(ncols, 4 * (int64_t)num_sms);
+      qr_trail_kernel<T, NB><<<grid, 256, 0, st>>>(W, s, n, p, kb, Tm);
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  qr_finalize_kernel<T><<<(unsigned)n, 256, 0, st>>>(W, s, n, diagR, R, c);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_qr(bool fp64, const double* Y, int64_t s, int64_t n, void* work, double* aux,
                       unsigned* bar, double* R, double* c, int* err, int num_sms, cudaStream_t st) {
+  if (!fp64 && qr_blocked_fits<float>(s, 24))
+    return run_qr_blocked<float, 24>(Y, s, n, static_cast<float*>(work), aux, R, c, num_sms, st);
   if (fp64)
     return run_qr<double>(Y, s, n, static_cast<double*>(work), aux, bar, R, c, err, num_sms, st);
   return run_qr<float>(Y, s, n, static_cast<float*>(work), aux, bar, R, c, err, num_sms, st);

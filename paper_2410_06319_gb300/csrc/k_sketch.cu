@@ -201,7 +201,10 @@ cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const d
 // ============================================================ tcgen05 sketch
 constexpr int kSkGenWarps = 16;
 constexpr int kSkGenThreads = kSkGenWarps * 32;
-constexpr int kSkThreads = (2 + kSkGenWarps) * 32;
+constexpr int kSkFixWarps = 2;                // resolve the FP64 fallbacks of a stage
+constexpr int kSkFixThreads = kSkFixWarps * 32;
+constexpr int kSkFixFirst = 2 + kSkGenWarps;
+constexpr int kSkThreads = (2 + kSkGenWarps + kSkFixWarps) * 32;
 constexpr int kSkQMax = 256;                 // FP64 fallbacks queued per stage
 
 struct SketchTcArgs {
@@ -212,8 +215,8 @@ struct SketchTcArgs {
   int* err;
 };
 
-__device__ __forceinline__ void gen_barrier() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kSkGenThreads) : "memory");
+__device__ __forceinline__ void fix_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kSkFixThreads) : "memory");
 }
 
 // Smem descriptor for a K-major operand whose rows are ROWB bytes (128: 128-byte
@@ -255,11 +258,14 @@ __global__ void __launch_bounds__(kSkThreads, 1)
   const uint32_t b_bytes = (uint32_t)a.bn * ROWB;              // one plane of Bt per stage
   const uint32_t stage_bytes = S_BYTES + NT * b_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4 * STAGES + 1);
   uint32_t* qcnt = tslot + 4;                                 // [STAGES]
   uint32_t* qbuf = qcnt + 4;                                  // [STAGES][kSkQMax][3]
+  // full: TMA bytes + fixer warps; empty: MMA commit; genned: generator warps done
+  // with the FP32 pass; fixed: fallbacks written and the queue reset.
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t done_bar = smem_u32(bars + 2 * STAGES);
+  const uint32_t genned0 = smem_u32(bars + 2 * STAGES), fixed0 = smem_u32(bars + 3 * STAGES);
+  const uint32_t done_bar = smem_u32(bars + 4 * STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t mt = blockIdx.x, ng = blockIdx.y, split = blockIdx.z;
@@ -270,8 +276,10 @@ __global__ void __launch_bounds__(kSkThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) {
-      mbar_init(full0 + 8 * st, kSkGenWarps + 1);
+      mbar_init(full0 + 8 * st, kSkFixWarps + 1);
       mbar_init(empty0 + 8 * st, 1);
+      mbar_init(genned0 + 8 * st, kSkGenWarps);
+      mbar_init(fixed0 + 8 * st, kSkFixWarps);
       qcnt[st] = 0;
     }
     mbar_init(done_bar, 1);
@@ -334,13 +342,14 @@ __global__ void __launch_bounds__(kSkThreads, 1)
       }
       tc_commit(done_bar);
     }
-  } else {
+  } else if (warp < kSkFixFirst) {
     // ---------------- generator warps: fl_s(G) tile, 128 rows x BK columns
     const int g = threadIdx.x - 64;
     for (int ks = 0; ks < nk; ++ks) {
       const int st = ks % STAGES;
       const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
       if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
+      if (!mbar_wait(fixed0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
       uint8_t* S = smem + st * stage_bytes;
       uint32_t* qb = qbuf + st * (kSkQMax * 3);
       const int64_t kbase = k_begin + (int64_t)ks * BK;
@@ -381,10 +390,22 @@ __global__ void __launch_bounds__(kSkThreads, 1)
         }
         *reinterpret_cast<uint4*>(S + swz_chunk<ROWB>(row, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
-      gen_barrier();
-      // FP64 fallbacks of this stage, spread over all generator threads
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(genned0 + 8 * st);
+    }
+  } else {
+    // ---------------- fixer warps: FP64 definition for the queued pairs of a stage,
+    // overlapping the generation of the next stage
+    const int fx = threadIdx.x - kSkFixFirst * 32;
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % STAGES;
+      const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+      if (!mbar_wait(genned0 + 8 * st, ph, a.err, DEV_TIMEOUT_FULL)) break;
+      uint8_t* S = smem + st * stage_bytes;
+      const uint32_t* qb = qbuf + st * (kSkQMax * 3);
       const uint32_t nq = min(qcnt[st], (uint32_t)kSkQMax);
-      for (uint32_t qi = g; qi < nq; qi += kSkGenThreads) {
+      for (uint32_t qi = fx; qi < nq; qi += kSkFixThreads) {
         const uint32_t pos = qb[qi * 3];
         uint32_t be, bo;
         gauss_pair_slow<GF>(qb[qi * 3 + 1], qb[qi * 3 + 2], be, bo);
@@ -395,11 +416,14 @@ __global__ void __launch_bounds__(kSkThreads, 1)
         else
           *reinterpret_cast<uint16_t*>(cp + 2 * pi) = (uint16_t)(be | (bo << 8));
       }
-      gen_barrier();
-      if (g == 0) qcnt[st] = 0;
       fence_proxy_async_smem();
+      fix_barrier();            // every fixer has read qcnt and written its pairs
+      if (fx == 0) qcnt[st] = 0;
       __syncwarp();
-      if (lane == 0) mbar_arrive(full0 + 8 * st);
+      if (lane == 0) {
+        mbar_arrive(full0 + 8 * st);
+        mbar_arrive(fixed0 + 8 * st);
+      }
     }
   }
 
@@ -454,8 +478,8 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
   p->bn = bn;
   p->mtiles = (int)((s + 127) / 128);
   const size_t stage = (size_t)128 * p->rowb + (size_t)p->nt * bn * p->rowb;
-  p->stages = (4 * stage + 1024 + 256 + 16 + 4 * kSkQMax * 12 <= 232448) ? 4 : 2;
-  p->smem = 1024 + (size_t)p->stages * stage + 256 + 16 + (size_t)p->stages * kSkQMax * 12;
+  p->stages = (4 * stage + 1024 + 512 + 4 * kSkQMax * 12 <= 232448) ? 4 : 2;
+  p->smem = 1024 + (size_t)p->stages * stage + 512 + (size_t)p->stages * kSkQMax * 12;
   if (p->smem > 232448) return false;
   const int64_t base = (int64_t)p->mtiles * p->ngroups;
   const int64_t ksteps = (m + BK - 1) / BK;

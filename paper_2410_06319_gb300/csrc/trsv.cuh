@@ -6,8 +6,8 @@
 // update y_r -= sum_c M(r, i0 + c) x_c of the remaining rows by all threads.
 // The update operands are contiguous column segments of the column-major
 // matrix; they are staged into shared memory with cp.async in chunks of at
-// most TR rows, double buffered across chunks and steps, so the loads of the
-// next chunk (and of the next D_k^-1) overlap the current one.
+// most TR rows, NBUF buffers deep across chunks and steps, so the loads of the
+// next chunks (and of the next D_k^-1) overlap the current one.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -26,12 +26,13 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared memory the solver needs: two chunk buffers of 32 x TR elements and two
-// diagonal-inverse buffers of 32 x 32 elements.
+// Shared memory the solver needs: NBUF chunk buffers of 32 x TR elements and
+// NBUF diagonal-inverse buffers of 32 x 32 elements (copies run NBUF-1 items ahead).
 template <typename T>
 struct TrsvSmem {
   static constexpr int TR = (sizeof(T) == 4) ? 512 : 256;   // rows per staged chunk
-  static constexpr size_t bytes = (size_t)2 * 32 * TR * sizeof(T) + (size_t)2 * 1024 * sizeof(T);
+  static constexpr int NBUF = 3;
+  static constexpr size_t bytes = (size_t)NBUF * 32 * TR * sizeof(T) + (size_t)NBUF * 1024 * sizeof(T);
 };
 
 // Solves in place on xs (shared, n entries): upper -> R x = y, lower -> L x = y.
@@ -42,9 +43,11 @@ template <typename T, bool UPPER>
 __device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, const T* __restrict__ D,
                                            int n, T* xs, unsigned char* buf) {
   constexpr int TR = TrsvSmem<T>::TR;
+  constexpr int NBUF = TrsvSmem<T>::NBUF;
   constexpr int VE = 16 / sizeof(T);                 // elements per 16-byte copy
-  T* chunk[2] = {reinterpret_cast<T*>(buf), reinterpret_cast<T*>(buf) + 32 * TR};
-  T* dbuf[2] = {reinterpret_cast<T*>(buf) + 64 * TR, reinterpret_cast<T*>(buf) + 64 * TR + 1024};
+  T* const base = reinterpret_cast<T*>(buf);
+  auto chunk = [&](int sl) { return base + sl * 32 * TR; };
+  auto dbuf = [&](int sl) { return base + NBUF * 32 * TR + sl * 1024; };
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = (n + 31) >> 5;
   // work items: (step, row chunk); a step with no remaining rows still has one
@@ -72,7 +75,7 @@ __device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, 
     int lo, hi;
     rows_of(step, lo, hi);
     if (ci == 0) {  // the diagonal inverse of the step travels with its first chunk
-      for (int e = tid * VE; e < 1024; e += blockDim.x * VE) cp_async16(dbuf[sl] + e, D + (size_t)k * 1024 + e);
+      for (int e = tid * VE; e < 1024; e += blockDim.x * VE) cp_async16(dbuf(sl) + e, D + (size_t)k * 1024 + e);
     }
     const int r0 = lo + ci * TR, r1 = min(hi, r0 + TR);
     if (r1 > r0) {
@@ -80,30 +83,46 @@ __device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, 
       const int segs = (r1 - a0 + VE - 1) / VE;       // 16-byte pieces per column
       for (int e = tid; e < w * segs; e += blockDim.x) {
         const int c = e / segs, sgi = e % segs;
-        cp_async16(chunk[sl] + c * TR + sgi * VE, M + (size_t)(i0 + c) * ld + a0 + sgi * VE);
+        cp_async16(chunk(sl) + c * TR + sgi * VE, M + (size_t)(i0 + c) * ld + a0 + sgi * VE);
       }
     }
     cp_async_commit();
   };
+  // the item sequence (step, chunk), advanced in order
+  auto advance = [&](int& st, int& c) {
+    if (++c >= nchunks(st)) {
+      ++st;
+      c = 0;
+    }
+  };
+  // prefetch the first NBUF-1 items
+  int pst = 0, pci = 0, psl = 0;
+  for (int q = 0; q < NBUF - 1; ++q) {
+    if (pst < nb) {
+      issue(pst, pci, psl);
+      advance(pst, pci);
+    } else {
+      cp_async_commit();
+    }
+    psl = (psl + 1) % NBUF;
+  }
   int step = 0, ci = 0, sl = 0;
-  issue(0, 0, 0);
   while (step < nb) {
     const int k = UPPER ? nb - 1 - step : step;
     const int i0 = k * 32, w = min(32, n - i0);
-    const int nch = nchunks(step);
-    // prefetch the next item
-    int nstep = step, nci = ci + 1;
-    if (nci >= nch) {
-      nstep = step + 1;
-      nci = 0;
+    // keep NBUF-1 items in flight
+    if (pst < nb) {
+      issue(pst, pci, psl);
+      advance(pst, pci);
+    } else {
+      cp_async_commit();
     }
-    if (nstep < nb) issue(nstep, nci, sl ^ 1);
-    else cp_async_commit();
-    cp_async_wait<1>();
+    psl = (psl + 1) % NBUF;
+    cp_async_wait<NBUF - 1>();
     __syncthreads();
     if (ci == 0) {   // diagonal block: x_k = D_k^-1 y_k
       if (warp == 0) {
-        const T* dk = dbuf[sl];
+        const T* dk = dbuf(sl);
         T acc = T(0);
 #pragma unroll 8
         for (int c = 0; c < w; ++c) acc += dk[c * 32 + lane] * xs[i0 + c];
@@ -117,7 +136,7 @@ __device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, 
     const int r0 = lo + ci * TR, r1 = min(hi, r0 + TR);
     if (r1 > r0) {
       const int a0 = r0 & ~(VE - 1);
-      const T* ch = chunk[sl];
+      const T* ch = chunk(sl);
       // TR rows, 1024 threads: 1024 / TR threads per row share the 32 columns
       constexpr int TPR = 1024 / TR;
       const int rr = tid / TPR, part = tid % TPR;
@@ -134,9 +153,8 @@ __device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, 
       if (r < r1 && part == 0) xs[r] -= acc;
     }
     __syncthreads();
-    step = nstep;
-    ci = nci;
-    sl ^= 1;
+    advance(step, ci);
+    sl = (sl + 1) % NBUF;
   }
   cp_async_wait<0>();
 }

@@ -212,3 +212,24 @@ def test_lsir_split_sketch_converges_where_bf16_fails(lsq, handle):
     R, c = qr.householder_qr(Y, n, dtype=np.float32)
     sv = np.linalg.svd(P.A @ np.linalg.inv(R), compute_uv=False)
     assert sv[0] / sv[-1] < 4.0
+
+
+def test_batched_uneven_problems_match_single_solves(lsq, handle):
+    """lsq_lsir_batched over uneven problems equals lsq_lsir on each problem."""
+    shapes = [(3000, 32, 1e2), (7000, 64, 1e4), (5000, 100, 1e3), (4100, 45, 10.0), (9000, 77, 1e5)]
+    probs, singles, P_all = [], [], []
+    for k, (m, n, kappa) in enumerate(shapes):
+        P = randsvd_problem(m, n, kappa, rho=1e-3, seed=40 + k)
+        P_all.append(P)
+        A, b = dev(P.A), dev(P.b)
+        x, r = zeros(n), zeros(m)
+        probs.append(dict(A=A, b=b, m=m, n=n, s=4 * n, seed=k, x=x, r=r))
+        xs, rs = zeros(n), zeros(m)
+        lsq.lsq_lsir(handle, A, b, m, n, 4 * n, "bf16x3", "f32", "f32", "f64", 1e-6, k, None, xs, rs)
+        singles.append((xs.cpu().numpy(), rs.cpu().numpy()))
+    st, sts, infos = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    assert st == 0 and all(v == 0 for v in sts)
+    for k, pr in enumerate(probs):
+        assert np.array_equal(pr["x"].cpu().numpy(), singles[k][0])
+        assert np.array_equal(pr["r"].cpu().numpy(), singles[k][1])
+        assert infos[k].ir_converged == 1
