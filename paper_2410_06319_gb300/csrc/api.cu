@@ -1026,7 +1026,9 @@ lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* pro
   }
   std::atomic<int32_t> next{0};
   std::vector<lsq_status> sts((size_t)nprob, LSQ_OK);
-  auto work = [&](lsq_handle* w) {
+  std::vector<int> who((size_t)nprob, 0);   // worker that ran each problem
+  auto work = [&](int k) {
+    lsq_handle* w = h->workers[(size_t)k];
     cudaSetDevice(h->device);
     for (;;) {
       const int32_t i = next.fetch_add(1);
@@ -1038,18 +1040,23 @@ lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* pro
       if ((double)probs[i].m * (double)probs[i].n < 67108864.0) o.no_graph = 1;
       lsq_info local;
       lsq_info* inf = infos ? &infos[i] : &local;
+      who[(size_t)i] = k;
       sts[(size_t)i] = lsq_lsir(w, probs[i].A, probs[i].b, probs[i].m, probs[i].n, probs[i].s, u_s, u_p,
                                 u_w, u_r, tol, probs[i].seed, &o, probs[i].x, probs[i].r, inf);
     }
   };
   std::vector<std::thread> threads;
-  for (int k = 1; k < nw; ++k) threads.emplace_back(work, h->workers[(size_t)k]);
-  work(h->workers[0]);
+  for (int k = 1; k < nw; ++k) threads.emplace_back(work, k);
+  work(0);
   for (auto& t : threads) t.join();
   lsq_status agg = LSQ_OK;
   for (int32_t i = 0; i < nprob; ++i) {
     if (statuses) statuses[i] = sts[(size_t)i];
-    if (sts[(size_t)i] < 0 && agg >= 0) agg = sts[(size_t)i];
+    if (sts[(size_t)i] < 0 && agg >= 0) {
+      agg = sts[(size_t)i];
+      if (agg == LSQ_E_CUDA)   // the text of the first failure, on the caller's handle
+        h->last_cuda = "problem " + std::to_string(i) + ": " + h->workers[(size_t)who[(size_t)i]]->last_cuda;
+    }
     else if (sts[(size_t)i] == LSQ_NOT_CONVERGED && agg == LSQ_OK) agg = LSQ_NOT_CONVERGED;
   }
   return agg;

@@ -220,4 +220,26 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   return __syncthreads_and(ok) != 0;
 }
 
+// ---------------------------------------------------------------- host
+// The dynamic shared-memory limit of a kernel is one setting per function and
+// device, shared by every host thread and stream.  Setting it to a
+// problem-dependent size races with concurrent launches of other sizes (one
+// thread lowers it under another's launch), so it is always raised to the
+// device's opt-in maximum less the kernel's static shared memory; a launch that
+// needs more than that fails as invalid.
+template <typename K>
+inline cudaError_t allow_dyn_smem(K kern, size_t need) {
+  int dev = 0, lim = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const size_t dyn = (size_t)lim > fa.sharedSizeBytes ? (size_t)lim - fa.sharedSizeBytes : 0;
+  if (need > dyn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 }  // namespace lsq

@@ -417,7 +417,7 @@ static cudaError_t dispatch_bulk(BulkArgs<T> p, int nblk, int num_sms_unused, cu
   if (smem < red_bytes) smem = red_bytes;
   smem += 2 * stages * 8;
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<nblk, kBulkThreads, smem, st>>>(p);
     return cudaGetLastError();
@@ -440,7 +440,7 @@ static cudaError_t dispatch_pass(const PassArgs<T>& p, int nblk, cudaStream_t st
   const size_t smem = (size_t)8 * p.nv * VW * sizeof(T);
   auto go = [&](auto kern) -> cudaError_t {
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = allow_dyn_smem(kern, smem);
       if (e != cudaSuccess) return e;
     }
     kern<<<nblk, 256, smem, st>>>(p);
@@ -878,8 +878,7 @@ cudaError_t launch_lsqr_step(const Tri<T>& f, const T* s, T* v, T* w, T* z, T* t
                              bool init, cudaStream_t strm) {
   if (f.n > 1024) return cudaErrorInvalidValue;
   const size_t smem = TrsvSmem<T>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(lsqr_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_dyn_smem(lsqr_step_kernel<T>, smem);
   if (e != cudaSuccess) return e;
   lsqr_step_kernel<T><<<1, 1024, smem, strm>>>(f, s, v, w, z, t, st, init);
   return cudaGetLastError();
@@ -1196,8 +1195,7 @@ cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const d
                             cudaStream_t s) {
   const size_t smem = (size_t)(ldh - 1) * (ldh - 1) * sizeof(double);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gm_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_dyn_smem(gm_solve_kernel, smem);
     if (e != cudaSuccess) return e;
   }
   gm_solve_kernel<<<1, 32, smem, s>>>(st, H, ldh, g, y);

@@ -284,7 +284,7 @@ static cudaError_t run_qr(const double* Y, int64_t s, int64_t n, T* W, double* a
   const size_t smem = (size_t)s * sizeof(T);
   auto kern = qr_kernel<T>;
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
   int occ = 0;
@@ -316,7 +316,7 @@ static cudaError_t run_qr_blocked(const double* Y, int64_t s, int64_t n, T* W, d
   T* tau = reinterpret_cast<T*>(aux + 2 * n + 8);
   T* Tm = tau + NB;
   const size_t smem = (size_t)s * NB * sizeof(T);
-  e = cudaFuncSetAttribute(qr_panel_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = allow_dyn_smem(qr_panel_kernel<T, NB>, smem);
   if (e != cudaSuccess) return e;
   for (int64_t p = 0; p < n; p += NB) {
     const int kb = (int)std::min<int64_t>(NB, n - p);

@@ -495,16 +495,18 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
 
 bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
                     int box_rows, int rowb) {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // looked up once (thread-safe static initialisation; batched solves call this
+  // from several host threads)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void**>(&fn),
-                                         12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-      fn = nullptr;
-      return false;
-    }
-  }
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  if (!fn) return false;
   const int EB = (fmt == FMT_E4M3) ? 1 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ldb * EB)};
@@ -522,7 +524,7 @@ template <int FMT, int STAGES, int ROWB, int NT>
 static cudaError_t launch_tc_inst(const SketchPlan& p, const CUtensorMap& tm, const SketchTcArgs& a,
                                   cudaStream_t st) {
   auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
   kern<<<grid, kSkThreads, p.smem, st>>>(tm, a);

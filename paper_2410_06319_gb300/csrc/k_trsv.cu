@@ -44,12 +44,12 @@ cudaError_t launch_trsv(bool upper, const Tri<T>& f, const TIN* y, double yscale
   const size_t smem = TrsvSmem<T>::bytes;
   if (upper) {
     auto kern = trsv_kernel<T, TIN, TOUT, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<1, kTrsvThreads, smem, st>>>(f.R, f.ld, f.DU, (int)f.n, y, yscale, x, done, jp, ys, xstr);
   } else {
     auto kern = trsv_kernel<T, TIN, TOUT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<1, kTrsvThreads, smem, st>>>(f.L, f.ld, f.DL, (int)f.n, y, yscale, x, done, jp, ys, xstr);
   }

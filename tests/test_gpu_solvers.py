@@ -106,17 +106,25 @@ def test_lsir_mixed_reaches_working_precision(lsq, handle, fmt):
     assert abs(io["its"] - info.ir_its) <= 1
 
 
-def test_lsir_full_size_bench_workload(lsq, handle):
-    """m=1e5, n=500, kappa=1e6, rho=1e-3, s=4n, FP32 QR/LSQR, FP64 residuals (the bench workload)."""
+def test_lsir_full_size_single_term_bf16_flags_condition(lsq, handle):
+    """m=1e5, n=500, kappa=1e6: single-term BF16 has kappa(A) u_s >> 1 (Sec. 3.4)."""
     m, n, s = 100000, 500, 2000
     P = randsvd_problem(m, n, 1e6, rho=1e-3, seed=1)
     A, b = dev(P.A), dev(P.b)
-    # single-term BF16: kappa(A) u_s >> 1 (Sec. 3.4) -> warning bit, still finite iterates
+    # warning bit, still finite iterates
     x, r = zeros(n), zeros(m)
     st, info = lsq.lsq_lsir(handle, A, b, m, n, s, "bf16", "f32", "f32", "f64", 1e-6, 0,
                             {"ir_maxit": 2}, x, r)
     assert st in (0, 1) and (info.flags & 1)
     assert np.all(np.isfinite(x.cpu().numpy()))
+
+
+def test_lsir_full_size_bench_workload(lsq, handle):
+    """m=1e5, n=500, kappa=1e6, rho=1e-3, s=4n, BF16X3 sketch, FP32 QR/LSQR, FP64 residuals
+    (the bench workload)."""
+    m, n, s = 100000, 500, 2000
+    P = randsvd_problem(m, n, 1e6, rho=1e-3, seed=1)
+    A, b = dev(P.A), dev(P.b)
     # the three-term split sketch: converges to the working-precision level
     x, r = zeros(n), zeros(m)
     st, info = lsq.lsq_lsir(handle, A, b, m, n, s, "bf16x3", "f32", "f32", "f64", 1e-6, 0, None, x, r)
