@@ -72,7 +72,8 @@ typedef enum lsq_status {
   LSQ_E_CUDA = -5,         /* a CUDA call failed (see lsq_last_cuda_error) */
   LSQ_E_TIMEOUT = -6,      /* a bounded device-side wait ran out */
   LSQ_E_NOMEM = -7,        /* workspace allocation failed */
-  LSQ_E_UNSUPPORTED = -8   /* valid but not supported on this device/build */
+  LSQ_E_UNSUPPORTED = -8,  /* valid but not supported on this device/build */
+  LSQ_E_SIZE = -9          /* larger than the fixed scratch of lsq_qr_r_noalloc */
 } lsq_status;
 
 /* info.flags bits */
@@ -240,6 +241,52 @@ lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* pro
  */
 lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_prec u_s,
                      uint64_t seed, double* out);
+
+/*
+ * lsq_qr_r_noalloc -- the QR of lsq_qr_r (Algorithm 1 step 2) for callers
+ * that cannot allocate.  The paper has no counterpart: this is an interface
+ * of this library only.
+ *
+ * Who needs it: code that may not allocate device memory when it runs, e.g. a
+ * service whose device memory is fully committed up front (a fixed budget that
+ * must not grow), a latency-critical loop where cudaMalloc / cudaFree would
+ * synchronise the device and stall other streams, or a caller that cannot
+ * create a handle (lsq_create owns streams and a workspace that grows on
+ * demand).  This call allocates nothing, host or device, and needs no handle:
+ * its scratch is one file-scope device array of fixed size per device,
+ * LSQ_NOALLOC_WORK_BYTES for the working copy of Y plus 64 KiB for the other
+ * factors and 256 bytes of control words.
+ *
+ * In:  Y, device FP64, s x (n+1) column-major with leading dimension s (the
+ *      output of lsq_sketch; column n is Omega b).  u_p = LSQ_F32 or LSQ_F64,
+ *      the precision of the factorization.  cuda_stream = a cudaStream_t
+ *      (NULL = legacy default stream) on which all work is enqueued.
+ * Out: R, device FP64 n x n column-major (ld = n), upper triangular with a
+ *      non-negative diagonal, the same values lsq_qr_r writes for the same Y
+ *      and u_p; c (device FP64, n; may be NULL) = (Q^T Omega b)[:n] with the
+ *      same sign normalisation, so that x_s = R^-1 c (Sec. 4).
+ *      The caller owns Y, R and c.
+ * Limits: 1 <= n <= LSQ_NOALLOC_MAX_N, n <= s <= 16384 (else LSQ_E_INVAL), and
+ *      s * (n + 1) * (4 for F32, 8 for F64) <= LSQ_NOALLOC_WORK_BYTES, else
+ *      LSQ_E_SIZE before any device work.
+ * Errors: LSQ_E_RANK (zero or non-finite diagonal of R), LSQ_E_TIMEOUT (a
+ *      bounded grid barrier ran out), LSQ_E_CUDA.  On any error R and c are
+ *      unspecified.
+ * Synchronisation: returns after the factorization has completed (it
+ *      synchronises cuda_stream once to read the scratch's error word).
+ * Set-up: the first call on a device, with that device current, looks up the
+ *      address of the device's scratch array (cudaGetSymbolAddress); make that
+ *      first call before any stream capture begins on the device.
+ * Concurrency: all calls on one device share one scratch array.  Calls that
+ *      overlap in time on the same device (from several host threads, or on
+ *      several streams) race on it and give wrong results; serialise them.
+ *      The scratch's barrier and error words must be zero when the kernels
+ *      start: each call clears them on cuda_stream itself.
+ */
+#define LSQ_NOALLOC_WORK_BYTES 8388608
+#define LSQ_NOALLOC_MAX_N 1024
+lsq_status lsq_qr_r_noalloc(const double* Y, int64_t s, int64_t n, lsq_prec u_p, double* R,
+                            double* c, void* cuda_stream);
 
 #ifdef __cplusplus
 }

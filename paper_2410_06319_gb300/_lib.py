@@ -22,7 +22,7 @@ lib = ctypes.CDLL(library_path())
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "bf16x3": 5}
 STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RANK",
           -3: "LSQ_E_BREAKDOWN", -4: "LSQ_E_NONFINITE", -5: "LSQ_E_CUDA", -6: "LSQ_E_TIMEOUT",
-          -7: "LSQ_E_NOMEM", -8: "LSQ_E_UNSUPPORTED"}
+          -7: "LSQ_E_NOMEM", -8: "LSQ_E_UNSUPPORTED", -9: "LSQ_E_SIZE"}
 
 
 #: kernels timed with opts.timing (order of lsq_info.kern_ms)
@@ -92,8 +92,9 @@ lib.lsq_omega.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_uint64, _
 lib.lsq_lsir_batched.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
+lib.lsq_qr_r_noalloc.argtypes = [_P, _I64, _I64, ctypes.c_int, _P, _P, _P]
 for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir",
-           "lsq_omega", "lsq_lsir_batched"):
+           "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -228,3 +229,18 @@ def lsq_lsir_batched(h, problems, u_s, u_p, u_w, u_r, tol, opts=None):
 def lsq_omega(h, s, j0, cols, u_s, seed, out):
     return _check(h, lib.lsq_omega(h.ptr, s, j0, cols, _prec(u_s), int(seed), _ptr(out)),
                   "lsq_omega", allow=(0,))
+
+
+def lsq_qr_r_noalloc(Y, s, n, u_p, R, c=None, stream=None):
+    """QR of a sketch in the library's fixed device scratch (no allocation, no handle).
+
+    Returns the status; raises LsqError on errors other than LSQ_E_SIZE, which is
+    returned so callers can fall back to lsq_qr_r.
+    """
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.lsq_qr_r_noalloc(_ptr(Y), s, n, _prec(u_p), _ptr(R), _ptr(c), _P(stream))
+    if st not in (0, -9):
+        raise LsqError(st, "lsq_qr_r_noalloc")
+    return st

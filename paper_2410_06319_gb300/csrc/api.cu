@@ -829,6 +829,7 @@ const char* lsq_status_string(lsq_status st) {
     case LSQ_E_TIMEOUT: return "LSQ_E_TIMEOUT";
     case LSQ_E_NOMEM: return "LSQ_E_NOMEM";
     case LSQ_E_UNSUPPORTED: return "LSQ_E_UNSUPPORTED";
+    case LSQ_E_SIZE: return "LSQ_E_SIZE";
   }
   return "LSQ_UNKNOWN";
 }
