@@ -267,6 +267,228 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ------------------------------------------------------ register-panel variant
+// The same blocked algorithm with the panel held in registers: 1024 threads,
+// thread t owns panel rows t, t + 1024, ... (RPT rows), NB columns each.  A
+// column costs two block reductions: ||x_j|| (with x_j[j] broadcast through
+// shared memory so every thread forms alpha, tau and v_jj itself), then one
+// reduction of v_j^T x_c for all other panel columns at once -- c > j are the
+// update coefficients, c < j are the Gram entries v_c^T v_j from which warp 0
+// extends the compact-WY factor T (T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]).
+// Within a warp the NB partial sums are reduced by recursive halving (NB
+// shuffles instead of 5 NB).
+constexpr int kQrRegThreads = 1024;
+
+// After the call lane l holds the warp total of v[l >> 1] (N = 16).
+template <int N>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[N], int lane) {
+  static_assert(N == 16, "16 values over 32 lanes");
+#pragma unroll
+  for (int o = 16, cnt = N; o >= 2; o >>= 1, cnt >>= 1) {
+    const bool upper = (lane & o) != 0;
+    const int half = cnt / 2;
+#pragma unroll
+    for (int t = 0; t < N / 2; ++t) {
+      if (t < half) {
+        const float send = upper ? v[t] : v[t + half];
+        const float keep = upper ? v[t + half] : v[t];
+        v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <int NB, int RPT>
+__global__ void __launch_bounds__(kQrRegThreads, 1)
+    qr_panel_reg_kernel(float* __restrict__ W, int64_t s, int64_t p, int kb, double* __restrict__ diagR,
+                        float* __restrict__ tau, float* __restrict__ Tm) {
+  __shared__ float redA[32];
+  __shared__ float redB[32][NB];
+  __shared__ float Ts[NB * NB];
+  __shared__ float x0s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t len = s - p;
+  float x[RPT][NB];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int64_t r = tid + (int64_t)i * kQrRegThreads;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x[i][c] = (r < len && c < kb) ? W[(p + c) * s + p + r] : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      // ---- alpha = ||x_j[j:]||, tau_j, v_jj
+      float part = 0.0f;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int64_t r = tid + (int64_t)i * kQrRegThreads;
+        if (r >= j) part += x[i][j] * x[i][j];
+      }
+      part = warp_sum(part);
+      if (lane == 0) redA[warp] = part;
+      if (tid == j) x0s = x[0][j];
+      __syncthreads();
+      const float n2 = warp_sum(redA[lane]);
+      const float x0 = x0s;
+      const float alpha = sqrtf(n2);
+      const float sgn = (x0 >= 0.0f) ? 1.0f : -1.0f;
+      const float tj = (alpha > 0.0f) ? 1.0f / (alpha * (alpha + fabsf(x0))) : 0.0f;
+      if (tid == j) {
+        x[0][j] = x0 + sgn * alpha;          // v_j lives in rows j.. of panel column j
+        diagR[p + j] = (double)(-sgn * alpha);
+        tau[j] = tj;
+      }
+      // ---- d_c = v_j^T x_c for every other column (rows >= j; v_j is zero above)
+      float pw[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        pw[c] = 0.0f;
+        if (c != j) {
+#pragma unroll
+          for (int i = 0; i < RPT; ++i) {
+            const int64_t r = tid + (int64_t)i * kQrRegThreads;
+            if (r >= j) pw[c] += x[i][j] * x[i][c];
+          }
+        }
+      }
+      const float wsum = warp_reduce_scatter<NB>(pw, lane);
+      if ((lane & 1) == 0) redB[warp][lane >> 1] = wsum;
+      __syncthreads();
+      float d = 0.0f;
+      if (lane < NB) {
+#pragma unroll 8
+        for (int w = 0; w < 32; ++w) d += redB[w][lane];
+      }
+      // ---- trailing panel columns: x_c -= tau_j d_c v_j
+#pragma unroll
+      for (int c = j + 1; c < NB; ++c) {
+        const float coef = tj * __shfl_sync(0xffffffffu, d, c);
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const int64_t r = tid + (int64_t)i * kQrRegThreads;
+          if (r >= j) x[i][c] -= coef * x[i][j];
+        }
+      }
+      // ---- T column j (warp 0): T_jj = tau_j, T[a, j] = -tau_j sum_{l=a}^{j-1} T[a, l] G[l, j]
+      if (warp == 0) {
+        float tcol = 0.0f;
+#pragma unroll
+        for (int l = 0; l < j; ++l) {
+          const float g = __shfl_sync(0xffffffffu, d, l);
+          if (lane <= l) tcol += Ts[lane + l * NB] * g;
+        }
+        if (lane < j) Ts[lane + j * NB] = -tj * tcol;
+        if (lane == j) Ts[j + j * NB] = tj;
+        if (lane > j && lane < NB) Ts[lane + j * NB] = 0.0f;
+        __syncwarp();
+      }
+    } else if (warp == 0 && lane < NB) {
+      Ts[lane + j * NB] = 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) Tm[e] = Ts[e];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int64_t r = tid + (int64_t)i * kQrRegThreads;
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (r < len && c < kb) W[(p + c) * s + p + r] = x[i][c];
+  }
+}
+
+// y -= V T^T V^T y for the trailing columns (V in registers, one block
+// reduction per column; reduction buffers alternate so one barrier suffices).
+template <int NB, int RPT>
+__global__ void __launch_bounds__(kQrRegThreads, 1)
+    qr_trail_reg_kernel(float* __restrict__ W, int64_t s, int64_t n, int64_t p, int kb,
+                        const float* __restrict__ Tm) {
+  __shared__ float red[2][32][NB];
+  __shared__ float Ts[NB * NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t len = s - p;
+  for (int e = tid; e < NB * NB; e += blockDim.x) Ts[e] = Tm[e];
+  float V[RPT][NB];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int64_t r = tid + (int64_t)i * kQrRegThreads;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) V[i][c] = (r < len && c < kb && r >= c) ? W[(p + c) * s + p + r] : 0.0f;
+  }
+  __syncthreads();
+  int par = 0;
+  for (int64_t col = p + kb + blockIdx.x; col <= n; col += gridDim.x, par ^= 1) {
+    float* y = W + col * s + p;
+    float yv[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int64_t r = tid + (int64_t)i * kQrRegThreads;
+      yv[i] = (r < len) ? y[r] : 0.0f;
+    }
+    float pw[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      pw[c] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) pw[c] += V[i][c] * yv[i];
+    }
+    const float wsum = warp_reduce_scatter<NB>(pw, lane);
+    if ((lane & 1) == 0) red[par][warp][lane >> 1] = wsum;
+    __syncthreads();
+    float w = 0.0f;
+    if (lane < NB) {
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) w += red[par][q][lane];
+    }
+    // w2 = T^T w: w2_c = sum_{a <= c} T[a, c] w_a
+    float w2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const float wa = __shfl_sync(0xffffffffu, w, a);
+      if (lane < NB && a <= lane) w2 += Ts[a + lane * NB] * wa;
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      const float w2c = __shfl_sync(0xffffffffu, w2, c);
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) yv[i] -= V[i][c] * w2c;
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int64_t r = tid + (int64_t)i * kQrRegThreads;
+      if (r < len) y[r] = yv[i];
+    }
+  }
+}
+
+template <int RPT>
+static cudaError_t run_qr_reg(const double* Y, int64_t s, int64_t n, float* W, double* aux, double* R,
+                              double* c, int num_sms, cudaStream_t st) {
+  constexpr int NB = 16;
+  const int64_t total = s * (n + 1);
+  convert_y_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Y, W, total);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double* diagR = aux + n;
+  float* tau = reinterpret_cast<float*>(aux + 2 * n + 8);
+  float* Tm = tau + NB;
+  for (int64_t p = 0; p < n; p += NB) {
+    const int kb = (int)std::min<int64_t>(NB, n - p);
+    qr_panel_reg_kernel<NB, RPT><<<1, kQrRegThreads, 0, st>>>(W, s, p, kb, diagR, tau, Tm);
+    const int64_t ncols = n + 1 - (p + kb);
+    if (ncols > 0) {
+      const unsigned grid = (unsigned)std::min<int64_t>(ncols, (int64_t)num_sms);
+      qr_trail_reg_kernel<NB, RPT><<<grid, kQrRegThreads, 0, st>>>(W, s, n, p, kb, Tm);
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  qr_finalize_kernel<float><<<(unsigned)n, 256, 0, st>>>(W, s, n, diagR, R, c);
+  return cudaGetLastError();
+}
+
 template <typename T>
 static bool qr_blocked_fits(int64_t s, int nb) {
   return (size_t)s * nb * sizeof(T) <= 200 * 1024;
@@ -336,6 +558,10 @@ static cudaError_t run_qr_blocked(const double* Y, int64_t s, int64_t n, T* W, d
 
 cudaError_t launch_qr(bool fp64, const double* Y, int64_t s, int64_t n, void* work, double* aux,
                       unsigned* bar, double* R, double* c, int* err, int num_sms, cudaStream_t st) {
+  if (!fp64 && s <= kQrRegThreads)
+    return run_qr_reg<1>(Y, s, n, static_cast<float*>(work), aux, R, c, num_sms, st);
+  if (!fp64 && s <= 2 * kQrRegThreads)
+    return run_qr_reg<2>(Y, s, n, static_cast<float*>(work), aux, R, c, num_sms, st);
   if (!fp64 && qr_blocked_fits<float>(s, 24))
     return run_qr_blocked<float, 24>(Y, s, n, static_cast<float*>(work), aux, R, c, num_sms, st);
   if (fp64)

@@ -14,6 +14,7 @@
 //  * reduce: FP64 sum of the split partials, times s^-1/2 and 2^-k_j.
 #include <cudaTypedefs.h>
 
+#include "cast.cuh"
 #include "common.cuh"
 #include "gauss.cuh"
 #include "kernels.h"
@@ -75,6 +76,17 @@ cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t 
 }
 
 // ============================================================ cast pass
+// Roundings run on integer units (cast.cuh); the FP64 definition is left only
+// for out-of-range values (subnormal results, overflow, subnormal or
+// non-finite inputs).
+
+// FP64 bits -> FP32 value, round to nearest even.
+__device__ __forceinline__ float f64bits_to_f32(uint64_t u) {
+  uint32_t t[3];
+  if (cast_terms_int<EncF32, false>(u, 0, t)) return __uint_as_float(t[0]);
+  return __double2float_rn(__longlong_as_double((long long)u));
+}
+
 __global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
                                   const double* __restrict__ b, int64_t m, int64_t n,
                                   unsigned long long* cmax, float* __restrict__ a32, int64_t lda32,
@@ -82,23 +94,28 @@ __global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
   const int64_t r0 = blockIdx.x * rows_per_block;
   const int64_t r1 = min(m, r0 + rows_per_block);
   const int64_t cend = a32 ? max(n + 1, lda32) : n + 1;
+  const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
+  const uint64_t* bu = reinterpret_cast<const uint64_t*>(b);
+  constexpr uint64_t kAbs = 0x7FFFFFFFFFFFFFFFull;
+  // |v| as FP64 bits is monotone in |v| for non-NaN values: the column maximum
+  // is an integer maximum
   for (int64_t c = threadIdx.x; c < cend; c += blockDim.x) {
-    double mx = 0.0;
+    uint64_t mx = 0;
     if (c < n) {
 #pragma unroll 4
       for (int64_t i = r0; i < r1; ++i) {
-        const double v = __ldcs(A + i * lda + c);
-        mx = fmax(mx, fabs(v));
-        if (a32) a32[i * lda32 + c] = (float)v;
+        const uint64_t u = __ldcs(Au + i * lda + c);
+        mx = max(mx, u & kAbs);
+        if (a32) a32[i * lda32 + c] = f64bits_to_f32(u);
       }
     } else if (c == n) {
-      for (int64_t i = r0; i < r1; ++i) mx = fmax(mx, fabs(b[i]));
+      for (int64_t i = r0; i < r1; ++i) mx = max(mx, bu[i] & kAbs);
       if (a32 && c < lda32)
         for (int64_t i = r0; i < r1; ++i) a32[i * lda32 + c] = 0.0f;
     } else {
       for (int64_t i = r0; i < r1; ++i) a32[i * lda32 + c] = 0.0f;
     }
-    if (c <= n && mx > 0.0) atomicMax(cmax + c, (unsigned long long)__double_as_longlong(mx));
+    if (c <= n && mx > 0) atomicMax(cmax + c, (unsigned long long)mx);
   }
 }
 
@@ -131,18 +148,39 @@ cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols
 }
 
 template <int FMT>
+struct FmtEnc;
+template <>
+struct FmtEnc<FMT_BF16> {
+  using T = EncBF16;
+};
+template <>
+struct FmtEnc<FMT_BF16X3> {
+  using T = EncBF16;
+};
+template <>
+struct FmtEnc<FMT_F16> {
+  using T = EncF16;
+};
+template <>
+struct FmtEnc<FMT_E4M3> {
+  using T = EncE4M3;
+};
+
+template <int FMT>
 __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
                                       const double* __restrict__ b, int64_t m, int64_t n,
                                       const int* __restrict__ kexp, void* __restrict__ Bt,
                                       int64_t ldb, int64_t plane_rows) {
-  __shared__ double tile[32][33];
+  __shared__ uint64_t tile[32][33];
   const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
+  const uint64_t* bu = reinterpret_cast<const uint64_t*>(b);
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t j = j0 + r, c = c0 + threadIdx.x;
-    double v = 0.0;
+    uint64_t v = 0;
     if (j < m) {
-      if (c < n) v = A[j * lda + c];
-      else if (c == n) v = b[j];
+      if (c < n) v = __ldcs(Au + j * lda + c);
+      else if (c == n) v = bu[j];
     }
     tile[r][threadIdx.x] = v;
   }
@@ -150,23 +188,34 @@ __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t c = c0 + r, j = j0 + threadIdx.x;
     if (c <= n && j < m) {
-      const double v = ldexp(tile[threadIdx.x][r], kexp[c]);
+      const uint64_t u = tile[threadIdx.x][r];
+      const int k = kexp[c];
       if constexpr (FMT == FMT_F32) {
+        const double v = ldexp(__longlong_as_double((long long)u), k);
         reinterpret_cast<float*>(Bt)[c * ldb + j] = __double2float_rn(v);
-      } else if constexpr (FMT == FMT_BF16X3) {
-        // three BF16 terms hi + lo + lo2 (differences exact in FP64), one plane each
-        uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
-        const uint32_t hi = round_f64<FMT_BF16>(v);
-        const double r1 = v - bits_to_double<FMT_BF16>(hi);
-        const uint32_t lo = round_f64<FMT_BF16>(r1);
-        const uint32_t lo2 = round_f64<FMT_BF16>(r1 - bits_to_double<FMT_BF16>(lo));
-        P[c * ldb + j] = (uint16_t)hi;
-        P[(plane_rows + c) * ldb + j] = (uint16_t)lo;
-        P[(2 * plane_rows + c) * ldb + j] = (uint16_t)lo2;
-      } else if constexpr (FMT == FMT_E4M3) {
-        reinterpret_cast<uint8_t*>(Bt)[c * ldb + j] = (uint8_t)round_f64<FMT>(v);
       } else {
-        reinterpret_cast<uint16_t*>(Bt)[c * ldb + j] = (uint16_t)round_f64<FMT>(v);
+        uint32_t t[3];
+        if (!cast_terms_int<typename FmtEnc<FMT>::T, FMT == FMT_BF16X3>(u, k, t)) {   // FP64 definition
+          const double v = ldexp(__longlong_as_double((long long)u), k);
+          constexpr int G = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;
+          t[0] = round_f64<G>(v);
+          if constexpr (FMT == FMT_BF16X3) {
+            const double r1 = v - bits_to_double<G>(t[0]);
+            t[1] = round_f64<G>(r1);
+            t[2] = round_f64<G>(r1 - bits_to_double<G>(t[1]));
+          }
+        }
+        if constexpr (FMT == FMT_BF16X3) {
+          // three BF16 terms hi + lo + lo2, one plane each
+          uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
+          P[c * ldb + j] = (uint16_t)t[0];
+          P[(plane_rows + c) * ldb + j] = (uint16_t)t[1];
+          P[(2 * plane_rows + c) * ldb + j] = (uint16_t)t[2];
+        } else if constexpr (FMT == FMT_E4M3) {
+          reinterpret_cast<uint8_t*>(Bt)[c * ldb + j] = (uint8_t)t[0];
+        } else {
+          reinterpret_cast<uint16_t*>(Bt)[c * ldb + j] = (uint16_t)t[0];
+        }
       }
     }
   }
