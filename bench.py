@@ -351,6 +351,8 @@ def run_ours(args):
             "converged": bool(last["ir_converged"]),
             "iterations": {"lsqr": last["lsqr_its"], "ir": last["ir_its"],
                            "fgmres_total": last["gmres_its_total"], "escalated": last["escalated"]},
+            "ir_hist": {"dx_rel": last["ir_dx_hist"], "dr_rel": last["ir_dr_hist"],
+                        "gmres_its": last["gmres_its"], "gmres_relres": last["gmres_relres"]},
             "stage_ms": last["stage_ms"], "kappa_R_est": last["kappa_R_est"],
             "sketch": sketch, "passes": passes,
             "fp64_path": {"tts_ms": fp64_ms, "lsqr_its": info64.lsqr_its, "tol": tol64, "status": st64,

@@ -93,7 +93,8 @@ typedef struct lsq_opts {
   int32_t ir_stop;        /* refinement stop rule, with dx_i, dr_i the corrections of step i:
                              0: ||dx_i|| <= u||x|| and ||dr_i|| <= u||r||, or (i >= 1) the
                                 contraction estimate rho_i = ||dx_i||/||dx_{i-1}|| < 1/2 with
-                                rho_i ||dx_i|| <= u||x|| (and the same for r);
+                                rho_i ||dx_i|| <= 4u||x|| (and the same for r), the
+                                estimated remaining error at the 4u level of Sec. 5;
                              1: the first test only */
   int32_t timing;         /* 1: time every sketch GEMM and pass launch with CUDA events
                              on the handle's stream (info->kern_ms / kern_launches) */

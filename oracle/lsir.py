@@ -20,8 +20,9 @@ are <= 4u; ``lsir`` does exactly that when (xstar, rstar) are given.
 Otherwise it uses the computable rule of this build: stop after step i if
 ||dx_i|| <= u ||x_{i+1}|| and ||dr_i|| <= u ||r_{i+1}||, or if (i >= 1) the
 contraction estimates rho = ||d_i|| / ||d_{i-1}|| are below 1/2 and
-rho ||dx_i|| <= u ||x_{i+1}||, rho ||dr_i|| <= u ||r_{i+1}|| (the next
-correction, i.e. the remaining error, is then below u).
+rho ||dx_i|| <= 4u ||x_{i+1}||, rho ||dr_i|| <= 4u ||r_{i+1}|| (the next
+correction, i.e. the remaining error, is then within the 4u the paper asks
+of the forward errors).
 
 Here u_r is the correctly rounded residual of ``exact.residual_aug`` when
 ``ur='exact'`` and plain FP64 otherwise; h_i is solved in FP64.
@@ -68,7 +69,7 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
             if not done and prev is not None:
                 rx = ndx / prev[0] if prev[0] > 0 else 1.0
                 rr = ndr / prev[1] if prev[1] > 0 else 1.0
-                done = rx < 0.5 and rr < 0.5 and rx * ndx <= u * nx and rr * ndr <= u * nr
+                done = rx < 0.5 and rr < 0.5 and rx * ndx <= 4 * u * nx and rr * ndr <= 4 * u * nr
             prev = (ndx, ndr)
         if done:
             converged = True

@@ -55,21 +55,19 @@ cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n
 cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s);
 cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
                              int nblk, cudaStream_t s);
-// Partial dots of w with V[:, 0..j]; with az, first forms w_top = V[:m, j] + az.
+// Classical Gram-Schmidt pass of an Arnoldi step (one of two).  mdot: h = V[:, 0..j]^T w
+// (with az, first forms w_top = V[:m, j] + az), H[:, j] += h.  axpy: w -= V h; after the
+// first pass it decides whether the second pass runs (Kahan: iff ||w'||^2 < (||w'||^2 +
+// ||h||^2) / 2) and, when it does not, or after the second pass, finishes the step
+// (h_{j+1,j} = ||w||, Givens rotation, residual estimate, j += 1).  `cnt` is a device
+// counter that is zero between launches (each launch leaves it zero).
 template <typename TAZ>
 cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
                            int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m,
-                           bool second = false);
-cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
-                           int ldh, cudaStream_t s, bool second = false);
+                           bool second, unsigned* cnt, double* h, double* H, int ldh);
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
-                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s,
-                           bool second = false);
-// Second-pass test: reorthogonalise iff ||w'||^2 < (||w'||^2 + ||h||^2) / 2.
-cudaError_t launch_gm_reorth_test(const double* sq_partial, int nblk, const double* h, GmState* st,
-                                  cudaStream_t s);
-cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
-                             double* cs, double* sn, double* g, cudaStream_t s);
+                           GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second,
+                           unsigned* cnt, double* H, int ldh, double* cs, double* sn, double* g);
 cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
                              float* v32, int64_t m, int nblk, cudaStream_t s);
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,

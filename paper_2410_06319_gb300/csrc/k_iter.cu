@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) pass_bulk_kernel(BulkArgs<T> 
   if (warp == kBulkRows) {
     // ---------------- producer
     if (lane == 0) {
+      const uint64_t pol = l2_policy_evict_first();   // A is read once per pass
       for (int it = 0; it < nst; ++it) {
         const int slot = it % p.stages;
         const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
@@ -281,8 +282,8 @@ __global__ void __launch_bounds__(kBulkThreads, 1) pass_bulk_kernel(BulkArgs<T> 
         const int rows = (int)min((int64_t)kBulkRows, r1 - row0);
         const uint32_t bytes = (uint32_t)(rows * p.lda * sizeof(T));
         mbar_arrive_expect_tx(full0 + 8 * slot, bytes);
-        bulk_load(smem_u32(bulk_smem + (size_t)slot * stage_bytes), p.A + row0 * p.lda, bytes,
-                  full0 + 8 * slot);
+        bulk_load_hint(smem_u32(bulk_smem + (size_t)slot * stage_bytes), p.A + row0 * p.lda, bytes,
+                       full0 + 8 * slot, pol);
       }
     }
   } else {
@@ -785,7 +786,7 @@ __global__ void lsqr_colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n
 // alpha v = vt - beta v, plane rotation, z += (phi/rho) w, w = v - (theta/rho) w,
 // stopping tests ; then t = R^-1 v for the next pass.
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kTrsvThreads)
     lsqr_step_kernel(Tri<T> f, const T* __restrict__ s, T* __restrict__ v, T* __restrict__ w,
                      T* __restrict__ z, T* __restrict__ t, LsqrState* st, bool init) {
   if (!init && st->done) return;
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(1024)
   const int n = (int)f.n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = s[i];
   __syncthreads();
-  block_trsv<T, false>(f.L, f.ld, f.DL, n, xs, step_buf);       // xs = R^-T s
+  if (!block_trsv<T, false>(f.L, f.ld, f.DL, n, xs, step_buf, f.err)) return;   // xs = R^-T s
   const double beta = st->beta;
   double ss = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(1024)
     xs[i] = vn;
   }
   __syncthreads();
-  block_trsv<T, true>(f.R, f.ld, f.DU, n, xs, step_buf);        // t = R^-1 v
+  if (!block_trsv<T, true>(f.R, f.ld, f.DU, n, xs, step_buf, f.err)) return;    // t = R^-1 v
   for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = xs[i];
 }
 
@@ -880,7 +881,7 @@ cudaError_t launch_lsqr_step(const Tri<T>& f, const T* s, T* v, T* w, T* z, T* t
   const size_t smem = TrsvSmem<T>::bytes;
   cudaError_t e = allow_dyn_smem(lsqr_step_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  lsqr_step_kernel<T><<<1, 1024, smem, strm>>>(f, s, v, w, z, t, st, init);
+  lsqr_step_kernel<T><<<1, kTrsvThreads, smem, strm>>>(f, s, v, w, z, t, st, init);
   return cudaGetLastError();
 }
 template cudaError_t launch_lsqr_colsum<float>(const float*, int, int64_t, const double*, LsqrState*, bool, float*, cudaStream_t);
@@ -962,10 +963,28 @@ __global__ void gm_init_kernel(const double* sq_partial, int nblk, GmState* st, 
 
 // partial dots of w with V[:, 0..j] over a row range: Dp[b][c]; one warp per
 // column (no block-wide barrier per column), w's range cached in L1.
+// The Arnoldi kernels end with a "last block" step: every block publishes its
+// partial results, counts itself done on a device counter, and the block that
+// finishes last (it sees every other block's partials) performs the small
+// reduction in a fixed order, then resets the counter.  No block waits for
+// another, and the results do not depend on block scheduling.
+__device__ __forceinline__ bool last_block_done(unsigned* cnt) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// Partial dot products Dp[b][c] = V[:, c]^T w over block b's rows for c <= j;
+// the last block sums them: h[c] = sum_b Dp[b][c], H[c][j] += h[c].
 template <typename TAZ>
 __global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, double* __restrict__ w,
                                int64_t len, const GmState* st, int maxc, double* Dp,
-                               const TAZ* __restrict__ az, int64_t m, bool second) {
+                               const TAZ* __restrict__ az, int64_t m, bool second, unsigned* cnt,
+                               double* h, double* H, int ldh) {
   if (st->done || (second && !st->reorth)) return;
   const int ncols = st->j + 1;
   const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
@@ -983,94 +1002,33 @@ __global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, double*
     s = warp_sum(s);
     if (lane == 0) Dp[(int64_t)blockIdx.x * maxc + c] = s;
   }
-}
-
-// h[c] = sum_b Dp[b][c] ; H[c][j] += h[c]   (one 32 x 32 block, fixed order)
-__global__ void gm_hsum_kernel(const double* Dp, int nblk, int maxc, GmState* st, double* h,
-                               double* H, int ldh, bool second) {
-  if (st->done || (second && !st->reorth)) return;
-  __shared__ double part[32][33];
-  const int ncols = st->j + 1;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int c0 = 0; c0 < ncols; c0 += 32) {
-    const int c = c0 + tx;
-    double s = 0.0;
-    if (c < ncols)
-      for (int b = ty; b < nblk; b += 32) s += Dp[(int64_t)b * maxc + c];
-    part[ty][tx] = s;
-    __syncthreads();
-    if (ty == 0 && c < ncols) {
-      double t = 0.0;
-      for (int k = 0; k < 32; ++k) t += part[k][tx];
+  if (!last_block_done(cnt)) return;
+  const int nblk = gridDim.x;
+  for (int c = warp; c < ncols; c += nw) {
+    double t = 0.0;
+    for (int b = lane; b < nblk; b += 32) t += __ldcg(Dp + (int64_t)b * maxc + c);
+    t = warp_sum(t);
+    if (lane == 0) {
       h[c] = t;
       H[(int64_t)st->j * ldh + c] += t;
     }
-    __syncthreads();
   }
+  if (threadIdx.x == 0) *cnt = 0u;
 }
 
-// w[i] -= sum_c V[c][i] h[c] ; optional partial ||w||^2
-__global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
-                               double* __restrict__ w, int64_t len, const GmState* st,
-                               double* sq_partial, bool second) {
-  if (st->done || (second && !st->reorth)) return;
-  __shared__ double hs[128];
-  __shared__ double red[33];
-  const int ncols = st->j + 1;
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = h[c];
-  __syncthreads();
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = w[i];
-    for (int c = 0; c < ncols; ++c) acc -= V[(int64_t)c * ld + i] * hs[c];
-    w[i] = acc;
-    s += acc * acc;
-  }
-  if (sq_partial) {
-    s = block_sum_d(s, red);
-    if (threadIdx.x == 0) sq_partial[blockIdx.x] = s;
-  }
-}
-
-// Kahan's "twice is enough" test after the first Gram-Schmidt pass.
-__global__ void gm_reorth_test_kernel(const double* sq_partial, int nblk, const double* h, GmState* st) {
-  if (st->done) return;
-  __shared__ double red[33];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
-  s = block_sum_d(s, red);
-  double hh = 0.0;
-  for (int c = threadIdx.x; c <= st->j; c += blockDim.x) hh += h[c] * h[c];
-  hh = block_sum_d(hh, red);
-  if (threadIdx.x == 0) {
-    const int need = (s < 0.5 * (s + hh)) ? 1 : 0;
-    st->reorth = need;
-    st->nreorth += need;
-  }
-}
-cudaError_t launch_gm_reorth_test(const double* sq_partial, int nblk, const double* h, GmState* st,
-                                  cudaStream_t s) {
-  gm_reorth_test_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, h, st);
-  return cudaGetLastError();
-}
-
-// h_{j+1,j} = ||w|| ; Givens rotations on column j ; residual estimate ; j++.
-__global__ void gm_finish_kernel(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
-                                 double* cs, double* sn, double* g) {
-  if (st->done) return;
-  __shared__ double red[33];
+// h_{j+1,j} = sqrt(s) ; Givens rotations on column j ; residual estimate ; j++.
+// One block (the last block of the Gram-Schmidt update).
+__device__ void gm_finish_block(double s, GmState* st, double* H, int ldh, double* cs, double* sn,
+                                double* g) {
   __shared__ double hcs[130], css[130], sns[130];
   const int j = st->j;
   double* hc = H + (int64_t)j * ldh;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    hcs[i] = hc[i];
+    hcs[i] = __ldcg(hc + i);
     css[i] = cs[i];
     sns[i] = sn[i];
   }
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq_partial[b];
-  s = block_sum_d(s, red);   // contains the barriers that publish hcs/css/sns
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double hn = sqrt(s);
     hcs[j + 1] = hn;
@@ -1093,6 +1051,50 @@ __global__ void gm_finish_kernel(const double* sq_partial, int nblk, GmState* st
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = hcs[i];
+}
+
+// w[i] -= sum_c V[c][i] h[c] with partial ||w||^2 per block; the last block then
+// (first pass) applies Kahan's "twice is enough" test -- the second pass is
+// needed when the update lost more than half of ||w||^2 -- and, when no second
+// pass follows, or (second pass) always, finishes the Arnoldi step.
+__global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
+                               double* __restrict__ w, int64_t len, GmState* st, double* sq_partial,
+                               bool second, unsigned* cnt, double* H, int ldh, double* cs, double* sn,
+                               double* g) {
+  if (st->done || (second && !st->reorth)) return;
+  __shared__ double hs[128];
+  __shared__ double red[33];
+  const int ncols = st->j + 1;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int c = 0; c < ncols; ++c) acc -= V[(int64_t)c * ld + i] * hs[c];
+    w[i] = acc;
+    s += acc * acc;
+  }
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) sq_partial[blockIdx.x] = s;
+  if (!last_block_done(cnt)) return;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(sq_partial + b);
+  t = block_sum_d(t, red);
+  bool finish = true;
+  if (!second) {
+    double hh = 0.0;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hh += hs[c] * hs[c];
+    hh = block_sum_d(hh, red);
+    const int need = (t < 0.5 * (t + hh)) ? 1 : 0;
+    if (threadIdx.x == 0) {
+      st->reorth = need;
+      st->nreorth += need;
+    }
+    finish = !need;
+  }
+  if (finish) gm_finish_block(t, st, H, ldh, cs, sn, g);
+  if (threadIdx.x == 0) *cnt = 0u;
 }
 
 // V[:, j] = w * inv_h  (j read after gm_finish incremented it)
@@ -1163,27 +1165,20 @@ cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, doub
 template <typename TAZ>
 cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
                            int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m,
-                           bool second) {
-  gm_mdot_kernel<TAZ><<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp, az, m, second);
+                           bool second, unsigned* cnt, double* h, double* H, int ldh) {
+  gm_mdot_kernel<TAZ><<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp, az, m, second, cnt, h, H, ldh);
   return cudaGetLastError();
 }
 template cudaError_t launch_gm_mdot<float>(const double*, int64_t, double*, int64_t, const GmState*, int,
-                                           double*, int, cudaStream_t, const float*, int64_t, bool);
+                                           double*, int, cudaStream_t, const float*, int64_t, bool,
+                                           unsigned*, double*, double*, int);
 template cudaError_t launch_gm_mdot<double>(const double*, int64_t, double*, int64_t, const GmState*, int,
-                                            double*, int, cudaStream_t, const double*, int64_t, bool);
-cudaError_t launch_gm_hsum(const double* Dp, int nblk, int maxc, GmState* st, double* h, double* H,
-                           int ldh, cudaStream_t s, bool second) {
-  gm_hsum_kernel<<<1, dim3(32, 32), 0, s>>>(Dp, nblk, maxc, st, h, H, ldh, second);
-  return cudaGetLastError();
-}
+                                            double*, int, cudaStream_t, const double*, int64_t, bool,
+                                            unsigned*, double*, double*, int);
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
-                           const GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second) {
-  gm_axpy_kernel<<<nblk, 256, 0, s>>>(V, ld, h, w, len, st, sq_partial, second);
-  return cudaGetLastError();
-}
-cudaError_t launch_gm_finish(const double* sq_partial, int nblk, GmState* st, double* H, int ldh,
-                             double* cs, double* sn, double* g, cudaStream_t s) {
-  gm_finish_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, st, H, ldh, cs, sn, g);
+                           GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second,
+                           unsigned* cnt, double* H, int ldh, double* cs, double* sn, double* g) {
+  gm_axpy_kernel<<<nblk, 256, 0, s>>>(V, ld, h, w, len, st, sq_partial, second, cnt, H, ldh, cs, sn, g);
   return cudaGetLastError();
 }
 cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,

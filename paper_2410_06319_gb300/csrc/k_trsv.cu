@@ -8,21 +8,19 @@
 // followed by a rank-32 update of the remaining rows by all threads; there is
 // no serial substitution chain inside a block.  The matrices are R (upper) and
 // L = R^T (lower), both column-major, so every update reads contiguous column
-// segments; the next step's segments and diagonal inverse are prefetched into
-// L1 while the current step runs.
+// segments, which cp.async stages into shared memory ahead of the step that
+// uses them (trsv.cuh).
 #include "common.cuh"
 #include "kernels.h"
 #include "trsv.cuh"
 
 namespace lsq {
 
-constexpr int kTrsvThreads = 1024;
-
 template <typename T, typename TIN, typename TOUT, bool UPPER>
 __global__ void __launch_bounds__(kTrsvThreads)
     trsv_kernel(const T* __restrict__ M, int64_t ld, const T* __restrict__ D, int n,
                 const TIN* __restrict__ y, double yscale, TOUT* __restrict__ x, const int* done,
-                const int* jp, int64_t ys, int64_t xstr) {
+                const int* jp, int64_t ys, int64_t xstr, int* err) {
   if (done && *done) return;
   if (jp) {  // column j of a basis: offsets read on the device (graph-replayable)
     const int64_t j = *jp;
@@ -33,7 +31,7 @@ __global__ void __launch_bounds__(kTrsvThreads)
   extern __shared__ __align__(16) unsigned char trsv_buf[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (T)((double)y[i] * yscale);
   __syncthreads();
-  block_trsv<T, UPPER>(M, ld, D, n, xs, trsv_buf);
+  if (!block_trsv<T, UPPER>(M, ld, D, n, xs, trsv_buf, err)) return;
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (TOUT)xs[i];
 }
 
@@ -46,12 +44,12 @@ cudaError_t launch_trsv(bool upper, const Tri<T>& f, const TIN* y, double yscale
     auto kern = trsv_kernel<T, TIN, TOUT, true>;
     cudaError_t e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<1, kTrsvThreads, smem, st>>>(f.R, f.ld, f.DU, (int)f.n, y, yscale, x, done, jp, ys, xstr);
+    kern<<<1, kTrsvThreads, smem, st>>>(f.R, f.ld, f.DU, (int)f.n, y, yscale, x, done, jp, ys, xstr, f.err);
   } else {
     auto kern = trsv_kernel<T, TIN, TOUT, false>;
     cudaError_t e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<1, kTrsvThreads, smem, st>>>(f.L, f.ld, f.DL, (int)f.n, y, yscale, x, done, jp, ys, xstr);
+    kern<<<1, kTrsvThreads, smem, st>>>(f.L, f.ld, f.DL, (int)f.n, y, yscale, x, done, jp, ys, xstr, f.err);
   }
   return cudaGetLastError();
 }

@@ -77,6 +77,7 @@ struct Tri {
   const T* DL;
   int64_t n;
   int64_t ld;
+  int* err = nullptr;   // device error word for bounded waits (may be null)
 };
 inline int64_t tri_ld(int64_t n, int elem_bytes) {
   const int64_t q = 16 / elem_bytes;

@@ -14,6 +14,8 @@
 
 namespace lsq {
 
+constexpr int kTrsvThreads = 1024;
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
                    static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
@@ -38,10 +40,11 @@ struct TrsvSmem {
 // Solves in place on xs (shared, n entries): upper -> R x = y, lower -> L x = y.
 // M is column-major with leading dimension ld (a multiple of 16 bytes / sizeof(T)),
 // D holds the 1024-entry inverses of the diagonal blocks, `buf` is TrsvSmem<T>::bytes
-// of shared memory.  Needs blockDim.x == 1024.
+// of shared memory.  Needs blockDim.x == kTrsvThreads.  Has no waits that can run
+// out, so it always returns true (the signature matches solvers that do).
 template <typename T, bool UPPER>
-__device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, const T* __restrict__ D,
-                                           int n, T* xs, unsigned char* buf) {
+__device__ __forceinline__ bool block_trsv(const T* __restrict__ M, int64_t ld, const T* __restrict__ D,
+                                           int n, T* xs, unsigned char* buf, int* /*err*/) {
   constexpr int TR = TrsvSmem<T>::TR;
   constexpr int NBUF = TrsvSmem<T>::NBUF;
   constexpr int VE = 16 / sizeof(T);                 // elements per 16-byte copy
@@ -157,6 +160,7 @@ __device__ __forceinline__ void block_trsv(const T* __restrict__ M, int64_t ld, 
     sl = (sl + 1) % NBUF;
   }
   cp_async_wait<0>();
+  return true;
 }
 
 }  // namespace lsq
