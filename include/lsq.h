@@ -100,7 +100,10 @@ typedef struct lsq_opts {
                              on the handle's stream (info->kern_ms / kern_launches) */
   int32_t no_graph;       /* 1: launch LSQR / FGMRES iteration batches directly instead of
                              replaying cached CUDA graphs (same arithmetic) */
-  int32_t reserved1;
+  int32_t sketch_exact;   /* 1: tensor-core sketch resolves the entries of fl_s(G) whose FP32
+                             estimate lies near a rounding midpoint inside the GEMM pipeline;
+                             0 (default): the GEMM uses the estimates and a correction kernel
+                             adds the exact differences afterwards (same product, faster) */
   double gmres_tol;       /* FGMRES relative-residual tolerance; 0 -> tol */
   double kappa_hint;      /* kappa(A) for the escalation rule; 0 -> estimate from R */
   const double* Y_in;     /* optional device sketch, s x (n+1) column-major (ld = s):

@@ -34,7 +34,7 @@ class Opts(ctypes.Structure):
                 ("ir_maxit", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("no_escalate", ctypes.c_int32), ("no_colscale", ctypes.c_int32),
                 ("ir_stop", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("no_graph", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("no_graph", ctypes.c_int32), ("sketch_exact", ctypes.c_int32),
                 ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
                 ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p)]
 

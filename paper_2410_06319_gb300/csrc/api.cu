@@ -367,7 +367,24 @@ void stage_sketch(Ctx& c, double* Y) {
     if (!encode_bt_tmap(&tm, Bt, fmt, (int64_t)p.nt * rows, c.m, ldb, p.bn / p.nsub, p.rowb))
       throw StatusFail{LSQ_E_UNSUPPORTED};
     float* partial = static_cast<float*>(ws(c.h, "partial", (size_t)p.splits * ncols * p.s_pad * 4));
-    {
+    bool exact = c.o.sketch_exact != 0;
+    if (!exact) {
+      // deferred correction of the near-midpoint entries (timed together with the GEMM)
+      const uint32_t cap = sketch_rec_cap(p);
+      const int64_t lists = sketch_rec_lists(p);
+      auto* rec = static_cast<uint64_t*>(ws(c.h, "sk_rec", (size_t)lists * cap * 8));
+      auto* cnt = static_cast<uint32_t*>(ws(c.h, "sk_cnt", (size_t)lists * 4));
+      int* ovf = static_cast<int*>(ws(c.h, "sk_ovf", 64));
+      CK(cudaMemsetAsync(ovf, 0, 4, c.st));
+      {
+        KernTimer kt(c.h, K_SKETCH, c.o.timing);
+        L(launch_sketch_tc(p, tm, c.seed, partial, c.h->d_err, c.st, rec, cnt, cap));
+        L(launch_sketch_fix(p, c.seed, rec, cnt, cap, c.A, c.lda, c.b, kexp, partial, ovf, c.st));
+      }
+      c.h->launches += 1;
+      exact = read_state<int>(c, ovf) != 0;   // a list overflowed: redo in exact mode
+    }
+    if (exact) {
       KernTimer kt(c.h, K_SKETCH, c.o.timing);
       L(launch_sketch_tc(p, tm, c.seed, partial, c.h->d_err, c.st));
     }

@@ -140,23 +140,38 @@ __device__ __forceinline__ void spec_gauss_pair(uint32_t a, uint32_t b, double& 
 // 1 ulp.  Total 12 ulp = 2^-20.4; kFastRelBound = 2^-19 leaves a 2.6x margin.
 constexpr float kFastRelBound = 0x1p-19f;
 
+// Integer -> FP32 conversions and the rounding to u_s in the FP32 path are
+// written with integer and FMA-pipe instructions: on GB300 the conversion
+// instructions share the narrow FP64 pipe.  The values are the same as the
+// conversions' (round to nearest even).
+//
+// x < 2^32 -> RN(x): both 16-bit halves are exact in FP32, one FMA rounds once.
+__device__ __forceinline__ float u32_to_f32_rn(uint32_t x) {
+  const float hi = __uint_as_float(0x4B000000u | (x >> 16)) - 8388608.0f;
+  const float lo = __uint_as_float(0x4B000000u | (x & 0xFFFFu)) - 8388608.0f;
+  return fmaf(hi, 65536.0f, lo);
+}
+// small non-negative integer field f (f < 2^23) minus `bias`, exactly
+__device__ __forceinline__ float field_minus(uint32_t f, float bias) {
+  return (__uint_as_float(0x4B000000u | f) - 8388608.0f) - bias;
+}
+
 __device__ __forceinline__ float fast_ln_u1(uint32_t a) {
   float z, e;
   if (a >= 0xB504F334u) {  // U1 > sqrt(1/2): ln(1 - V) with V = 1 - U1 exact in integers
-    const float V = (float)(~a) * 0x1p-32f;
+    const float V = u32_to_f32_rn(~a) * 0x1p-32f;
     z = __fdividef(-V, 2.0f - V);
     e = 0.0f;
   } else {
-    const float u = (float)(a + 1u) * 0x1p-32f;
+    const float u = u32_to_f32_rn(a + 1u) * 0x1p-32f;
     const uint32_t ub = __float_as_uint(u);
-    int ex = (int)(ub >> 23) - 127;
     float f = __uint_as_float((ub & 0x007FFFFFu) | 0x3F800000u);
+    e = field_minus(ub >> 23, 127.0f);   // exponent of u (u is normal)
     if (f > 1.41421356f) {
       f *= 0.5f;
-      ex += 1;
+      e += 1.0f;
     }
     z = __fdividef(f - 1.0f, f + 1.0f);
-    e = (float)ex;
   }
   const float w = z * z;
   float p = 1.0f / 13.0f;
@@ -177,7 +192,8 @@ __device__ __forceinline__ void fast_cos_sin_2pi(uint32_t b, float& c, float& s)
     rb -= (1 << 30);
     q = (q + 1u) & 3u;
   }
-  const float phi = ((float)rb * 0x1p-30f) * 1.57079632679489662f;
+  const float rm = u32_to_f32_rn((uint32_t)(rb < 0 ? -rb : rb));   // RN(|rb|), |rb| <= 2^29
+  const float phi = ((rb < 0 ? -rm : rm) * 0x1p-30f) * 1.57079632679489662f;
   const float w = phi * phi;
   float ps = 1.0f / 6227020800.0f;
   ps = fmaf(w, ps, -1.0f / 39916800.0f);
@@ -233,14 +249,43 @@ __device__ __forceinline__ double bits_to_double(uint32_t v) {
   }
 }
 
-// Rounds one FP32 estimate; returns false when the FP64 definition is needed.
+// Rounds one FP32 estimate g to u_s; returns false when the FP64 definition is
+// needed.  The true value lies within d = 2^-19 |g| of g, which is below 32
+// FP32 ulps of g; if the nearest rounding midpoint of u_s (the FP32 pattern
+// whose discarded low bits are exactly one half) is more than 32 ulps away,
+// every value in [g - d, g + d] rounds as g does.  Binade changes within the
+// interval do not matter: the format's values at a power of two are exact.
+// Normal range of u_s only (g below it, or u_s overflow, falls back); `out` is
+// always a finite pattern of the format's width (callers pack it, and the
+// deferred sketch multiplies with it before correcting): fl_s(g), or signed zero
+// below the normal range.
 template <int FMT>
 __device__ __forceinline__ bool round_checked(float g, uint32_t& out) {
-  const float d = kFastRelBound * fabsf(g);
-  const uint32_t lo = round_f32<FMT>(g - d);
-  const uint32_t hi = round_f32<FMT>(g + d);
-  out = round_f32<FMT>(g);
-  return lo == hi;
+  const uint32_t b = __float_as_uint(g);
+  const uint32_t sg = b >> 31, mag = b & 0x7FFFFFFFu;
+  if constexpr (FMT == FMT_BF16) {   // 7 fraction bits: 16 low bits dropped
+    const int off = (int)(mag & 0xFFFFu) - 0x8000;
+    out = (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+    return (off > 32 || off < -32) && mag >= 0x00800000u;
+  } else if constexpr (FMT == FMT_F16) {   // 10 fraction bits, normal for |g| >= 2^-14
+    if (mag < 0x38800000u) {   // below the normal range: signed zero, exact value later
+      out = sg << 15;
+      return false;
+    }
+    const int off = (int)(mag & 0x1FFFu) - 0x1000;
+    const uint32_t r = mag + 0xFFFu + ((mag >> 13) & 1u);
+    out = ((sg << 15) | ((r >> 13) - (112u << 10))) & 0xFFFFu;
+    return (off > 32 || off < -32) && r < 0x47800000u;
+  } else {   // E4M3: 3 fraction bits, normal for 2^-6 <= |g|, finite below 2^8 here
+    if (mag < 0x3C800000u) {   // below the normal range: signed zero, exact value later
+      out = sg << 7;
+      return false;
+    }
+    const int off = (int)(mag & 0xFFFFFu) - 0x80000;
+    const uint32_t r = mag + 0x7FFFFu + ((mag >> 20) & 1u);
+    out = ((sg << 7) | ((r >> 20) - (120u << 3))) & 0xFFu;
+    return (off > 32 || off < -32) && r < 0x43800000u;
+  }
 }
 
 // FP32 evaluation of one (a, b) word pair; false when the FP64 definition is

@@ -166,6 +166,22 @@ struct FmtEnc<FMT_E4M3> {
   using T = EncE4M3;
 };
 
+// The terms of fl_s(2^k x) (x given by its FP64 bits u): integer path, else the
+// FP64 definition (round-to-odd into FP32, then to the format).
+template <int FMT>
+__device__ __forceinline__ void cast_bits(uint64_t u, int k, uint32_t (&t)[3]) {
+  if (!cast_terms_int<typename FmtEnc<FMT>::T, FMT == FMT_BF16X3>(u, k, t)) {
+    const double v = ldexp(__longlong_as_double((long long)u), k);
+    constexpr int G = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;
+    t[0] = round_f64<G>(v);
+    if constexpr (FMT == FMT_BF16X3) {
+      const double r1 = v - bits_to_double<G>(t[0]);
+      t[1] = round_f64<G>(r1);
+      t[2] = round_f64<G>(r1 - bits_to_double<G>(t[1]));
+    }
+  }
+}
+
 template <int FMT>
 __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
                                       const double* __restrict__ b, int64_t m, int64_t n,
@@ -195,16 +211,7 @@ __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
         reinterpret_cast<float*>(Bt)[c * ldb + j] = __double2float_rn(v);
       } else {
         uint32_t t[3];
-        if (!cast_terms_int<typename FmtEnc<FMT>::T, FMT == FMT_BF16X3>(u, k, t)) {   // FP64 definition
-          const double v = ldexp(__longlong_as_double((long long)u), k);
-          constexpr int G = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;
-          t[0] = round_f64<G>(v);
-          if constexpr (FMT == FMT_BF16X3) {
-            const double r1 = v - bits_to_double<G>(t[0]);
-            t[1] = round_f64<G>(r1);
-            t[2] = round_f64<G>(r1 - bits_to_double<G>(t[1]));
-          }
-        }
+        cast_bits<FMT>(u, k, t);
         if constexpr (FMT == FMT_BF16X3) {
           // three BF16 terms hi + lo + lo2, one plane each
           uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
@@ -253,8 +260,11 @@ constexpr int kSkGenThreads = kSkGenWarps * 32;
 constexpr int kSkFixWarps = 2;                // resolve the FP64 fallbacks of a stage
 constexpr int kSkFixThreads = kSkFixWarps * 32;
 constexpr int kSkFixFirst = 2 + kSkGenWarps;
-constexpr int kSkThreads = (2 + kSkGenWarps + kSkFixWarps) * 32;
 constexpr int kSkQMax = 256;                 // FP64 fallbacks queued per stage
+// threads of the kernel: TMA + MMA warps, generators, and (exact mode) fixers
+__host__ __device__ constexpr int sk_threads(bool defer) {
+  return (2 + kSkGenWarps + (defer ? 0 : kSkFixWarps)) * 32;
+}
 
 struct SketchTcArgs {
   int64_t s, m, ncols, kchunk, s_pad;
@@ -262,6 +272,11 @@ struct SketchTcArgs {
   uint32_t k0, k1;
   float* partial;
   int* err;
+  // deferred mode: per generator warp a list of the (a, b) pairs whose FP32
+  // estimate was too close to a rounding midpoint, packed (data row << 16 | sketch row)
+  uint64_t* rec;
+  uint32_t* rec_cnt;
+  uint32_t rec_cap;
 };
 
 __device__ __forceinline__ void fix_barrier() {
@@ -289,8 +304,14 @@ __device__ __forceinline__ uint32_t swz_chunk(int row, int kc) {
 }
 
 // Y partial = fl_s(G)[128 rows] x (sum over NT planes of Bt)[bn columns] over one split of m.
-template <int FMT, int STAGES, int ROWB, int NT>
-__global__ void __launch_bounds__(kSkThreads, 1)
+// Exact mode (DEFER = false): pairs whose FP32 estimate is too close to a rounding
+// midpoint of u_s are queued per stage and replaced by the FP64 definition by the
+// fixer warps before the stage is multiplied.  Deferred mode: the stage is
+// multiplied with the FP32 estimates at once and those pairs are recorded;
+// sketch_fix_kernel then evaluates them in FP64 and adds (fl_s(G) - estimate) times
+// the matching rows of A_s to the partials, which gives the same product.
+template <int FMT, int STAGES, int ROWB, int NT, bool DEFER>
+__global__ void __launch_bounds__(sk_threads(DEFER), 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap tmB, const SketchTcArgs a) {
   constexpr int GF = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;   // format of the sketch operand
   constexpr int EB = (GF == FMT_E4M3) ? 1 : 2;                // bytes per element
@@ -325,7 +346,7 @@ __global__ void __launch_bounds__(kSkThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) {
-      mbar_init(full0 + 8 * st, kSkFixWarps + 1);
+      mbar_init(full0 + 8 * st, DEFER ? 1 + kSkGenWarps : kSkFixWarps + 1);
       mbar_init(empty0 + 8 * st, 1);
       mbar_init(genned0 + 8 * st, kSkGenWarps);
       mbar_init(fixed0 + 8 * st, kSkFixWarps);
@@ -394,11 +415,14 @@ __global__ void __launch_bounds__(kSkThreads, 1)
   } else if (warp < kSkFixFirst) {
     // ---------------- generator warps: fl_s(G) tile, 128 rows x BK columns
     const int g = threadIdx.x - 64;
+    uint32_t wcnt = 0;   // deferred mode: pairs recorded by this warp
+    const int64_t cta = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    uint64_t* rec_w = DEFER ? a.rec + (cta * kSkGenWarps + (warp - 2)) * (int64_t)a.rec_cap : nullptr;
     for (int ks = 0; ks < nk; ++ks) {
       const int st = ks % STAGES;
       const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
       if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
-      if (!mbar_wait(fixed0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
+      if (!DEFER && !mbar_wait(fixed0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
       uint8_t* S = smem + st * stage_bytes;
       uint32_t* qb = qbuf + st * (kSkQMax * 3);
       const int64_t kbase = k_begin + (int64_t)ks * BK;
@@ -413,7 +437,24 @@ __global__ void __launch_bounds__(kSkThreads, 1)
           uint32_t e0, o0, e1, o1;
           const bool ok0 = gauss_pair_fast<GF>(x.x, x.y, e0, o0);
           const bool ok1 = gauss_pair_fast<GF>(x.z, x.w, e1, o1);
-          if (!ok0 || !ok1) {
+          if constexpr (DEFER) {
+            // record the uncertain pairs, in lane order (deterministic lists)
+            const unsigned act = __activemask();
+            const unsigned m0 = __ballot_sync(act, !ok0), m1 = __ballot_sync(act, !ok1);
+            if ((m0 | m1) != 0u) {
+              const unsigned lt = (1u << lane) - 1u;
+              const uint64_t j0 = (q0 + (uint64_t)h) * 4u;
+              if (!ok0) {
+                const uint32_t x0 = wcnt + __popc(m0 & lt);
+                if (x0 < a.rec_cap) rec_w[x0] = (j0 << 16) | i;
+              }
+              if (!ok1) {
+                const uint32_t x1 = wcnt + __popc(m0) + __popc(m1 & lt);
+                if (x1 < a.rec_cap) rec_w[x1] = ((j0 + 2u) << 16) | i;
+              }
+              wcnt += __popc(m0) + __popc(m1);
+            }
+          } else if (!ok0 || !ok1) {
 #pragma unroll
             for (int p2 = 0; p2 < 2; ++p2) {
               if (p2 == 0 ? ok0 : ok1) continue;
@@ -441,9 +482,10 @@ __global__ void __launch_bounds__(kSkThreads, 1)
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(genned0 + 8 * st);
+      if (lane == 0) mbar_arrive(DEFER ? full0 + 8 * st : genned0 + 8 * st);
     }
-  } else {
+    if (DEFER && lane == 0) a.rec_cnt[cta * kSkGenWarps + (warp - 2)] = wcnt;
+  } else if constexpr (!DEFER) {
     // ---------------- fixer warps: FP64 definition for the queued pairs of a stage,
     // overlapping the generation of the next stage
     const int fx = threadIdx.x - kSkFixFirst * 32;
@@ -572,16 +614,24 @@ bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int6
 template <int FMT, int STAGES, int ROWB, int NT>
 static cudaError_t launch_tc_inst(const SketchPlan& p, const CUtensorMap& tm, const SketchTcArgs& a,
                                   cudaStream_t st) {
-  auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT>;
-  cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
-  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
-  kern<<<grid, kSkThreads, p.smem, st>>>(tm, a);
+  if (a.rec) {
+    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, true>;
+    cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, sk_threads(true), p.smem, st>>>(tm, a);
+  } else {
+    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, false>;
+    cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, sk_threads(false), p.smem, st>>>(tm, a);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_t seed,
-                             float* partial, int* err, cudaStream_t st) {
+                             float* partial, int* err, cudaStream_t st, uint64_t* rec,
+                             uint32_t* rec_cnt, uint32_t rec_cap) {
   SketchTcArgs a;
   a.s = p.s;
   a.m = p.m;
@@ -598,6 +648,9 @@ cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_
   a.k1 = (uint32_t)(seed >> 32);
   a.partial = partial;
   a.err = err;
+  a.rec = rec;
+  a.rec_cnt = rec_cnt;
+  a.rec_cap = rec_cap;
   const bool four = p.stages == 4;
   switch (p.fmt) {
     case FMT_F16: return four ? launch_tc_inst<FMT_F16, 4, 128, 1>(p, tm, a, st)
@@ -610,6 +663,171 @@ cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_
                                  : launch_tc_inst<FMT_BF16X3, 2, 64, 3>(p, tm, a, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// ============================================================ deferred correction
+// One block per sketch CTA (same grid): the pairs recorded by its generator warps,
+// in list order, 512 at a time.  Phase 1 (one pair per thread, full warps on the
+// FP64 pipe): d = fl_s(G) - fl_s(g32) for both entries of the pair; pairs with
+// d != 0 are compacted in order.  Phase 2 (one column per thread): for each kept
+// pair, partial[i][c] += d * A_s[j][c], with A_s[j][c] recomputed from A by the
+// cast's own rounding.  Every partial entry is updated by one thread in a fixed
+// order, so the result is deterministic.
+constexpr int kFixThreads = 512;
+
+struct SketchFixArgs {
+  int64_t s, m, n, ncols, s_pad, lda;
+  int bn;
+  uint32_t k0, k1, cap;
+  const uint64_t* rec;
+  const uint32_t* rec_cnt;
+  const double* A;
+  const double* b;
+  const int* kexp;
+  float* partial;
+  int* overflow;
+};
+
+struct FixRec {
+  uint32_t i, pad;
+  uint64_t j0;
+  double de, dodd;
+};
+
+template <int FMT>
+__global__ void __launch_bounds__(kFixThreads)
+    sketch_fix_kernel(const SketchFixArgs f) {
+  constexpr int GF = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;
+  __shared__ uint32_t off[kSkGenWarps + 1];
+  __shared__ int ovf;
+  __shared__ int wsum[kFixThreads / 32];
+  __shared__ FixRec kept[kFixThreads];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t cta = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+  if (tid == 0) {
+    uint32_t o = 0;
+    int bad = 0;
+    for (int w = 0; w < kSkGenWarps; ++w) {
+      const uint32_t c = f.rec_cnt[cta * kSkGenWarps + w];
+      if (c > f.cap) bad = 1;
+      off[w] = o;
+      o += min(c, f.cap);
+    }
+    off[kSkGenWarps] = o;
+    ovf = bad;
+  }
+  __syncthreads();
+  if (ovf) {   // lists incomplete: the caller reruns the exact kernel
+    if (tid == 0) atomicExch(f.overflow, 1);
+    return;
+  }
+  const uint32_t total = off[kSkGenWarps];
+  const int64_t split = blockIdx.z;
+  const int64_t col = (int64_t)blockIdx.y * f.bn + tid;
+  const bool has_col = tid < f.bn && col < f.ncols;
+  const int kc = has_col ? f.kexp[col] : 0;
+  const uint64_t* Au = reinterpret_cast<const uint64_t*>(f.A);
+  const uint64_t* bu = reinterpret_cast<const uint64_t*>(f.b);
+  for (uint32_t base = 0; base < total; base += kFixThreads) {
+    // ---- phase 1: exact minus estimate for one recorded pair
+    FixRec r{};
+    bool keep = false;
+    const uint32_t idx = base + tid;
+    if (idx < total) {
+      int w = 0;
+      while (idx >= off[w + 1]) ++w;
+      const uint64_t pk = f.rec[(cta * kSkGenWarps + w) * (int64_t)f.cap + (idx - off[w])];
+      r.i = (uint32_t)(pk & 0xFFFFu);
+      r.j0 = pk >> 16;
+      const uint4 x = philox4x32_10(gauss_counter(r.j0 >> 2, r.i), f.k0, f.k1);
+      const uint32_t pa = (r.j0 & 2u) ? x.z : x.x, pb = (r.j0 & 2u) ? x.w : x.y;
+      uint32_t fe, fo, xe, xo;
+      gauss_pair_fast<GF>(pa, pb, fe, fo);
+      gauss_pair_slow<GF>(pa, pb, xe, xo);
+      r.de = bits_to_double<GF>(xe) - bits_to_double<GF>(fe);
+      r.dodd = bits_to_double<GF>(xo) - bits_to_double<GF>(fo);
+      keep = (r.de != 0.0 || r.dodd != 0.0) && (int64_t)r.i < f.s;
+    }
+    // ---- ordered compaction of the kept pairs
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, nkept = 0;
+    for (int q = 0; q < kFixThreads / 32; ++q) {
+      if (q < warp) before += wsum[q];
+      nkept += wsum[q];
+    }
+    if (keep) kept[before + __popc(bal & ((1u << lane) - 1u))] = r;
+    __syncthreads();
+    // ---- phase 2: partial[i][col] += d * A_s[j][col]
+    if (has_col) {
+      float* pc = f.partial + (split * f.ncols + col) * f.s_pad;
+      for (int q = 0; q < nkept; ++q) {
+        const FixRec& k = kept[q];
+        double add = 0.0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const double d = e ? k.dodd : k.de;
+          const int64_t j = (int64_t)k.j0 + e;
+          if (d == 0.0 || j >= f.m) continue;
+          const uint64_t u = (col < f.n) ? Au[j * f.lda + col] : bu[j];
+          uint32_t t[3];
+          cast_bits<FMT>(u, kc, t);
+          double v = bits_to_double<GF>(t[0]);
+          if constexpr (FMT == FMT_BF16X3) v += bits_to_double<GF>(t[1]) + bits_to_double<GF>(t[2]);
+          add += d * v;
+        }
+        pc[k.i] += (float)add;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_sketch_fix(const SketchPlan& p, uint64_t seed, const uint64_t* rec,
+                              const uint32_t* rec_cnt, uint32_t cap, const double* A, int64_t lda,
+                              const double* b, const int* kexp, float* partial, int* overflow,
+                              cudaStream_t st) {
+  if (p.bn > kFixThreads) return cudaErrorInvalidValue;
+  SketchFixArgs f;
+  f.s = p.s;
+  f.m = p.m;
+  f.n = p.ncols - 1;
+  f.ncols = p.ncols;
+  f.s_pad = p.s_pad;
+  f.lda = lda;
+  f.bn = p.bn;
+  f.k0 = (uint32_t)seed;
+  f.k1 = (uint32_t)(seed >> 32);
+  f.cap = cap;
+  f.rec = rec;
+  f.rec_cnt = rec_cnt;
+  f.A = A;
+  f.b = b;
+  f.kexp = kexp;
+  f.partial = partial;
+  f.overflow = overflow;
+  dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
+  switch (p.fmt) {
+    case FMT_F16: sketch_fix_kernel<FMT_F16><<<grid, kFixThreads, 0, st>>>(f); break;
+    case FMT_BF16: sketch_fix_kernel<FMT_BF16><<<grid, kFixThreads, 0, st>>>(f); break;
+    case FMT_E4M3: sketch_fix_kernel<FMT_E4M3><<<grid, kFixThreads, 0, st>>>(f); break;
+    case FMT_BF16X3: sketch_fix_kernel<FMT_BF16X3><<<grid, kFixThreads, 0, st>>>(f); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Records per generator warp for deferred correction: the warp sees 4 * kchunk
+// (a, b) pairs; expected fractions near a midpoint are ~0.2% (BF16), ~1.6%
+// (FP16), ~0.01% (E4M3), so the capacity leaves a 4x or larger margin.
+uint32_t sketch_rec_cap(const SketchPlan& p) {
+  const int64_t pairs = 4 * p.kchunk;
+  const int64_t div = (p.fmt == FMT_F16) ? 16 : (p.fmt == FMT_E4M3) ? 1024 : 128;
+  return (uint32_t)(pairs / div + 64);
+}
+int64_t sketch_rec_lists(const SketchPlan& p) {
+  return (int64_t)p.mtiles * p.ngroups * p.splits * kSkGenWarps;
 }
 
 // ============================================================ CUDA-core sketch

@@ -47,8 +47,19 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
 // Encodes the TMA descriptor of the K-major operand Bt (rows x m, row stride ldb elements).
 bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
                     int box_rows, int rowb);
+// rec == nullptr: exact mode (FP64 fallbacks resolved inside the kernel).  Otherwise
+// deferred mode: the uncertain pairs go to sketch_rec_lists(p) lists of
+// sketch_rec_cap(p) entries (counts in rec_cnt) and launch_sketch_fix corrects the
+// partials; if it reports *overflow != 0 the exact mode must be rerun.
 cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_t seed,
-                             float* partial, int* err, cudaStream_t st);
+                             float* partial, int* err, cudaStream_t st, uint64_t* rec = nullptr,
+                             uint32_t* rec_cnt = nullptr, uint32_t rec_cap = 0);
+uint32_t sketch_rec_cap(const SketchPlan& p);
+int64_t sketch_rec_lists(const SketchPlan& p);
+cudaError_t launch_sketch_fix(const SketchPlan& p, uint64_t seed, const uint64_t* rec,
+                              const uint32_t* rec_cnt, uint32_t cap, const double* A, int64_t lda,
+                              const double* b, const int* kexp, float* partial, int* overflow,
+                              cudaStream_t st);
 // CUDA-core sketch in FP64 (fmt F64) or FP32 (fmt F32) from the FP64 data.
 cudaError_t launch_sketch_cc(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
                              int64_t n, int64_t s, uint64_t seed, int splits, int64_t kchunk,

@@ -82,3 +82,23 @@ def test_sketch_full_size_sampled_entries(lsq, handle):
             mag = np.ldexp((np.abs(g) @ np.abs(Ab))[0] / np.sqrt(s), -k)
             assert np.all(np.abs(got[i] - ref) <= (m + 2) * 2.0 ** -24 * mag)
             assert np.sqrt(np.mean(((got[i] - ref) / mag) ** 2)) <= 8 * np.sqrt(m) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16", "e4m3", "bf16x3"])
+def test_sketch_deferred_correction_matches_exact_mode(lsq, handle, fmt):
+    """The GEMM on FP32 estimates plus the correction of near-midpoint entries gives the
+    product with fl_s(G) itself: same values as resolving them inside the GEMM, up to the
+    FP32 accumulation order, and bit-identical from run to run."""
+    m, n, s = 20000, 70, 256
+    P = randsvd_problem(m, n, 1e3, rho=1e-2, seed=11)
+    got = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 5)
+    again = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 5)
+    exact = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 5, sketch_exact=1)
+    assert np.array_equal(got, again)
+    As, bs, kA, kb = sketch.cast_scaled(P.A, P.b, fmt)
+    Gs = rng.sketch_operand(s, 0, m, 5, fmt)
+    k = np.concatenate([kA, [kb]])
+    mag = np.ldexp(np.abs(Gs) @ np.abs(np.column_stack([As, bs])), -k[None, :]) / np.sqrt(s)
+    assert np.all(np.abs(got - exact) <= 2 * (m + 2) * 2.0 ** -24 * mag + 1e-300)
+    ref = sketch.sketch(P.A, P.b, s, 5, fmt)
+    assert np.all(np.abs(got - ref) <= (m + 2) * 2.0 ** -24 * mag + 1e-300)
