@@ -10,6 +10,8 @@
 // L = R^T (lower), both column-major, so every update reads contiguous column
 // segments, which cp.async stages into shared memory ahead of the step that
 // uses them (trsv.cuh).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "trsv.cuh"
@@ -35,10 +37,270 @@ __global__ void __launch_bounds__(kTrsvThreads)
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (TOUT)xs[i];
 }
 
+// ------------------------------------------------------------ cluster solve
+// One thread-block cluster of kTrsvCl CTAs (256 threads each).  Block row k (32
+// rows) belongs to CTA k % kTrsvCl; its warp (k / kTrsvCl) holds the block's
+// right-hand side in registers and the block's row panel of the matrix in shared
+// memory for the whole solve (row panels are contiguous in the transposed copy:
+// R's rows are L's columns and vice versa).  Steps run as a data flow: when
+// x_j arrives (an st.async of 32 values into every CTA's shared memory, which
+// completes that CTA's mbarrier j), each owner warp of a pending block applies
+// y_k -= M_kj x_j; once its last dependency is in, it forms x_k = D_k^-1 y_k and
+// sends it.  The critical path per block is one shared-memory hop across the
+// cluster plus two 32 x 32 products.
+constexpr int kTrsvCl = 8;
+constexpr int kTrsvClThreads = 256;
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_map(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+template <typename T>
+__device__ __forceinline__ void st_async_remote(uint32_t raddr, T v, uint32_t rbar) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr),
+                 "r"(__float_as_uint(v)), "r"(rbar)
+                 : "memory");
+  else
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
+                 "l"(__double_as_longlong(v)), "r"(rbar)
+                 : "memory");
+}
+// Bounded wait on a local mbarrier completed by remote st.async (cluster-scope acquire).
+__device__ __forceinline__ bool cl_wait(uint32_t bar, int* err) {
+  auto try_once = [&]() {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    return ok != 0;
+  };
+  if (try_once()) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!try_once()) {
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      set_error(err, DEV_TIMEOUT_FULL);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Panel geometry of block row k: width in columns (multiple of 32), row stride
+// in elements (16-byte multiple whose 16-byte count is odd: conflict-free
+// 16-byte reads of 8 consecutive rows), bytes.
+template <typename T>
+struct ClPanel {
+  static constexpr int VE = 16 / (int)sizeof(T);
+  __host__ __device__ static int width(bool upper, int k, int nb) { return upper ? 32 * (nb - 1 - k) : 32 * k; }
+  __host__ __device__ static int stride(int w) { return w + VE; }
+  __host__ __device__ static size_t bytes(int w) { return w ? (size_t)32 * stride(w) * sizeof(T) : 0; }
+};
+
+// Shared memory of CTA `q`: its panels, its diagonal inverses, x of every block, nb mbarriers.
+template <typename T>
+__host__ __device__ inline size_t cl_smem(bool upper, int n, int q) {
+  const int nb = (n + 31) / 32;
+  size_t b = 0;
+  for (int k = q; k < nb; k += kTrsvCl) b += ClPanel<T>::bytes(ClPanel<T>::width(upper, k, nb)) + 1024 * sizeof(T);
+  return b + (((size_t)32 * nb * sizeof(T) + 8 * (size_t)nb + 15) & ~(size_t)15);
+}
+
+template <typename T, typename TIN, typename TOUT, bool UPPER>
+__global__ void __launch_bounds__(kTrsvClThreads)
+    trsv_cluster_kernel(const T* __restrict__ Q, int64_t ld, const T* __restrict__ D, int n,
+                        const TIN* __restrict__ y, double yscale, TOUT* __restrict__ x, const int* done,
+                        const int* jp, int64_t ys, int64_t xstr, int* err) {
+  using P = ClPanel<T>;
+  if (done && *done) return;   // uniform over the cluster: no CTA reaches a cluster barrier
+  if (jp) {
+    const int64_t j = *jp;
+    y += j * ys;
+    x += j * xstr;
+  }
+  extern __shared__ __align__(16) unsigned char cl_buf[];
+  const int nb = (n + 31) >> 5;
+  const uint32_t q = cl_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // ---- layout: [x: 32 nb][bars: nb][panels of owned blocks][D of owned blocks]; x and
+  // the barriers sit at the same offsets in every CTA (remote addresses are mapped)
+  T* xall = reinterpret_cast<T*>(cl_buf);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cl_buf + (size_t)32 * nb * sizeof(T));
+  unsigned char* cur = cl_buf + (((size_t)32 * nb * sizeof(T) + 8 * (size_t)nb + 15) & ~(size_t)15);
+  T* panel[kTrsvClThreads / 32];
+  T* dblk[kTrsvClThreads / 32];
+  int nown = 0;
+  for (int k = (int)q; k < nb; k += kTrsvCl) {
+    panel[nown] = reinterpret_cast<T*>(cur);
+    cur += P::bytes(P::width(UPPER, k, nb));
+    ++nown;
+  }
+  for (int t = 0; t < nown; ++t) {
+    dblk[t] = reinterpret_cast<T*>(cur);
+    cur += 1024 * sizeof(T);
+  }
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t xall0 = smem_u32(xall);
+  __shared__ uint64_t load_bar;
+  const uint32_t lbar = smem_u32(&load_bar);
+  // ---- barriers: one per block (its x arrives as 32 * sizeof(T) bytes), one for the loads
+  if (tid == 0) {
+    for (int k = 0; k < nb; ++k) mbar_init(bar0 + 8 * k, 1);
+    mbar_init(lbar, 1);
+    fence_barrier_init();
+    for (int k = 0; k < nb; ++k) mbar_arrive_expect_tx(bar0 + 8 * k, 32u * (uint32_t)sizeof(T));
+  }
+  // zero the panels' column tails that the copies do not cover (partial last block)
+  for (int t = 0; t < nown; ++t) {
+    const int k = (int)q + t * kTrsvCl;
+    const int w = P::width(UPPER, k, nb);
+    if (!w) continue;
+    const int c0 = UPPER ? 32 * (k + 1) : 0;                 // first column of the panel
+    const int valid = min(w, n - c0);                        // columns inside the matrix
+    const int copied = (valid + P::VE - 1) / P::VE * P::VE;
+    const int rows = min(32, n - 32 * k);
+    for (int e = tid; e < 32 * P::stride(w); e += blockDim.x) {
+      const int r = e / P::stride(w), c = e % P::stride(w);
+      if (r >= rows || c >= copied) panel[t][e] = T(0);
+    }
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  // ---- bulk loads: panel rows (contiguous in Q), diagonal inverses
+  if (warp == 0) {
+    uint32_t bytes = 0;
+    for (int t = 0; t < nown; ++t) {
+      const int k = (int)q + t * kTrsvCl;
+      const int w = P::width(UPPER, k, nb);
+      const int c0 = UPPER ? 32 * (k + 1) : 0;
+      const int valid = w ? min(w, n - c0) : 0;
+      const uint32_t seg = (uint32_t)((valid + P::VE - 1) / P::VE * 16);
+      const int rows = min(32, n - 32 * k);
+      bytes += 1024u * (uint32_t)sizeof(T) + (seg ? seg * (uint32_t)rows : 0u);
+    }
+    if (lane == 0) mbar_arrive_expect_tx(lbar, bytes);
+    __syncwarp();
+    for (int t = 0; t < nown; ++t) {
+      const int k = (int)q + t * kTrsvCl;
+      const int w = P::width(UPPER, k, nb);
+      const int c0 = UPPER ? 32 * (k + 1) : 0;
+      const int valid = w ? min(w, n - c0) : 0;
+      const uint32_t seg = (uint32_t)((valid + P::VE - 1) / P::VE * 16);
+      const int rows = min(32, n - 32 * k);
+      if (lane == 0) bulk_load(smem_u32(dblk[t]), D + (size_t)k * 1024, 1024u * (uint32_t)sizeof(T), lbar);
+      if (seg && lane < rows)
+        bulk_load(smem_u32(panel[t] + lane * P::stride(w)), Q + (size_t)(32 * k + lane) * ld + c0, seg, lbar);
+    }
+  }
+  // every CTA's barriers are initialised before anyone sends
+  cl_sync();
+  // ---- block warps
+  if (warp < nown) {
+    const int t = warp;
+    const int k = (int)q + t * kTrsvCl;
+    const int w = P::width(UPPER, k, nb);
+    const int rows = min(32, n - 32 * k);
+    T acc = (lane < rows) ? (T)((double)y[32 * k + lane] * yscale) : T(0);
+    bool ok = mbar_wait(lbar, 0, err, DEV_TIMEOUT_FULL);
+    const T* pr = panel[t] + lane * P::stride(w);
+    // dependencies: UPPER j = nb-1 .. k+1, LOWER j = 0 .. k-1 (the order they are produced)
+    const int ndep = UPPER ? nb - 1 - k : k;
+    for (int d = 0; d < ndep && ok; ++d) {
+      const int j = UPPER ? nb - 1 - d : d;
+      ok = cl_wait(bar0 + 8 * j, err);
+      if (!ok) break;
+      const int off = UPPER ? 32 * (j - k - 1) : 32 * j;
+      const T* xj = xall + 32 * j;
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 32; c += P::VE) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 mv = *reinterpret_cast<const float4*>(pr + off + c);
+          const float4 xv = *reinterpret_cast<const float4*>(xj + c);
+          s += mv.x * xv.x + mv.y * xv.y + mv.z * xv.z + mv.w * xv.w;
+        } else {
+          const double2 mv = *reinterpret_cast<const double2*>(pr + off + c);
+          const double2 xv = *reinterpret_cast<const double2*>(xj + c);
+          s += mv.x * xv.x + mv.y * xv.y;
+        }
+      }
+      acc -= s;
+    }
+    // x_k = D_k^-1 y_k (lane r: sum_c D[c][r] y_c), then to every CTA of the cluster
+    const T* dk = dblk[t];
+    T xk = T(0);
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) xk += dk[c * 32 + lane] * __shfl_sync(0xffffffffu, acc, c);
+    if (lane >= rows) xk = T(0);
+    for (uint32_t dst = 0; dst < (uint32_t)kTrsvCl; ++dst)
+      st_async_remote<T>(cl_map(xall0 + (uint32_t)((32 * k + lane) * sizeof(T)), dst), xk,
+                         cl_map(bar0 + 8 * k, dst));
+    if (lane < rows) x[32 * k + lane] = (TOUT)xk;
+    (void)w;
+  }
+  // ---- leave only when every x has landed here (no st.async still targets this CTA)
+  if (tid == 0)
+    for (int k = 0; k < nb; ++k) cl_wait(bar0 + 8 * k, err);
+  __syncthreads();
+  cl_sync();
+}
+
+template <typename T, typename TIN, typename TOUT, bool UPPER>
+static cudaError_t launch_trsv_cluster(const T* Q, int64_t ld, const T* D, int n, const TIN* y, double yscale,
+                                       TOUT* x, const int* done, cudaStream_t st, const int* jp, int64_t ys,
+                                       int64_t xstr, int* err, size_t smem) {
+  auto kern = trsv_cluster_kernel<T, TIN, TOUT, UPPER>;
+  cudaError_t e = allow_dyn_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kTrsvCl);
+  cfg.blockDim = dim3(kTrsvClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTrsvCl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, Q, ld, D, n, y, yscale, x, done, jp, ys, xstr, err);
+}
+
+// Largest per-CTA shared memory of the cluster solve (0 if it does not fit).
+template <typename T>
+static size_t cl_smem_max(bool upper, int n) {
+  const int nb = (n + 31) / 32;
+  if (nb > kTrsvCl * (kTrsvClThreads / 32)) return 0;   // at most one block per warp
+  size_t mx = 0;
+  for (int q = 0; q < kTrsvCl; ++q) mx = std::max(mx, cl_smem<T>(upper, n, q));
+  return mx <= 200 * 1024 ? mx : 0;
+}
+
 template <typename T, typename TIN, typename TOUT>
 cudaError_t launch_trsv(bool upper, const Tri<T>& f, const TIN* y, double yscale, TOUT* x,
                         const int* done, cudaStream_t st, const int* jp, int64_t ys, int64_t xstr) {
   if (f.n > 1024) return cudaErrorInvalidValue;
+  // the cluster solve whenever its panels fit in shared memory (every CTA the same size)
+  const size_t csm = cl_smem_max<T>(upper, (int)f.n);
+  if (csm) {
+    return upper ? launch_trsv_cluster<T, TIN, TOUT, true>(f.L, f.ld, f.DU, (int)f.n, y, yscale, x, done, st,
+                                                          jp, ys, xstr, f.err, csm)
+                 : launch_trsv_cluster<T, TIN, TOUT, false>(f.R, f.ld, f.DL, (int)f.n, y, yscale, x, done,
+                                                           st, jp, ys, xstr, f.err, csm);
+  }
   const size_t smem = TrsvSmem<T>::bytes;
   if (upper) {
     auto kern = trsv_kernel<T, TIN, TOUT, true>;
