@@ -579,8 +579,8 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   double* p4 = static_cast<double*>(ws(c.h, "gmp4", 4 * c.nblk2 * 8));
   double* nrm = static_cast<double*>(ws(c.h, "gmnrm", 4 * 8));
   GmState* gst = static_cast<GmState*>(ws(c.h, "gm_state", sizeof(GmState)));
-  unsigned* cnt = static_cast<unsigned*>(ws(c.h, "gm_cnt", 64));
-  CK(cudaMemsetAsync(cnt, 0, 64, c.st));
+  unsigned* gbar = static_cast<unsigned*>(ws(c.h, "gm_bar", 64));
+  CK(cudaMemsetAsync(gbar, 0, 64, c.st));
   GmState hs{};
   hs.tol = tol;
   hs.maxit = maxit;
@@ -603,13 +603,9 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
       L((launch_colsum<TOP, TOP>(P, c.nblk, n, nullptr, 1.0, sb, dn, c.st)));
       L((launch_trsv<TOP, TOP, double>(false, tri, sb, 1.0, wv + m, dn, c.st)));
       // classical Gram-Schmidt; the second pass runs only when the first one lost
-      // more than half of ||w||^2 ("twice is enough")
-      L(launch_gm_mdot<TOP>(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st, az, m, false, cnt, hh, H, ldh));
-      L(launch_gm_axpy(V, ld, hh, wv, ld, gst, sqp, c.nblk2, c.st, false, cnt + 1, H, ldh, cs, sn, g));
-      L(launch_gm_mdot<TOP>(V, ld, wv, ld, gst, maxc, Dp, c.nblk2, c.st, nullptr, m, true, cnt, hh, H,
-                            ldh));
-      L(launch_gm_axpy(V, ld, hh, wv, ld, gst, sqp, c.nblk2, c.st, true, cnt + 1, H, ldh, cs, sn, g));
-      L(launch_gm_newcol(wv, ld, gst, V, ld, v32, m, c.nblk2, c.st));
+      // more than half of ||w||^2 ("twice is enough"); Givens step; new column
+      L(launch_gm_step<TOP>(V, ld, wv, ld, m, az, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, v32, gbar,
+                            c.h->d_err, c.h->num_sms, c.st));
     }
   };
   CachedGraph* G =
@@ -619,7 +615,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
                              graph_key(sizeof(TOP) == 4 ? "fgm32" : "fgm64",
                                        {PV(Aop), ldop, m, n, maxit, PV(V), PV(Zb), PV(wv), PV(P), PV(az), PV(v32),
                                         PV(sb), PV(H), PV(cs), PV(sn), PV(g), PV(hh), PV(Dp), PV(sqp),
-                                        PV(gst), PV(cnt), PV(tri.R), PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk,
+                                        PV(gst), PV(gbar), PV(tri.R), PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk,
                                         c.nblk2}),
                              body);
   int j = 0;

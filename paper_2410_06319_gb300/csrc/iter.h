@@ -68,6 +68,14 @@ cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, 
 cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
                            GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second,
                            unsigned* cnt, double* H, int ldh, double* cs, double* sn, double* g);
+// The whole Arnoldi step in one cooperative launch (same arithmetic as mdot / axpy /
+// newcol above, blocks synchronised by a bounded grid barrier on bar[0..1], which
+// must be zero between launches; each launch leaves it zero): needs maxc <= 128.
+template <typename TAZ>
+cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
+                           GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
+                           double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
+                           int num_sms, cudaStream_t s);
 cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
                              float* v32, int64_t m, int nblk, cudaStream_t s);
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,

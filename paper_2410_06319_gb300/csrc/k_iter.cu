@@ -9,6 +9,8 @@
 // results are deterministic.
 #include <type_traits>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "iter.h"
 #include "kernels.h"
@@ -1096,6 +1098,163 @@ __global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const d
   if (finish) gm_finish_block(t, st, H, ldh, cs, sn, g);
   if (threadIdx.x == 0) *cnt = 0u;
 }
+
+// ---------------------------------------------------------------- fused Arnoldi step
+// One cooperative launch per FGMRES iteration (blocks co-resident, each owning a
+// contiguous row range of the length-(m+n) vectors): w_top = v_top + A z; then
+// classical Gram-Schmidt passes h = V^T w (block partials; bounded grid barrier;
+// block c sums column c over the blocks in a fixed order; grid barrier), w -= V h,
+// ||w||^2 (grid barrier; every block sums the block partials in the same fixed
+// order); a second pass only when the first lost more than half of
+// ||w||^2 ("twice is enough"); then block 0 applies the Givens rotations and the
+// new column V[:, j+1] = w / ||w|| (and its FP32 top copy) is written.  FP64
+// throughout, as the separate kernels it replaces.
+template <typename TAZ>
+struct GmStepArgs {
+  double* V;
+  int64_t ld, len, m;
+  double* w;
+  const TAZ* az;
+  GmState* st;
+  int maxc, ldh;
+  double* Dp;
+  double* sq;
+  double* hsum;
+  double* H;
+  double* cs;
+  double* sn;
+  double* g;
+  float* v32;
+  unsigned* bar;
+  int* err;
+};
+
+template <typename TAZ>
+__global__ void __launch_bounds__(256) gm_step_kernel(const GmStepArgs<TAZ> a) {
+  if (a.st->done) return;   // uniform: read before any grid barrier
+  __shared__ double hs[128];
+  __shared__ double red[33];
+  const int j = a.st->j, ncols = j + 1;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t chunk = (a.len + nb - 1) / nb;
+  const int64_t r0 = (int64_t)b * chunk, r1 = min(a.len, r0 + chunk);
+  double* w = a.w;
+  const double* V = a.V;
+  if (a.az) {   // w_top = v_top + A z (the pass left A z in az)
+    const double* vj = V + (int64_t)j * a.ld;
+    for (int64_t i = r0 + threadIdx.x; i < min(r1, a.m); i += blockDim.x) w[i] = vj[i] + (double)a.az[i];
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    // ---- h = V^T w: block partials, one warp per column (four rows in flight per lane)
+    for (int c = warp; c < ncols; c += nw) {
+      const double* vc = V + (int64_t)c * a.ld;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      int64_t i = r0 + lane;
+      for (; i + 96 < r1; i += 128) {
+        t0 += vc[i] * w[i];
+        t1 += vc[i + 32] * w[i + 32];
+        t2 += vc[i + 64] * w[i + 64];
+        t3 += vc[i + 96] * w[i + 96];
+      }
+      for (; i < r1; i += 32) t0 += vc[i] * w[i];
+      double t = warp_sum((t0 + t1) + (t2 + t3));
+      if (lane == 0) a.Dp[(int64_t)b * a.maxc + c] = t;
+    }
+    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
+    // h[c] = sum over blocks in a fixed order: warp 0 of block c, then shared by all
+    if (b < ncols && warp == 0) {
+      double t = 0.0;
+      for (int q = lane; q < nb; q += 32) t += __ldcg(a.Dp + (int64_t)q * a.maxc + b);
+      t = warp_sum(t);
+      if (lane == 0) a.hsum[b] = t;
+    }
+    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(a.hsum + c);
+    __syncthreads();
+    if (b == 0)
+      for (int c = threadIdx.x; c < ncols; c += blockDim.x) a.H[(int64_t)j * a.ldh + c] += hs[c];
+    // ---- w -= V h and ||w||^2
+    double sqp = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      // four independent partial sums over the columns (loads in flight)
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int c = 0;
+      for (; c + 3 < ncols; c += 4) {
+        p0 += V[(int64_t)c * a.ld + i] * hs[c];
+        p1 += V[(int64_t)(c + 1) * a.ld + i] * hs[c + 1];
+        p2 += V[(int64_t)(c + 2) * a.ld + i] * hs[c + 2];
+        p3 += V[(int64_t)(c + 3) * a.ld + i] * hs[c + 3];
+      }
+      for (; c < ncols; ++c) p0 += V[(int64_t)c * a.ld + i] * hs[c];
+      const double acc = w[i] - ((p0 + p1) + (p2 + p3));
+      w[i] = acc;
+      sqp += acc * acc;
+    }
+    sqp = block_sum_d(sqp, red);
+    if (threadIdx.x == 0) a.sq[b] = sqp;
+    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
+    double t = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) t += __ldcg(a.sq + q);
+    s = block_sum_d(t, red);
+    if (pass == 1) break;
+    double hh = 0.0;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hh += hs[c] * hs[c];
+    hh = block_sum_d(hh, red);
+    const int need = (s < 0.5 * (s + hh)) ? 1 : 0;
+    if (b == 0 && threadIdx.x == 0) {
+      a.st->reorth = need;
+      a.st->nreorth += need;
+    }
+    if (!need) break;
+  }
+  // ---- new column (every block, own rows) and the Givens step (block 0)
+  const double hn = sqrt(s);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double* vn = a.V + (int64_t)(j + 1) * a.ld;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double v = w[i] * inv;
+    vn[i] = v;
+    if (a.v32 && i < a.m) a.v32[i] = (float)v;
+  }
+  if (b == 0) gm_finish_block(s, a.st, a.H, a.ldh, a.cs, a.sn, a.g);
+}
+
+template <typename TAZ>
+cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
+                           GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
+                           double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
+                           int num_sms, cudaStream_t s) {
+  static_assert(sizeof(GmStepArgs<TAZ>) < 4096, "kernel parameter block");
+  if (maxc > 128) return cudaErrorInvalidValue;
+  auto kern = gm_step_kernel<TAZ>;
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int nblk = std::min(occ, 2) * num_sms;
+  if (nblk < maxc) return cudaErrorInvalidConfiguration;   // one block per column of h
+  GmStepArgs<TAZ> a{V, ld, len, m, w, az, st, maxc, 0, Dp, sq, hsum, H, cs, sn, g, v32, bar, err};
+  a.ldh = ldh;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nblk);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+template cudaError_t launch_gm_step<float>(double*, int64_t, double*, int64_t, int64_t, const float*, GmState*,
+                                           int, double*, double*, double*, double*, int, double*, double*,
+                                           double*, float*, unsigned*, int*, int, cudaStream_t);
+template cudaError_t launch_gm_step<double>(double*, int64_t, double*, int64_t, int64_t, const double*,
+                                            GmState*, int, double*, double*, double*, double*, int, double*,
+                                            double*, double*, float*, unsigned*, int*, int, cudaStream_t);
 
 // V[:, j] = w * inv_h  (j read after gm_finish incremented it)
 __global__ void gm_newcol_kernel(const double* __restrict__ w, int64_t len, const GmState* st,

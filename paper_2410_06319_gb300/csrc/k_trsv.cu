@@ -64,6 +64,13 @@ __device__ __forceinline__ uint32_t cl_map(uint32_t saddr, uint32_t rank) {
 __device__ __forceinline__ void cl_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// 16 bytes into another CTA's shared memory, completing `rbar` there by 16 bytes.
+__device__ __forceinline__ void st_async_16(uint32_t raddr, uint4 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   raddr),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar)
+               : "memory");
+}
 template <typename T>
 __device__ __forceinline__ void st_async_remote(uint32_t raddr, T v, uint32_t rbar) {
   if constexpr (sizeof(T) == 4)
@@ -75,12 +82,14 @@ __device__ __forceinline__ void st_async_remote(uint32_t raddr, T v, uint32_t rb
                  "l"(__double_as_longlong(v)), "r"(rbar)
                  : "memory");
 }
-// Bounded wait on a local mbarrier completed by remote st.async (cluster-scope acquire).
+// Bounded wait on a local mbarrier completed by remote st.async (cluster-scope
+// acquire).  Polls with the non-blocking test_wait: the solve's critical path is
+// one such wait per block, and a suspended try_wait wakes late.
 __device__ __forceinline__ bool cl_wait(uint32_t bar, int* err) {
   auto try_once = [&]() {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(bar)
@@ -162,7 +171,8 @@ __global__ void __launch_bounds__(kTrsvClThreads)
     fence_barrier_init();
     for (int k = 0; k < nb; ++k) mbar_arrive_expect_tx(bar0 + 8 * k, 32u * (uint32_t)sizeof(T));
   }
-  // zero the panels' column tails that the copies do not cover (partial last block)
+  // zero what the copies do not cover: the column tail past the matrix (the
+  // partial last column block) and the rows past the matrix (the partial last block)
   for (int t = 0; t < nown; ++t) {
     const int k = (int)q + t * kTrsvCl;
     const int w = P::width(UPPER, k, nb);
@@ -171,10 +181,11 @@ __global__ void __launch_bounds__(kTrsvClThreads)
     const int valid = min(w, n - c0);                        // columns inside the matrix
     const int copied = (valid + P::VE - 1) / P::VE * P::VE;
     const int rows = min(32, n - 32 * k);
-    for (int e = tid; e < 32 * P::stride(w); e += blockDim.x) {
-      const int r = e / P::stride(w), c = e % P::stride(w);
-      if (r >= rows || c >= copied) panel[t][e] = T(0);
-    }
+    const int tail = w - copied;
+    for (int e = tid; e < rows * tail; e += blockDim.x)
+      panel[t][(e / tail) * P::stride(w) + copied + e % tail] = T(0);
+    for (int e = tid; e < (32 - rows) * w; e += blockDim.x)
+      panel[t][(rows + e / w) * P::stride(w) + e % w] = T(0);
   }
   fence_proxy_async_smem();
   __syncthreads();
@@ -240,13 +251,39 @@ __global__ void __launch_bounds__(kTrsvClThreads)
     }
     // x_k = D_k^-1 y_k (lane r: sum_c D[c][r] y_c), then to every CTA of the cluster
     const T* dk = dblk[t];
-    T xk = T(0);
+    T xa = T(0), xb = T(0);
 #pragma unroll 8
-    for (int c = 0; c < 32; ++c) xk += dk[c * 32 + lane] * __shfl_sync(0xffffffffu, acc, c);
+    for (int c = 0; c < 32; c += 2) {
+      xa += dk[c * 32 + lane] * __shfl_sync(0xffffffffu, acc, c);
+      xb += dk[(c + 1) * 32 + lane] * __shfl_sync(0xffffffffu, acc, c + 1);
+    }
+    T xk = xa + xb;
     if (lane >= rows) xk = T(0);
-    for (uint32_t dst = 0; dst < (uint32_t)kTrsvCl; ++dst)
-      st_async_remote<T>(cl_map(xall0 + (uint32_t)((32 * k + lane) * sizeof(T)), dst), xk,
-                         cl_map(bar0 + 8 * k, dst));
+    // send x_k: 16-byte pieces, destinations spread over the lanes (lane l serves
+    // CTA l % 8, pieces l / 8, l / 8 + 4, ...)
+    constexpr int EP = 16 / (int)sizeof(T);                 // elements per piece
+    constexpr int PIECES = 32 / EP;                         // pieces per destination
+    const uint32_t dst = (uint32_t)(lane & (kTrsvCl - 1));
+    const uint32_t rx = cl_map(xall0 + (uint32_t)(32 * k * sizeof(T)), dst);
+    const uint32_t rb = cl_map(bar0 + 8 * k, dst);
+#pragma unroll
+    for (int pc = lane / kTrsvCl; pc < PIECES; pc += 32 / kTrsvCl) {
+      uint4 v;
+      if constexpr (sizeof(T) == 4) {
+        v.x = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 0));
+        v.y = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 1));
+        v.z = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 2));
+        v.w = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 3));
+      } else {
+        const double d0 = __shfl_sync(0xffffffffu, xk, pc * EP + 0);
+        const double d1 = __shfl_sync(0xffffffffu, xk, pc * EP + 1);
+        v.x = (uint32_t)__double2loint(d0);
+        v.y = (uint32_t)__double2hiint(d0);
+        v.z = (uint32_t)__double2loint(d1);
+        v.w = (uint32_t)__double2hiint(d1);
+      }
+      st_async_16(rx + (uint32_t)(pc * 16), v, rb);
+    }
     if (lane < rows) x[32 * k + lane] = (TOUT)xk;
     (void)w;
   }
