@@ -126,6 +126,24 @@ class Clocks:
         return out
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch (read + write) of the dominant pass from its committed ncu
+    summary, or None if there is none or the kernel's source changed since the capture."""
+    if kernel != "fgmres_pass":
+        return None
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "pass_bulk_fgmres_m100000_n500.md")
+    try:
+        text = open(path).read()
+        tb = int(re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M).group(1))
+        src, h = re.search(r"^source: (\S+) sha256\[:16\] ([0-9a-f]+)", text, re.M).groups()
+        cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    except (OSError, AttributeError, ValueError):
+        return None
+    return tb if cur == h else None
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -288,7 +306,7 @@ def run_ours(args):
     if dom:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["gbs"], "peak": hbm,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": passes[dom]["gbs"] / hbm,
-                    "traffic": None, "algorithmic_bytes_per_launch": kbytes[dom],
+                    "traffic": measured_traffic(dom), "algorithmic_bytes_per_launch": kbytes[dom],
                     "how": "CUDA events around each launch over the instrumented steps"}
 
     # ---- the configuration's literal single-term sketch precisions (kappa u_s >> 1)
