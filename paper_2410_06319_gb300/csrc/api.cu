@@ -573,8 +573,8 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   double* sn = static_cast<double*>(ws(c.h, "gmsn", (maxit + 1) * 8));
   double* g = static_cast<double*>(ws(c.h, "gmg", (maxit + 2) * 8, true));
   double* y = static_cast<double*>(ws(c.h, "gmy", (maxit + 1) * 8));
-  double* hh = static_cast<double*>(ws(c.h, "gmhh", (maxit + 1) * 8));
-  double* Dp = static_cast<double*>(ws(c.h, "gmDp", (size_t)c.nblk2 * (maxit + 1) * 8));
+  double* hh = static_cast<double*>(ws(c.h, "gmhh", (maxit + 2) * 8));
+  double* Dp = static_cast<double*>(ws(c.h, "gmDp", (size_t)c.nblk2 * (maxit + 2) * 8));
   double* sqp = static_cast<double*>(ws(c.h, "gmsq", c.nblk2 * 8));
   double* p4 = static_cast<double*>(ws(c.h, "gmp4", 4 * c.nblk2 * 8));
   double* nrm = static_cast<double*>(ws(c.h, "gmnrm", 4 * 8));

@@ -1100,15 +1100,21 @@ __global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const d
 }
 
 // ---------------------------------------------------------------- fused Arnoldi step
-// One cooperative launch per FGMRES iteration (blocks co-resident, each owning a
-// contiguous row range of the length-(m+n) vectors): w_top = v_top + A z; then
-// classical Gram-Schmidt passes h = V^T w (block partials; bounded grid barrier;
-// block c sums column c over the blocks in a fixed order; grid barrier), w -= V h,
-// ||w||^2 (grid barrier; every block sums the block partials in the same fixed
-// order); a second pass only when the first lost more than half of
-// ||w||^2 ("twice is enough"); then block 0 applies the Givens rotations and the
-// new column V[:, j+1] = w / ||w|| (and its FP32 top copy) is written.  FP64
-// throughout, as the separate kernels it replaces.
+// One cooperative launch per FGMRES iteration, one 512-thread CTA per SM, each owning a
+// contiguous row range of the length-(m+n) vectors:
+//   sweep 1: w_top = v_top + A z; partials of h = V^T w and of ||w||^2
+//   [grid barrier] CTA c sums column c of the partials (CTA ncols sums ||w||^2), in a
+//   fixed order  [grid barrier]  every CTA reads h and ||w||^2
+//   Kahan's "twice is enough": the first pass loses more than half of ||w||^2 iff
+//   ||h||^2 > ||w||^2 / 2 (Pythagoras; decided before the update, exact at the
+//   threshold up to rounding); then
+//   one pass:  w -= V h, partial ||w||^2 [barrier]
+//   two passes: w -= V h, partials of h2 = V^T w [barrier] column sums [barrier]
+//               w -= V h2, partial ||w||^2 [barrier]
+//   every CTA sums the ||w||^2 partials in the same order; CTA 0 applies the Givens
+//   rotations; the new column V[:, j+1] = w / ||w|| (and its FP32 top copy) is written.
+// FP64 throughout; all grid barriers have bounded waits.
+constexpr int kGmThreads = 512;
 template <typename TAZ>
 struct GmStepArgs {
   double* V;
@@ -1117,9 +1123,9 @@ struct GmStepArgs {
   const TAZ* az;
   GmState* st;
   int maxc, ldh;
-  double* Dp;
-  double* sq;
-  double* hsum;
+  double* Dp;     // [nblk][maxc + 1] partials (column maxc: ||w||^2)
+  double* sq;     // [nblk] partials of the final ||w||^2
+  double* hsum;   // [maxc + 1] column sums
   double* H;
   double* cs;
   double* sn;
@@ -1129,16 +1135,65 @@ struct GmStepArgs {
   int* err;
 };
 
+// partial dots of V[:, 0..ncols) with w over rows [r0, r1) (warp per column), and
+// optionally of ||w||^2, into Dp[b][.]
+__device__ __forceinline__ void gm_partials(const double* V, int64_t ld, const double* w, int64_t r0, int64_t r1,
+                                            int ncols, double* Dpb, bool with_norm, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncols; c += nw) {
+    const double* vc = V + (int64_t)c * ld;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int64_t i = r0 + lane;
+    for (; i + 96 < r1; i += 128) {
+      t0 += vc[i] * w[i];
+      t1 += vc[i + 32] * w[i + 32];
+      t2 += vc[i + 64] * w[i + 64];
+      t3 += vc[i + 96] * w[i + 96];
+    }
+    for (; i < r1; i += 32) t0 += vc[i] * w[i];
+    const double t = warp_sum((t0 + t1) + (t2 + t3));
+    if (lane == 0) Dpb[c] = t;
+  }
+  if (with_norm) {
+    double q = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) q += w[i] * w[i];
+    q = block_sum_d(q, red);
+    if (threadIdx.x == 0) Dpb[ncols] = q;
+  }
+}
+
+// w[i] -= sum_c V[c][i] h[c] over rows [r0, r1); returns this thread's sum of w[i]^2
+__device__ __forceinline__ double gm_update(const double* V, int64_t ld, double* w, int64_t r0, int64_t r1,
+                                            int ncols, const double* hs) {
+  double sqp = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    int c = 0;
+    for (; c + 3 < ncols; c += 4) {
+      p0 += V[(int64_t)c * ld + i] * hs[c];
+      p1 += V[(int64_t)(c + 1) * ld + i] * hs[c + 1];
+      p2 += V[(int64_t)(c + 2) * ld + i] * hs[c + 2];
+      p3 += V[(int64_t)(c + 3) * ld + i] * hs[c + 3];
+    }
+    for (; c < ncols; ++c) p0 += V[(int64_t)c * ld + i] * hs[c];
+    const double acc = w[i] - ((p0 + p1) + (p2 + p3));
+    w[i] = acc;
+    sqp += acc * acc;
+  }
+  return sqp;
+}
+
 template <typename TAZ>
-__global__ void __launch_bounds__(256) gm_step_kernel(const GmStepArgs<TAZ> a) {
+__global__ void __launch_bounds__(kGmThreads) gm_step_kernel(const GmStepArgs<TAZ> a) {
   if (a.st->done) return;   // uniform: read before any grid barrier
-  __shared__ double hs[128];
+  __shared__ double hs[129];
   __shared__ double red[33];
   const int j = a.st->j, ncols = j + 1;
   const int nb = gridDim.x, b = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t chunk = (a.len + nb - 1) / nb;
   const int64_t r0 = (int64_t)b * chunk, r1 = min(a.len, r0 + chunk);
+  const int ldp = a.maxc + 1;
   double* w = a.w;
   const double* V = a.V;
   if (a.az) {   // w_top = v_top + A z (the pass left A z in az)
@@ -1146,70 +1201,49 @@ __global__ void __launch_bounds__(256) gm_step_kernel(const GmStepArgs<TAZ> a) {
     for (int64_t i = r0 + threadIdx.x; i < min(r1, a.m); i += blockDim.x) w[i] = vj[i] + (double)a.az[i];
     __syncthreads();
   }
-  double s = 0.0;
-  for (int pass = 0; pass < 2; ++pass) {
-    // ---- h = V^T w: block partials, one warp per column (four rows in flight per lane)
-    for (int c = warp; c < ncols; c += nw) {
-      const double* vc = V + (int64_t)c * a.ld;
-      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-      int64_t i = r0 + lane;
-      for (; i + 96 < r1; i += 128) {
-        t0 += vc[i] * w[i];
-        t1 += vc[i + 32] * w[i + 32];
-        t2 += vc[i + 64] * w[i + 64];
-        t3 += vc[i + 96] * w[i + 96];
-      }
-      for (; i < r1; i += 32) t0 += vc[i] * w[i];
-      double t = warp_sum((t0 + t1) + (t2 + t3));
-      if (lane == 0) a.Dp[(int64_t)b * a.maxc + c] = t;
-    }
-    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
-    // h[c] = sum over blocks in a fixed order: warp 0 of block c, then shared by all
-    if (b < ncols && warp == 0) {
+  // column sums of the partials: CTA c takes column c, in a fixed order
+  auto column_sums = [&](int cols) -> bool {
+    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return false;
+    if (b < cols && warp == 0) {
       double t = 0.0;
-      for (int q = lane; q < nb; q += 32) t += __ldcg(a.Dp + (int64_t)q * a.maxc + b);
+      for (int q = lane; q < nb; q += 32) t += __ldcg(a.Dp + (int64_t)q * ldp + b);
       t = warp_sum(t);
       if (lane == 0) a.hsum[b] = t;
     }
-    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(a.hsum + c);
+    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return false;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) hs[c] = __ldcg(a.hsum + c);
     __syncthreads();
+    return true;
+  };
+  // ---- first pass: h and ||w||^2
+  gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp + (int64_t)b * ldp, true, red);
+  if (!column_sums(ncols + 1)) return;
+  const double wn2 = hs[ncols];
+  double hh = 0.0;
+  for (int c = 0; c < ncols; ++c) hh += hs[c] * hs[c];   // same order in every thread
+  const bool second = hh > 0.5 * wn2;
+  if (b == 0) {
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) a.H[(int64_t)j * a.ldh + c] += hs[c];
+    if (threadIdx.x == 0) {
+      a.st->reorth = second ? 1 : 0;
+      a.st->nreorth += second ? 1 : 0;
+    }
+  }
+  double sqp = gm_update(V, a.ld, w, r0, r1, ncols, hs);
+  if (second) {
+    __syncthreads();   // this CTA's rows of w are final for the second pass
+    gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp + (int64_t)b * ldp, false, red);
+    if (!column_sums(ncols)) return;
     if (b == 0)
       for (int c = threadIdx.x; c < ncols; c += blockDim.x) a.H[(int64_t)j * a.ldh + c] += hs[c];
-    // ---- w -= V h and ||w||^2
-    double sqp = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      // four independent partial sums over the columns (loads in flight)
-      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      int c = 0;
-      for (; c + 3 < ncols; c += 4) {
-        p0 += V[(int64_t)c * a.ld + i] * hs[c];
-        p1 += V[(int64_t)(c + 1) * a.ld + i] * hs[c + 1];
-        p2 += V[(int64_t)(c + 2) * a.ld + i] * hs[c + 2];
-        p3 += V[(int64_t)(c + 3) * a.ld + i] * hs[c + 3];
-      }
-      for (; c < ncols; ++c) p0 += V[(int64_t)c * a.ld + i] * hs[c];
-      const double acc = w[i] - ((p0 + p1) + (p2 + p3));
-      w[i] = acc;
-      sqp += acc * acc;
-    }
-    sqp = block_sum_d(sqp, red);
-    if (threadIdx.x == 0) a.sq[b] = sqp;
-    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
-    double t = 0.0;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) t += __ldcg(a.sq + q);
-    s = block_sum_d(t, red);
-    if (pass == 1) break;
-    double hh = 0.0;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hh += hs[c] * hs[c];
-    hh = block_sum_d(hh, red);
-    const int need = (s < 0.5 * (s + hh)) ? 1 : 0;
-    if (b == 0 && threadIdx.x == 0) {
-      a.st->reorth = need;
-      a.st->nreorth += need;
-    }
-    if (!need) break;
+    sqp = gm_update(V, a.ld, w, r0, r1, ncols, hs);
   }
+  sqp = block_sum_d(sqp, red);
+  if (threadIdx.x == 0) a.sq[b] = sqp;
+  if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
+  double t = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) t += __ldcg(a.sq + q);
+  const double s = block_sum_d(t, red);
   // ---- new column (every block, own rows) and the Givens step (block 0)
   const double hn = sqrt(s);
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
@@ -1231,16 +1265,16 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
   if (maxc > 128) return cudaErrorInvalidValue;
   auto kern = gm_step_kernel<TAZ>;
   int occ = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGmThreads, 0);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int nblk = std::min(occ, 2) * num_sms;
-  if (nblk < maxc) return cudaErrorInvalidConfiguration;   // one block per column of h
+  const int nblk = num_sms;
+  if (nblk < maxc + 1) return cudaErrorInvalidConfiguration;   // one block per column of h and ||w||^2
   GmStepArgs<TAZ> a{V, ld, len, m, w, az, st, maxc, 0, Dp, sq, hsum, H, cs, sn, g, v32, bar, err};
   a.ldh = ldh;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kGmThreads);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
