@@ -157,7 +157,8 @@ def barrier_max(t, world):
         return t
     import torch
     import torch.distributed as dist
-    v = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    v = torch.tensor([t], dtype=torch.float64, device=dev)
     dist.all_reduce(v, op=dist.ReduceOp.MAX)
     return float(v.item())
 
