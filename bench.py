@@ -296,6 +296,9 @@ def run_ours(args):
             avg_ms = tot[k] / cnt[k]
             passes[k] = {"launches": cnt[k], "avg_us": avg_ms * 1e3, "gbs": by / (avg_ms * 1e-3) / 1e9,
                          "total_ms": tot[k], "bytes_per_launch": by}
+    # the FGMRES iteration's other kernels (latency- or FP64-bound): event-timed averages
+    others = {k: {"launches": cnt[k], "avg_us": tot[k] / cnt[k] * 1e3, "total_ms": tot[k]}
+              for k in ("arnoldi_step", "fgmres_trsv") if cnt.get(k)}
     nterms = 3 if WL["u_s"] == "bf16x3" else 1
     sk_flop = 2.0 * s * m * (n + 1) * nterms
     sk_ms = tot["sketch_gemm"] / max(1, cnt["sketch_gemm"])
@@ -373,7 +376,7 @@ def run_ours(args):
             "ir_hist": {"dx_rel": last["ir_dx_hist"], "dr_rel": last["ir_dr_hist"],
                         "gmres_its": last["gmres_its"], "gmres_relres": last["gmres_relres"]},
             "stage_ms": last["stage_ms"], "kappa_R_est": last["kappa_R_est"],
-            "sketch": sketch, "passes": passes,
+            "sketch": sketch, "passes": passes, "fgmres_other_kernels": others,
             "fp64_path": {"tts_ms": fp64_ms, "lsqr_its": info64.lsqr_its, "tol": tol64, "status": st64,
                           "speedup_of_mixed": fp64_ms / value},
             "single_term_sketch": {k: {kk: vv for kk, vv in v.items() if kk not in ("x", "r")}

@@ -135,9 +135,10 @@ typedef struct lsq_info {
   double ir_dx_hist[32];    /* ||dx_i|| / ||x_{i+1}|| of each refinement step */
   double ir_dr_hist[32];    /* ||dr_i|| / ||r_{i+1}|| of each refinement step */
   double gmres_relres[32];  /* FGMRES relative residual reached in each refinement step */
-  double kern_ms[4];        /* with opts->timing: summed device time of the sketch GEMM,
-                               LSQR pass, FGMRES pass and residual pass launches */
-  int64_t kern_launches[4]; /* number of launches behind each kern_ms entry */
+  double kern_ms[8];        /* with opts->timing: summed device time of the sketch GEMM (with its
+                               correction), LSQR pass, FGMRES pass, residual pass, FGMRES Arnoldi
+                               step and FGMRES triangular solves; two entries spare */
+  int64_t kern_launches[8]; /* number of launches behind each kern_ms entry */
 } lsq_info;
 
 /* sizeof(lsq_opts) for which = 0, sizeof(lsq_info) for which = 1, else 0: lets

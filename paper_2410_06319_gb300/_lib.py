@@ -26,7 +26,8 @@ STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RAN
 
 
 #: kernels timed with opts.timing (order of lsq_info.kern_ms)
-KERNELS = ["sketch_gemm", "lsqr_pass", "fgmres_pass", "residual_pass"]
+KERNELS = ["sketch_gemm", "lsqr_pass", "fgmres_pass", "residual_pass", "arnoldi_step", "fgmres_trsv",
+           "spare6", "spare7"]
 
 
 class Opts(ctypes.Structure):
@@ -51,7 +52,7 @@ class Info(ctypes.Structure):
                 ("stage_ms", ctypes.c_double * 8), ("gpu_launches", ctypes.c_int64),
                 ("ir_dx_hist", ctypes.c_double * 32), ("ir_dr_hist", ctypes.c_double * 32),
                 ("gmres_relres", ctypes.c_double * 32),
-                ("kern_ms", ctypes.c_double * 4), ("kern_launches", ctypes.c_int64 * 4)]
+                ("kern_ms", ctypes.c_double * 8), ("kern_launches", ctypes.c_int64 * 8)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

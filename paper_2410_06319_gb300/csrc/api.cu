@@ -68,8 +68,8 @@ struct lsq_handle {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::unordered_map<std::string, CachedGraph*> graphs;
   CachedGraph* cap = nullptr;          // graph being captured
-  double kern_acc[4] = {0, 0, 0, 0};
-  int64_t kern_cnt[4] = {0, 0, 0, 0};
+  double kern_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t kern_cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int device = 0;
   int num_sms = 0;
   std::unordered_map<std::string, Buf> bufs;
@@ -135,7 +135,7 @@ struct StageTimer {
 };
 
 enum Stage { ST_CAST = 0, ST_SKETCH, ST_QR, ST_LSQR, ST_RES, ST_FGMRES, ST_UPDATE, ST_TOTAL };
-enum Kern { K_SKETCH = 0, K_LSQR_PASS, K_FGM_PASS, K_RES_PASS };
+enum Kern { K_SKETCH = 0, K_LSQR_PASS, K_FGM_PASS, K_RES_PASS, K_ARNOLDI, K_TRSV, K_NKERN = 8 };
 constexpr int kKernMark = 100;   // marks with stage >= kKernMark time single kernels
 
 // Brackets one launch with events when timing is on (opts.timing).
@@ -594,18 +594,27 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
     for (int k = 0; k < kBatch; ++k) {
       const int* dn = &gst->done;
       const int* jp = &gst->j;
-      L((launch_trsv<TOP, double, TOP>(true, tri, V + m, 1.0, Zb, dn, c.st, jp, ld, ldz)));
+      {
+        KernTimer kt(c.h, K_TRSV, c.o.timing);
+        L((launch_trsv<TOP, double, TOP>(true, tri, V + m, 1.0, Zb, dn, c.st, jp, ld, ldz)));
+      }
       {
         KernTimer kt(c.h, K_FGM_PASS, c.o.timing);
         L(launch_pass_fgm<TOP>(Aop, ldop, m, n, Zb, vcoef, az, P, c.nblk, dn, c.st, jp, ldz, vstr,
                                c.h->d_err));
       }
       L((launch_colsum<TOP, TOP>(P, c.nblk, n, nullptr, 1.0, sb, dn, c.st)));
-      L((launch_trsv<TOP, TOP, double>(false, tri, sb, 1.0, wv + m, dn, c.st)));
+      {
+        KernTimer kt(c.h, K_TRSV, c.o.timing);
+        L((launch_trsv<TOP, TOP, double>(false, tri, sb, 1.0, wv + m, dn, c.st)));
+      }
       // classical Gram-Schmidt; the second pass runs only when the first one lost
       // more than half of ||w||^2 ("twice is enough"); Givens step; new column
-      L(launch_gm_step<TOP>(V, ld, wv, ld, m, az, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, v32, gbar,
-                            c.h->d_err, c.h->num_sms, c.st));
+      {
+        KernTimer kt(c.h, K_ARNOLDI, c.o.timing);
+        L(launch_gm_step<TOP>(V, ld, wv, ld, m, az, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, v32, gbar,
+                              c.h->d_err, c.h->num_sms, c.st));
+      }
     }
   };
   CachedGraph* G =
@@ -712,7 +721,7 @@ void finish_timing(lsq_handle* h, lsq_info* info) {
   CK(cudaStreamSynchronize(h->stream));
   if (info) {
     for (int k = 0; k < 8; ++k) info->stage_ms[k] = 0.0;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < K_NKERN; ++k) {
       info->kern_ms[k] = h->kern_acc[k];
       info->kern_launches[k] = h->kern_cnt[k];
     }
@@ -729,7 +738,7 @@ void finish_timing(lsq_handle* h, lsq_info* info) {
   }
   h->marks.clear();
   h->next_event = 0;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < K_NKERN; ++k) {
     h->kern_acc[k] = 0.0;
     h->kern_cnt[k] = 0;
   }
@@ -741,7 +750,7 @@ lsq_status run_guarded(lsq_handle* h, lsq_info* info, const std::function<lsq_st
   try {
     h->marks.clear();
     h->next_event = 0;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < K_NKERN; ++k) {
       h->kern_acc[k] = 0.0;
       h->kern_cnt[k] = 0;
     }
