@@ -635,7 +635,10 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
     else body();
     out = read_state<GmState>(c, gst);
     const int ran = std::min(kBatch, out.j - j);
-    if (c.o.timing) c.h->marks.resize(mark0 + ran);
+    if (c.o.timing) {   // keep the marks of the iterations that did work (same count per iteration)
+      const size_t per_it = (c.h->marks.size() - mark0) / kBatch;
+      c.h->marks.resize(mark0 + (size_t)ran * per_it);
+    }
     j = out.j;
     if (out.done || j >= maxit) break;
   }
