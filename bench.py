@@ -137,11 +137,20 @@ def measured_traffic(kernel):
     try:
         text = open(path).read()
         tb = int(re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M).group(1))
-        src, h = re.search(r"^source: (\S+) sha256\[:16\] ([0-9a-f]+)", text, re.M).groups()
-        cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+        srcs = re.findall(r'^source: (\S+)(?: from "(.+?)" to "(.+?)")? sha256\[:16\] ([0-9a-f]+)$', text, re.M)
+        if not srcs:
+            return None
+        for src, start, end, h in srcs:
+            body = open(os.path.join(ROOT, src), "rb").read()
+            if start:   # the kernel's own region of the file
+                t = body.decode()
+                i = t.index(start)
+                body = t[i:t.index(end, i)].encode()
+            if hashlib.sha256(body).hexdigest()[:16] != h:
+                return None
     except (OSError, AttributeError, ValueError):
         return None
-    return tb if cur == h else None
+    return tb
 
 
 def dist_setup():

@@ -55,29 +55,15 @@ cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n
 cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s);
 cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
                              int nblk, cudaStream_t s);
-// Classical Gram-Schmidt pass of an Arnoldi step (one of two).  mdot: h = V[:, 0..j]^T w
-// (with az, first forms w_top = V[:m, j] + az), H[:, j] += h.  axpy: w -= V h; after the
-// first pass it decides whether the second pass runs (Kahan: iff ||w'||^2 < (||w'||^2 +
-// ||h||^2) / 2) and, when it does not, or after the second pass, finishes the step
-// (h_{j+1,j} = ||w||, Givens rotation, residual estimate, j += 1).  `cnt` is a device
-// counter that is zero between launches (each launch leaves it zero).
-template <typename TAZ>
-cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
-                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m,
-                           bool second, unsigned* cnt, double* h, double* H, int ldh);
-cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
-                           GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second,
-                           unsigned* cnt, double* H, int ldh, double* cs, double* sn, double* g);
-// The whole Arnoldi step in one cooperative launch (same arithmetic as mdot / axpy /
-// newcol above, blocks synchronised by a bounded grid barrier on bar[0..1], which
-// must be zero between launches; each launch leaves it zero): needs maxc <= 128.
+// The whole Arnoldi step in one cooperative launch (classical Gram-Schmidt with the
+// twice-is-enough second pass, Givens step, new column; blocks synchronised by a
+// bounded grid barrier on bar[0..1], which must be zero before the first launch; each
+// launch leaves it reusable): needs maxc <= 128 and num_sms >= maxc + 1.
 template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
                            int num_sms, cudaStream_t s);
-cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
-                             float* v32, int64_t m, int nblk, cudaStream_t s);
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
                             cudaStream_t s);
 template <typename TB>

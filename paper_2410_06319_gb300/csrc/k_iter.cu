@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
 // one row of each stage.  Each CTA owns a contiguous range of rows.  The per-row
 // scalars of the next stage are loaded one stage ahead.
 //   PM_LSQR: q = A t + cu u ; u_out = q ; P = A^T q ; sq = sum q^2
-//   PM_FGM : az = A z ; P = A^T v            (v_top + az is formed by gm_mdot)
+//   PM_FGM : az = A z ; P = A^T v            (v_top + az is formed by the Arnoldi step)
 //   PM_RES : f = b - r - A x ; P = A^T (-r)
 constexpr int kBulkRows = 16;
 constexpr int kBulkThreads = (kBulkRows + 1) * 32;
@@ -963,63 +963,8 @@ __global__ void gm_init_kernel(const double* sq_partial, int nblk, GmState* st, 
   }
 }
 
-// partial dots of w with V[:, 0..j] over a row range: Dp[b][c]; one warp per
-// column (no block-wide barrier per column), w's range cached in L1.
-// The Arnoldi kernels end with a "last block" step: every block publishes its
-// partial results, counts itself done on a device counter, and the block that
-// finishes last (it sees every other block's partials) performs the small
-// reduction in a fixed order, then resets the counter.  No block waits for
-// another, and the results do not depend on block scheduling.
-__device__ __forceinline__ bool last_block_done(unsigned* cnt) {
-  __shared__ int last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == gridDim.x - 1) ? 1 : 0;
-  __syncthreads();
-  if (last) __threadfence();
-  return last != 0;
-}
-
-// Partial dot products Dp[b][c] = V[:, c]^T w over block b's rows for c <= j;
-// the last block sums them: h[c] = sum_b Dp[b][c], H[c][j] += h[c].
-template <typename TAZ>
-__global__ void gm_mdot_kernel(const double* __restrict__ V, int64_t ld, double* __restrict__ w,
-                               int64_t len, const GmState* st, int maxc, double* Dp,
-                               const TAZ* __restrict__ az, int64_t m, bool second, unsigned* cnt,
-                               double* h, double* H, int ldh) {
-  if (st->done || (second && !st->reorth)) return;
-  const int ncols = st->j + 1;
-  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(len, r0 + chunk);
-  if (az) {  // w_top = v_top + A z for this block's rows (the pass left A z in az)
-    const double* vj = V + (int64_t)(ncols - 1) * ld;
-    for (int64_t i = r0 + threadIdx.x; i < min(r1, m); i += blockDim.x) w[i] = vj[i] + (double)az[i];
-    __syncthreads();
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = warp; c < ncols; c += nw) {
-    const double* vc = V + (int64_t)c * ld;
-    double s = 0.0;
-    for (int64_t i = r0 + lane; i < r1; i += 32) s += vc[i] * w[i];
-    s = warp_sum(s);
-    if (lane == 0) Dp[(int64_t)blockIdx.x * maxc + c] = s;
-  }
-  if (!last_block_done(cnt)) return;
-  const int nblk = gridDim.x;
-  for (int c = warp; c < ncols; c += nw) {
-    double t = 0.0;
-    for (int b = lane; b < nblk; b += 32) t += __ldcg(Dp + (int64_t)b * maxc + c);
-    t = warp_sum(t);
-    if (lane == 0) {
-      h[c] = t;
-      H[(int64_t)st->j * ldh + c] += t;
-    }
-  }
-  if (threadIdx.x == 0) *cnt = 0u;
-}
-
 // h_{j+1,j} = sqrt(s) ; Givens rotations on column j ; residual estimate ; j++.
-// One block (the last block of the Gram-Schmidt update).
+// One block (block 0 of the Arnoldi step).
 __device__ void gm_finish_block(double s, GmState* st, double* H, int ldh, double* cs, double* sn,
                                 double* g) {
   __shared__ double hcs[130], css[130], sns[130];
@@ -1053,50 +998,6 @@ __device__ void gm_finish_block(double s, GmState* st, double* H, int ldh, doubl
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = hcs[i];
-}
-
-// w[i] -= sum_c V[c][i] h[c] with partial ||w||^2 per block; the last block then
-// (first pass) applies Kahan's "twice is enough" test -- the second pass is
-// needed when the update lost more than half of ||w||^2 -- and, when no second
-// pass follows, or (second pass) always, finishes the Arnoldi step.
-__global__ void gm_axpy_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
-                               double* __restrict__ w, int64_t len, GmState* st, double* sq_partial,
-                               bool second, unsigned* cnt, double* H, int ldh, double* cs, double* sn,
-                               double* g) {
-  if (st->done || (second && !st->reorth)) return;
-  __shared__ double hs[128];
-  __shared__ double red[33];
-  const int ncols = st->j + 1;
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = h[c];
-  __syncthreads();
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = w[i];
-    for (int c = 0; c < ncols; ++c) acc -= V[(int64_t)c * ld + i] * hs[c];
-    w[i] = acc;
-    s += acc * acc;
-  }
-  s = block_sum_d(s, red);
-  if (threadIdx.x == 0) sq_partial[blockIdx.x] = s;
-  if (!last_block_done(cnt)) return;
-  double t = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(sq_partial + b);
-  t = block_sum_d(t, red);
-  bool finish = true;
-  if (!second) {
-    double hh = 0.0;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hh += hs[c] * hs[c];
-    hh = block_sum_d(hh, red);
-    const int need = (t < 0.5 * (t + hh)) ? 1 : 0;
-    if (threadIdx.x == 0) {
-      st->reorth = need;
-      st->nreorth += need;
-    }
-    finish = !need;
-  }
-  if (finish) gm_finish_block(t, st, H, ldh, cs, sn, g);
-  if (threadIdx.x == 0) *cnt = 0u;
 }
 
 // ---------------------------------------------------------------- fused Arnoldi step
@@ -1290,20 +1191,6 @@ template cudaError_t launch_gm_step<double>(double*, int64_t, double*, int64_t, 
                                             GmState*, int, double*, double*, double*, double*, int, double*,
                                             double*, double*, float*, unsigned*, int*, int, cudaStream_t);
 
-// V[:, j] = w * inv_h  (j read after gm_finish incremented it)
-__global__ void gm_newcol_kernel(const double* __restrict__ w, int64_t len, const GmState* st,
-                                 double* __restrict__ V, int64_t ld, float* __restrict__ v32, int64_t m) {
-  if (st->done) return;
-  const double s = st->inv_h;
-  double* vc = V + (int64_t)st->j * ld;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = w[i] * s;
-    vc[i] = v;
-    if (v32 && i < m) v32[i] = (float)v;
-  }
-}
-
 // y = H[:k,:k]^-1 g[:k]  (k = st->j): one warp, column-oriented back substitution
 __global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, const double* g, double* y) {
   extern __shared__ double hs[];   // k x k, column-major
@@ -1353,30 +1240,6 @@ __global__ void gm_apply_kernel(const TB* __restrict__ B, int64_t ld, int64_t le
 
 cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s) {
   gm_init_kernel<<<1, 256, 0, s>>>(sq_partial, nblk, st, g);
-  return cudaGetLastError();
-}
-template <typename TAZ>
-cudaError_t launch_gm_mdot(const double* V, int64_t ld, double* w, int64_t len, const GmState* st,
-                           int maxc, double* Dp, int nblk, cudaStream_t s, const TAZ* az, int64_t m,
-                           bool second, unsigned* cnt, double* h, double* H, int ldh) {
-  gm_mdot_kernel<TAZ><<<nblk, 256, 0, s>>>(V, ld, w, len, st, maxc, Dp, az, m, second, cnt, h, H, ldh);
-  return cudaGetLastError();
-}
-template cudaError_t launch_gm_mdot<float>(const double*, int64_t, double*, int64_t, const GmState*, int,
-                                           double*, int, cudaStream_t, const float*, int64_t, bool,
-                                           unsigned*, double*, double*, int);
-template cudaError_t launch_gm_mdot<double>(const double*, int64_t, double*, int64_t, const GmState*, int,
-                                            double*, int, cudaStream_t, const double*, int64_t, bool,
-                                            unsigned*, double*, double*, int);
-cudaError_t launch_gm_axpy(const double* V, int64_t ld, const double* h, double* w, int64_t len,
-                           GmState* st, double* sq_partial, int nblk, cudaStream_t s, bool second,
-                           unsigned* cnt, double* H, int ldh, double* cs, double* sn, double* g) {
-  gm_axpy_kernel<<<nblk, 256, 0, s>>>(V, ld, h, w, len, st, sq_partial, second, cnt, H, ldh, cs, sn, g);
-  return cudaGetLastError();
-}
-cudaError_t launch_gm_newcol(const double* w, int64_t len, const GmState* st, double* V, int64_t ld,
-                             float* v32, int64_t m, int nblk, cudaStream_t s) {
-  gm_newcol_kernel<<<nblk, 256, 0, s>>>(w, len, st, V, ld, v32, m);
   return cudaGetLastError();
 }
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
