@@ -1012,11 +1012,28 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     }
     CK(cudaMemcpyAsync(x, x0, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
     CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
+    // FP64 products stream A in 16-byte pieces: an odd row stride (or an unaligned A)
+    // gets an even-stride, zero-padded copy first
+    auto a64 = [&](int64_t* ld) -> const double* {
+      if ((reinterpret_cast<uintptr_t>(c.A) & 15) == 0 && c.lda % 2 == 0) {
+        *ld = c.lda;
+        return c.A;
+      }
+      const int64_t lp = round_up(c.n, 2);
+      double* Ap = static_cast<double*>(ws(c.h, "A64p", (size_t)c.m * lp * 8));
+      CK(cudaMemsetAsync(Ap, 0, (size_t)c.m * lp * 8, c.st));
+      CK(cudaMemcpy2DAsync(Ap, lp * 8, c.A, c.lda * 8, c.n * 8, c.m, cudaMemcpyDeviceToDevice, c.st));
+      *ld = lp;
+      return Ap;
+    };
     bool conv;
-    if (c.uw == LSQ_F32)
+    if (c.uw == LSQ_F32) {
       conv = stage_refine<float>(c, fr.a32, c.lda32, fr.rc, x, rr, inf);
-    else
-      conv = stage_refine<double>(c, c.A, c.lda, fr.rc, x, rr, inf);
+    } else {
+      int64_t ldp;
+      const double* Ap = a64(&ldp);
+      conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf);
+    }
     const double kap = c.o.kappa_hint > 0 ? c.o.kappa_hint : inf->kappa_R_est;
     if (!conv && !c.o.no_escalate && kap < 1.0 / unit_roundoff(c.us) && c.uw == LSQ_F32) {
       // Sec. 5: re-run the refinement from (x0, r0) with u_A = u_L = u_R = u^2 (FP64 here)
@@ -1024,7 +1041,9 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
       CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
       inf->escalated = 1;
       inf->flags |= LSQ_INFO_ESCALATED;
-      conv = stage_refine<double>(c, c.A, c.lda, fr.rc, x, rr, inf);
+      int64_t ldp;
+      const double* Ap = a64(&ldp);
+      conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf);
     }
     inf->ir_converged = conv ? 1 : 0;
     return conv ? LSQ_OK : LSQ_NOT_CONVERGED;

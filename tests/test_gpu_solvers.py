@@ -152,6 +152,36 @@ def test_escalation_rule(lsq, handle):
     assert info.escalated == 0
 
 
+@pytest.mark.parametrize("n", [101, 37])
+def test_fp64_refinement_with_odd_row_stride(lsq, handle, n):
+    """FP64 FGMRES products (Sec. 5's escalation, and u = FP64) on an A whose rows
+    are not a multiple of 16 bytes: the solve runs on a padded copy."""
+    m, s, kappa = 2000, 4 * n, 1e2
+    P = randsvd_problem(m, n, kappa, rho=1e-2, seed=n)
+    xe, re = exact.reference_solution(P.A, P.b)
+    x, r = zeros(n), zeros(m)
+    st, info = lsq.lsq_lsir(handle, dev(P.A), dev(P.b), m, n, s, "f16", "f32", "f32", "f64", 1e-6, 0,
+                            {"ir_maxit": 1, "gmres_maxit": 2, "kappa_hint": 10.0}, x, r)
+    assert info.escalated == 1
+    assert np.linalg.norm(x.cpu().numpy() - xe) <= 1e-6 * np.linalg.norm(xe)
+    # u = u_r = FP64: the residual is no more accurate than the working precision,
+    # so the corrections stall at the rounding level and the ||d|| <= u rule does
+    # not fire (the oracle with plain FP64 residuals does the same); the forward
+    # errors still reach the level of the oracle's
+    its = 3
+    x, r = zeros(n), zeros(m)
+    st, info = lsq.lsq_lsir(handle, dev(P.A), dev(P.b), m, n, s, "bf16", "f64", "f64", "f64", 1e-15, 0,
+                            {"ir_maxit": its}, x, r)
+    Y = sketch.sketch(P.A, P.b, s, 0, "bf16")
+    R, c = qr.householder_qr(Y, n)
+    xo, ro, io = lsir.lsir(P.A, P.b, R, qr.sketch_and_solve(R, c), 2.0 ** -53, 1e-15, ir_maxit=its,
+                           w_dtype=np.float64, ur="f64")
+    assert st == (0 if io["converged"] else 1) and info.ir_its == io["its"]
+    ex, er = exact.forward_errors(x.cpu().numpy(), r.cpu().numpy(), xe, re)
+    exo, ero = exact.forward_errors(xo, ro, xe, re)
+    assert ex <= max(10 * exo, 1e-14) and er <= max(10 * ero, 1e-12), (ex, er, exo, ero)
+
+
 def test_invalid_and_degenerate_inputs(lsq, handle):
     P = randsvd_problem(300, 5, 10.0, seed=2)
     x = zeros(5)
