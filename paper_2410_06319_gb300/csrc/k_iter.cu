@@ -69,9 +69,8 @@ struct PassArgs {
   T* uout;
   const double* cu_ptr;
   double cu_mul;
-  const double* v;       // FGMRES
-  const double* vs_ptr;
-  double* wtop;
+  const T* v;            // FGMRES coefficient vector
+  T* az;                 // FGMRES: A x
   const double* r;       // residual
   const double* b;
   double* f;
@@ -108,9 +107,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
     for (int k = 0; k < VW; ++k) acc[v][k] = T(0);
   }
   T cu = T(0);
-  double vs = 1.0;
   if (MODE == PM_LSQR) cu = (T)((p.cu_ptr ? *p.cu_ptr : 1.0) * p.cu_mul);
-  if (MODE == PM_FGM) vs = p.vs_ptr ? *p.vs_ptr : 1.0;
   double sqacc = 0.0;
   for (int64_t i = gw; i < p.m; i += 2 * tw) {
     const int64_t i2 = i + tw;
@@ -159,13 +156,11 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
         }
       }
     } else if (MODE == PM_FGM) {
-      const double vi = p.v[i] * vs;
-      c1 = (T)vi;
-      if (lane == 0) p.wtop[i] = vi + (double)d;
+      c1 = p.v[i];
+      if (lane == 0) p.az[i] = d;
       if (has2) {
-        const double vi2 = p.v[i2] * vs;
-        c2 = (T)vi2;
-        if (lane == 0) p.wtop[i2] = vi2 + (double)d2;
+        c2 = p.v[i2];
+        if (lane == 0) p.az[i2] = d2;
       }
     } else {
       const double ri = p.r[i];
@@ -469,13 +464,30 @@ static int f64_vw(const double* A, int64_t lda, int64_t n) {
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// The bulk-streamed ring needs two stages of kBulkRows rows within its 200 KB of
+// shared memory and a bulk instantiation for the row's vector count; wider rows
+// (FP64 beyond 800 columns) take the register-blocked pass kernel instead.
+template <typename T, int VW>
+static bool bulk_fits(int64_t lda, int64_t nv) {
+  const int64_t vpl = (nv + 31) / 32;
+  return 2 * (size_t)kBulkRows * (size_t)lda * sizeof(T) <= (size_t)200 * 1024 &&
+         (vpl <= 8 || (VW <= 2 && vpl <= 16));
+}
+
 template <typename T>
 cudaError_t launch_pass_lsqr_t(const T* A, int64_t lda, int64_t m, int64_t n, const T* t,
                                const T* u_in, const double* cu_ptr, double cu_mul, T* u_out, T* Pblk,
                                double* sq, int nblk, const int* done, cudaStream_t st) {
   int vw = 4;
-  if constexpr (sizeof(T) == 8) vw = f64_vw(A, lda, n);
-  if (aligned16(A) && (sizeof(T) == 4 || lda % 2 == 0)) {
+  bool bulk = aligned16(A);
+  if constexpr (sizeof(T) == 4) {
+    bulk = bulk && bulk_fits<float, 4>(lda, (lda + 3) / 4);
+  } else {
+    vw = f64_vw(A, lda, n);
+    bulk = bulk && lda % 2 == 0 &&
+           (vw == 2 ? bulk_fits<double, 2>(lda, n / 2) : bulk_fits<double, 1>(lda, n));
+  }
+  if (bulk) {
     BulkArgs<T> b{};
     b.A = A; b.lda = lda; b.m = m; b.n = (int)n;
     b.x = t; b.uin = u_in; b.uout = u_out; b.cu_ptr = cu_ptr; b.cu_mul = cu_mul;
@@ -529,15 +541,26 @@ cudaError_t launch_pass_fgm(const TA* A, int64_t lda, int64_t m, int64_t n, cons
     b.nv = (int)((lda + 3) / 4);
     return dispatch_bulk<float, 4, PM_FGM>(b, nblk, 0, st);
   } else {
-    if (!aligned16(A) || (lda % 2) != 0) {
-      return cudaErrorInvalidValue;
+    const int vw = f64_vw(A, lda, n);
+    if (aligned16(A) && (lda % 2) == 0 &&
+        (vw == 2 ? bulk_fits<double, 2>(lda, n / 2) : bulk_fits<double, 1>(lda, n))) {
+      if (vw == 2) {
+        b.nv = (int)(n / 2);
+        return dispatch_bulk<double, 2, PM_FGM>(b, nblk, 0, st);
+      }
+      b.nv = (int)n;
+      return dispatch_bulk<double, 1, PM_FGM>(b, nblk, 0, st);
     }
-    if (f64_vw(A, lda, n) == 2) {
-      b.nv = (int)(n / 2);
-      return dispatch_bulk<double, 2, PM_FGM>(b, nblk, 0, st);
+    PassArgs<double> q{};
+    q.A = A; q.lda = lda; q.m = m; q.n = (int)n;
+    q.x = z; q.v = v; q.az = az; q.Pblk = Pblk; q.done = done;
+    q.jp = jp; q.xstr = zs; q.vstr = vstr;
+    if (vw == 2) {
+      q.nv = (int)(n / 2);
+      return dispatch_pass<double, 2, PM_FGM>(q, nblk, st);
     }
-    b.nv = (int)n;
-    return dispatch_bulk<double, 1, PM_FGM>(b, nblk, 0, st);
+    q.nv = (int)n;
+    return dispatch_pass<double, 1, PM_FGM>(q, nblk, st);
   }
 }
 template cudaError_t launch_pass_fgm<float>(const float*, int64_t, int64_t, int64_t, const float*,
@@ -550,7 +573,9 @@ template cudaError_t launch_pass_fgm<double>(const double*, int64_t, int64_t, in
 cudaError_t launch_pass_res(const double* A, int64_t lda, int64_t m, int64_t n, const double* x,
                             const double* r, const double* b, double* f, double* Pblk, int nblk,
                             cudaStream_t st) {
-  if (aligned16(A) && lda % 2 == 0) {
+  const int vw = f64_vw(A, lda, n);
+  if (aligned16(A) && lda % 2 == 0 &&
+      (vw == 2 ? bulk_fits<double, 2>(lda, n / 2) : bulk_fits<double, 1>(lda, n))) {
     BulkArgs<double> q{};
     q.A = A; q.lda = lda; q.m = m; q.n = (int)n;
     q.x = x; q.r = r; q.b = b; q.f = f; q.Pblk = Pblk;

@@ -182,6 +182,32 @@ def test_fp64_refinement_with_odd_row_stride(lsq, handle, n):
     assert ex <= max(10 * exo, 1e-14) and er <= max(10 * ero, 1e-12), (ex, er, exo, ero)
 
 
+@pytest.mark.parametrize("n", [1000, 901])
+def test_fp64_products_on_rows_wider_than_the_bulk_ring(lsq, handle, n):
+    """FP64 rows of more than 800 columns (n = 1000 in the largest configurations) do not
+    fit two stages of the bulk-streamed ring: the residual pass, the escalated FGMRES
+    products and the all-FP64 LSQR run on the register-blocked pass instead."""
+    m, s, kappa = 6000, 4 * n, 1e2
+    P = randsvd_problem(m, n, kappa, rho=1e-2, seed=n)
+    xt = P.x_true                      # the stored-data solution is within ~1e-14 of it here
+    x, r = zeros(n), zeros(m)
+    st, info = lsq.lsq_lsir(handle, dev(P.A), dev(P.b), m, n, s, "f16", "f32", "f32", "f64", 1e-6, 0,
+                            {"ir_maxit": 1, "gmres_maxit": 2, "kappa_hint": 10.0}, x, r)
+    assert info.escalated == 1
+    assert np.linalg.norm(x.cpu().numpy() - xt) <= 1e-6 * np.linalg.norm(xt)
+    x, r = zeros(n), zeros(m)
+    st, info = lsq.lsq_lsir(handle, dev(P.A), dev(P.b), m, n, s, "bf16x3", "f32", "f32", "f64", 1e-6, 0,
+                            None, x, r)
+    rp = P.b - P.A @ xt
+    ex = np.linalg.norm(x.cpu().numpy() - xt) / np.linalg.norm(xt)
+    er = np.linalg.norm(r.cpu().numpy() - rp) / np.linalg.norm(rp)
+    assert st == 0 and ex <= 4 * 2.0 ** -24 and er <= 4 * 2.0 ** -24, (ex, er)
+    x = zeros(n)
+    st, info = lsq.lsq_lsqr(handle, dev(P.A), dev(P.b), m, n, s, "f64", "f64", "f64", "f64", 1e-14, 0,
+                            None, x)
+    assert st == 0 and np.linalg.norm(x.cpu().numpy() - xt) <= 1e-12 * kappa * np.linalg.norm(xt)
+
+
 def test_invalid_and_degenerate_inputs(lsq, handle):
     P = randsvd_problem(300, 5, 10.0, seed=2)
     x = zeros(5)
