@@ -17,5 +17,8 @@ Right-hand sides:
 * ``kind='consistent+perp'``: b = A x_true + r_perp with x_true ~ N(0, I),
   r_perp = (I - U U^T) g scaled so that ||r_perp|| / ||b|| = rho.
 * ``kind='uniform'``: b ~ U(0, 1) normalised to unit norm (Sec. 5).
+
+The largest shapes are drawn on the device instead (``device.DeviceRandsvd``,
+same construction, torch's seeded generator).
 """
 from .problems import Problem, randsvd_problem, paper_problem, batch_specs  # noqa: F401

@@ -1,0 +1,155 @@
+"""The largest configurations at full size through the C ABI.
+
+* m = 1e6, n = 1000, s = 3n, kappa in {10, 1e3}, ||r_perp|| / ||b|| = 1e-2:
+  E4M3 (column-scaled) against FP16 sketches, FP64 QR; where kappa u_s
+  leaves the regime of Sec. 3 the preconditioner fails (kappa(A R^-1) grows
+  in proportion to kappa u_s, Fig. 3a) and LSQR slows down.  Fig. 3a puts
+  the constant near 3; with per-column power-of-two scaling each entry's cast
+  error is relative to that entry, and the constant is 0.1 to 0.3 (oracle
+  sketches of the same recipe at m = 3e4), so the bounds below span
+  [0.03, 3] kappa u_s.
+* m = 4e6, n = 1000, s = 4n, kappa = 1e7, ||r_perp|| / ||b|| = 1e-6: BF16
+  sketch (broken there, kappa u_s = 3.9e4) and the three-term BF16 split
+  (single precision), FP64 QR.  Here the FP32 accumulation of the tensor
+  cores, not the cast, bounds the split sketch.
+
+Checked against the oracle on sampled outputs (rows of Omega from its own
+Philox and Box-Muller, sampled columns of A) and against properties that hold
+at any size: R^T R = Y^T Y, and kappa(A R^-1) exactly from the generator's
+factors (A = U Sigma V^T with orthonormal U, so sigma(A R^-1) = sigma(Sigma
+V^T R^-1)) against the Marchenko-Pastur value (1 + sqrt(n/s)) / (1 - sqrt(n/s))
+of a good sketch.  Inputs are drawn on the device (lsq_synth.device).
+"""
+import numpy as np
+import pytest
+import torch
+
+from conftest import from_colmajor
+from oracle import rng, sketch
+
+pytestmark = pytest.mark.gpu
+
+U_S = {"f16": 2.0 ** -11, "e4m3": 2.0 ** -4, "bf16": 2.0 ** -8, "bf16x3": 2.0 ** -24}
+
+
+def kappa_mp(n, s):
+    q = np.sqrt(n / s)
+    return (1 + q) / (1 - q)
+
+
+def check_sampled_sketch(Y, A, b, s, fmt, seed, r):
+    """Entries of Y (device, column-major s x (n+1)) at sampled rows and columns
+    against the oracle's sum over all m products, one entry at a time."""
+    m, n = A.shape
+    cols = np.sort(r.choice(n, 40, replace=False))
+    rows = np.sort(r.choice(s, 3, replace=False))
+    Yc = Y.view(n + 1, s)
+    got = Yc[torch.as_tensor(np.append(cols, n), device=Y.device)].cpu().numpy()   # (k+1) x s
+    As, bs, kA, kb = sketch.cast_scaled(A[:, torch.as_tensor(cols, device=A.device)].cpu().numpy(),
+                                        b.cpu().numpy(), fmt)
+    Ab = np.column_stack([As, bs])
+    k = np.concatenate([kA, [kb]])
+    for i in rows:
+        g = rng.round_to_format(rng.gaussian_block(int(i), int(i) + 1, 0, m, seed), rng.OPERAND_FORMAT[fmt])
+        ref = np.ldexp((g @ Ab)[0] / np.sqrt(s), -k)
+        mag = np.ldexp((np.abs(g) @ np.abs(Ab))[0] / np.sqrt(s), -k)
+        err = np.abs(got[:, i] - ref)
+        assert np.all(err <= (m + 2) * 2.0 ** -24 * mag)
+        assert np.sqrt(np.mean((err / mag) ** 2)) <= 8 * np.sqrt(m) * 2.0 ** -24
+
+
+def qr_of_sketch(lsq, h, A, b, Y, s, fmt):
+    m, n = A.shape
+    R, xs = (torch.zeros(n * n, dtype=torch.float64, device="cuda"),
+             torch.zeros(n, dtype=torch.float64, device="cuda"))
+    lsq.lsq_qr_r(h, A, b, m, n, s, fmt, "f64", "f32", "f64", 1e-6, 0, {"Y_in": Y}, R, xs)
+    Rh = np.triu(from_colmajor(R, n, n))
+    Y1 = from_colmajor(Y, s, n + 1)[:, :n]
+    # Householder QR in FP64: R^T R = Y^T Y up to the rounding of the factorization
+    assert np.all(np.diag(Rh) > 0)
+    assert np.linalg.norm(Rh.T @ Rh - Y1.T @ Y1, 2) <= 1e-11 * np.linalg.norm(Y1, 2) ** 2
+    return R, Rh, xs
+
+
+def kappa_AR(gen, kappa, Rh):
+    SVt = gen.sigma(kappa)[:, None] * gen.V.T.cpu().numpy()
+    M = np.linalg.solve(Rh.T, SVt.T).T                      # Sigma V^T R^-1
+    sv = np.linalg.svd(M, compute_uv=False)
+    return sv[0] / sv[-1]
+
+
+@pytest.fixture(scope="module")
+def big_handle(lsq):
+    h = lsq.Handle()
+    yield h
+    h.close()
+    torch.cuda.empty_cache()
+
+
+def test_m1e6_n1000_e4m3_against_f16(lsq, big_handle):
+    from lsq_synth.device import DeviceRandsvd
+    m, n, s = 1_000_000, 1000, 3000
+    gen = DeviceRandsvd(m, n, seed=2)
+    r = np.random.default_rng(2)
+    kmp = kappa_mp(n, s)
+    seen = {}
+    for kappa in (10.0, 1e3):
+        A, b, _ = gen.problem(kappa, 1e-2)
+        for fmt in ("f16", "e4m3"):
+            Y = torch.full((s * (n + 1),), float("nan"), dtype=torch.float64, device="cuda")
+            lsq.lsq_sketch(big_handle, A, b, m, n, s, fmt, "f64", "f32", "f64", 1e-6, 0, None, Y)
+            check_sampled_sketch(Y, A, b, s, fmt, 0, r)
+            R, Rh, xs = qr_of_sketch(lsq, big_handle, A, b, Y, s, fmt)
+            kar = kappa_AR(gen, kappa, Rh)
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st, info = lsq.lsq_lsqr(big_handle, A, b, m, n, s, fmt, "f64", "f32", "f64", 1e-6, 0,
+                                    {"R_in": R, "x0_in": xs, "lsqr_maxit": 400}, x)
+            seen[(fmt, kappa)] = (kar, info.lsqr_its, st, info.flags)
+            print(fmt, kappa, "kappa(A R^-1) =", kar, "LSQR its", info.lsqr_its, "status", st)
+        del A, b
+    gen.release()
+    torch.cuda.empty_cache()
+    # kappa u_s << 1: the Marchenko-Pastur value of a Gaussian sketch with gamma = 3
+    kar, its, st, _ = seen[("f16", 10.0)]
+    assert 0.93 * kmp <= kar <= 1.07 * kmp and st == 0 and its <= 40
+    # kappa u_s = 62.5 for E4M3 at kappa = 1e3: the preconditioner fails; kappa(A R^-1)
+    # grows in proportion to kappa u_s (Fig. 3a), several times the good-sketch value
+    kar, its, st, flags = seen[("e4m3", 1e3)]
+    ku = 1e3 * U_S["e4m3"]
+    assert kar >= 3 * kmp and 0.03 * ku <= kar <= 3 * ku
+    assert its >= 2 * seen[("f16", 10.0)][1]
+    # borderline cases (kappa u_s = 0.49 and 0.63) stay within a small factor of the good value
+    for key in (("f16", 1e3), ("e4m3", 10.0)):
+        assert seen[key][0] <= 3 * kmp and seen[key][2] == 0
+
+
+def test_m4e6_n1000_kappa1e7_bf16_and_split_sketch(lsq, big_handle):
+    from lsq_synth.device import DeviceRandsvd
+    m, n, s, kappa, rho = 4_000_000, 1000, 4000, 1e7, 1e-6
+    gen = DeviceRandsvd(m, n, seed=4)
+    A, b, rperp = gen.problem(kappa, rho)
+    r = np.random.default_rng(4)
+    kars = {}
+    for fmt in ("bf16", "bf16x3"):
+        Y = torch.full((s * (n + 1),), float("nan"), dtype=torch.float64, device="cuda")
+        lsq.lsq_sketch(big_handle, A, b, m, n, s, fmt, "f64", "f32", "f64", 1e-6, 0, None, Y)
+        check_sampled_sketch(Y, A, b, s, fmt, 0, r)
+        _, Rh, _ = qr_of_sketch(lsq, big_handle, A, b, Y, s, fmt)
+        kars[fmt] = kappa_AR(gen, kappa, Rh)
+        print(fmt, "kappa(A R^-1) =", kars[fmt])
+        del Y
+    # BF16: kappa u_s = 3.9e4, far outside Sec. 3's condition; kappa(A R^-1) grows in
+    # proportion to kappa u_s (Fig. 3a)
+    ku = kappa * U_S["bf16"]
+    assert 0.03 * ku <= kars["bf16"] <= 3 * ku
+    # The split sketch casts A to single precision, but the tensor cores add the
+    # products in FP32: the product term of Sec. 3.2's bound on the sketching error
+    # (m^1/2 gamma_m) with FP32 for the accumulation, about 2^-24 sqrt(k/2) relative
+    # per entry for split-K chunks of k rows of A (a random walk of roundings),
+    # which kappa turns into kappa(A R^-1) of the order of kappa 2^-24 sqrt(k/2):
+    # far below BF16's, above the good-sketch value at this kappa and m
+    assert 0.9 * kappa_mp(n, s) <= kars["bf16x3"] <= min(kars["bf16"] / 5,
+                                                           2 * kappa * 2.0 ** -24 * np.sqrt(m / 2))
+    del A, b, rperp
+    gen.release()
+    torch.cuda.empty_cache()
