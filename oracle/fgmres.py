@@ -15,15 +15,19 @@ Readings where the paper is silent: x0 = 0, no restart, modified
 Gram-Schmidt Arnoldi and Givens rotations in FP64, stop when the residual
 estimate |g_{k+1}| <= tol ||s||, at most ``maxit`` iterations (50 in Sec. 5).
 The products with Atilde, M_L^-1 and M_R^-1 are formed in ``op_dtype``
-(u_A = u_L = u_R).
+(u_A = u_L = u_R).  ``work_dtype`` is the precision of everything else (the
+basis, the Gram-Schmidt and the rotations): FP64 by default (the GPU path's
+choice); the paper's own setting (Sec. 4: the remaining computations in u) is
+``work_dtype = u``.
 """
 import numpy as np
 
 from .qr import solve_upper, solve_upper_t
 
 
-def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64):
+def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64, work_dtype=np.float64):
     """Solve M_L^-1 Atilde M_R^-1 y = [f; h]; return (dr, dx, info)."""
+    wd = work_dtype
     A64 = np.asarray(A, dtype=np.float64)
     m, n = A64.shape
     Ao = A64.astype(op_dtype)
@@ -35,19 +39,19 @@ def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64):
         zt = vtop.astype(op_dtype)
         wt = zt + Ao @ zb
         wb = solve_upper_t(Ro, (Ao.T @ zt).astype(op_dtype)).astype(op_dtype)
-        return zb.astype(np.float64), np.concatenate([wt, wb]).astype(np.float64)
+        return zb.astype(wd), np.concatenate([wt, wb]).astype(wd)
 
-    rhs = np.concatenate([np.asarray(f, np.float64), np.asarray(h, np.float64)])
+    rhs = np.concatenate([np.asarray(f, np.float64), np.asarray(h, np.float64)]).astype(wd)
     beta = np.linalg.norm(rhs)
     info = dict(its=0, relres=0.0, converged=True)
     if beta == 0:
         return np.zeros(m), np.zeros(n), info
-    V = np.zeros((m + n, maxit + 1))
-    Zb = np.zeros((n, maxit))
-    H = np.zeros((maxit + 1, maxit))
-    cs = np.zeros(maxit)
-    sn = np.zeros(maxit)
-    g = np.zeros(maxit + 1)
+    V = np.zeros((m + n, maxit + 1), dtype=wd)
+    Zb = np.zeros((n, maxit), dtype=wd)
+    H = np.zeros((maxit + 1, maxit), dtype=wd)
+    cs = np.zeros(maxit, dtype=wd)
+    sn = np.zeros(maxit, dtype=wd)
+    g = np.zeros(maxit + 1, dtype=wd)
     g[0] = beta
     V[:, 0] = rhs / beta
     k = 0
@@ -78,5 +82,5 @@ def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64):
     y = solve_upper(H[:k, :k], g[:k])
     dr = V[:m, :k] @ y
     dx = Zb[:, :k] @ y
-    info.update(its=k, relres=relres, converged=relres <= tol)
-    return dr, dx, info
+    info.update(its=k, relres=float(relres), converged=bool(relres <= tol))
+    return dr.astype(np.float64), dx.astype(np.float64), info
