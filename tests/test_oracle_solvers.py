@@ -85,6 +85,28 @@ def test_lsqr_iteration_counts_match_paper_tables(golden):
         assert abs(np.mean(got) - int(its)) <= 2, (table, kappa, us, got, its)
 
 
+def test_lsqr_forward_errors_match_paper_tables(golden):
+    """Tables 1-2 print LSQR's forward errors against x*, r*.  The oracle's (geometric
+    mean over three draws of the recipe) lie within a factor 2 of them for kappa <= 1e2
+    and within 8 beyond, where one realisation's error varies more with kappa."""
+    for table, kappa, us, u, px, pr in golden("paper_lsqr_errors.txt"):
+        kappa, px, pr = float(kappa), float(px), float(pr)
+        fmt = {"single": "f32", "double": "f64"}[us]
+        dt = np.float32 if u == "single" else np.float64
+        tol = 1e-6 if u == "single" else 1e-12
+        errs = []
+        for seed in range(3):
+            P = paper_problem(kappa, seed=seed)
+            xstar, rstar = exact.reference_solution(P.A, P.b)
+            Y = sketch.sketch(P.A, P.b, 400, seed, fmt)
+            R, c = qr.householder_qr(Y, 100, dtype=dt)
+            x, _ = lsqr.lsqr(P.A, P.b, R, qr.sketch_and_solve(R, c), tol, 200, dtype=dt)
+            errs.append(exact.forward_errors(x, P.b - P.A @ x, xstar, rstar))
+        gx, gr = np.exp(np.mean(np.log(errs), axis=0))
+        f = 2.0 if kappa <= 1e2 else 8.0
+        assert px / f <= gx <= px * f and pr / f <= gr <= pr * f, (table, kappa, gx, gr, px, pr)
+
+
 def _dense_aug_prec(A, R):
     m, n = A.shape
     Ri = np.linalg.inv(R)
