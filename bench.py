@@ -185,8 +185,7 @@ def oracle_step(P, gpu_iters, m_sample):
     The oracle runs Algorithm 1 (BF16 sketch, FP32 Householder QR) and a fixed
     number of LSQR and FGMRES iterations on the first m_sample rows; each
     stage's time is scaled to the full m (linear in m for the sketch and the
-    passes, independent of m for the QR) and to the iteration counts the GPU
-    solve used.
+    passes, independent of m for the QR) and to the given iteration counts.
     """
     from oracle import fgmres, lsqr, qr, sketch
     A = P.A[:m_sample]
@@ -215,8 +214,15 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
+    from oracle import workload_counts
+    counts = workload_counts.load()
+    for k, v in counts["workload"].items():
+        if WL[k] != v:
+            raise SystemExit(f"oracle/workload_counts.json is for {k}={v}, the workload has {WL[k]}: "
+                             "rerun python -m oracle.workload_counts")
     P = make_problem()
-    iters = {"lsqr": 2 * WL["n"], "fgmres": 30 * 50}
+    # the oracle's own iteration counts on this workload (its full solve, run once)
+    iters = {"lsqr": counts["lsqr_its"], "fgmres": counts["fgmres_total"]}
     m_sample = 4000
     for _ in range(args.warmup):
         oracle_step(P, iters, m_sample)
@@ -233,7 +239,9 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WL,
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "ms", "cores": os.cpu_count(),
                              "sample": f"first {m_sample} rows; 4 LSQR + 4 FGMRES iterations timed and "
-                                       f"scaled to m={WL['m']}, 2n LSQR and 30x50 FGMRES iterations"},
+                                       f"scaled to m={WL['m']} and to the oracle's own iteration counts on "
+                                       f"this workload ({iters['lsqr']} LSQR, {iters['fgmres']} FGMRES; "
+                                       f"oracle/workload_counts.json)"},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

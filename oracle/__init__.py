@@ -25,6 +25,9 @@ and its application in GMRES-based iterative refinement" (arXiv 2410.06319):
                   solution x*, r* (the role of the 64-digit solve of Sec. 5).
 * ``theory``   -- closed forms used as pins (Sec. 2 identities, Eq. 4.1,
                   Marchenko-Pastur limits of kappa(A R^-1)).
+* ``workload_counts`` -- the oracle's iteration counts on the m = 1e5,
+                  n = 500 workload, which the reference leg of bench.py
+                  scales its sampled per-iteration times to.
 
 Arithmetic is FP64 unless a function takes an explicit working dtype (the
 paper's precisions u, u_A, u_L, u_R are parameters of the method).

@@ -34,12 +34,13 @@ def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64, work_dtype=np.float64):
     Ro = np.asarray(R, dtype=op_dtype)
 
     def apply(vtop, vbot):
-        """z = M_R^-1 v (u_R), then w = M_L^-1 Atilde z (u_A, u_L)."""
+        """z = M_R^-1 v (u_R), then w = M_L^-1 Atilde z (u_A, u_L).  The top block of
+        M_R^-1 and of M_L^-1 is I and Atilde's top-left block is I: z_top = v_top enters
+        w_top exactly, and only the products A z_bot and A^T z_top are rounded to u_A."""
         zb = solve_upper(Ro, vbot.astype(op_dtype)).astype(op_dtype)
-        zt = vtop.astype(op_dtype)
-        wt = zt + Ao @ zb
-        wb = solve_upper_t(Ro, (Ao.T @ zt).astype(op_dtype)).astype(op_dtype)
-        return zb.astype(wd), np.concatenate([wt, wb]).astype(wd)
+        wt = vtop + (Ao @ zb).astype(wd)
+        wb = solve_upper_t(Ro, (Ao.T @ vtop.astype(op_dtype)).astype(op_dtype)).astype(op_dtype)
+        return zb.astype(wd), np.concatenate([wt, wb.astype(wd)])
 
     rhs = np.concatenate([np.asarray(f, np.float64), np.asarray(h, np.float64)]).astype(wd)
     beta = np.linalg.norm(rhs)
