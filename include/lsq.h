@@ -67,7 +67,8 @@ typedef enum lsq_status {
   LSQ_NOT_CONVERGED = 1,   /* iteration cap reached; last iterate written */
   LSQ_E_INVAL = -1,        /* bad argument; nothing written */
   LSQ_E_RANK = -2,         /* R has a zero (or non-finite) diagonal entry */
-  LSQ_E_BREAKDOWN = -3,
+  LSQ_E_BREAKDOWN = -3,    /* reserved, not returned: a Krylov breakdown ends the method
+                              with its current iterate */
   LSQ_E_NONFINITE = -4,    /* non-finite value met in a stage output */
   LSQ_E_CUDA = -5,         /* a CUDA call failed (see lsq_last_cuda_error) */
   LSQ_E_TIMEOUT = -6,      /* a bounded device-side wait ran out */
@@ -78,7 +79,7 @@ typedef enum lsq_status {
 
 /* info.flags bits */
 #define LSQ_WARN_COND 1     /* kappa_est(R) * u_s >= 1: outside Thm 3.1 (Sec. 3.4) */
-#define LSQ_INFO_ESCALATED 2 /* refinement re-run with u_A = u_L = u_R = u_r (Sec. 5) */
+#define LSQ_INFO_ESCALATED 2 /* refinement re-run with FP64 FGMRES products (Sec. 5) */
 
 typedef struct lsq_handle lsq_handle;
 
@@ -88,7 +89,8 @@ typedef struct lsq_opts {
   int32_t lsqr_maxit;     /* LSQR cap; 0 -> 2n (Sec. 5) */
   int32_t ir_maxit;       /* refinement cap; 0 -> 30 (Sec. 5) */
   int32_t gmres_maxit;    /* FGMRES cap per refinement step; 0 -> 50 (Sec. 5) */
-  int32_t no_escalate;    /* 1 disables the Sec. 5 re-run with u_A=u_L=u_R=u^2 */
+  int32_t no_escalate;    /* 1 disables the Sec. 5 re-run with FGMRES products in FP64
+                             (u_A = u_L = u_R = double for u = single) */
   int32_t no_colscale;    /* 1 disables the power-of-two column scaling (Sec. 3.2) */
   int32_t ir_stop;        /* refinement stop rule, with dx_i, dr_i the corrections of step i:
                              0: ||dx_i|| <= u||x|| and ||dr_i|| <= u||r||, or (i >= 1) the
@@ -162,9 +164,13 @@ const char* lsq_last_cuda_error(const lsq_handle* h);
  * lsq_sketch -- Algorithm 1 step 1 (Sec. 3): Y = Omega [A | b] in precision
  * u_s, with the one-sided power-of-two column scaling of Sec. 3.2 (on unless
  * opts->no_colscale) applied before the cast and removed from Y afterwards.
- * F16/BF16 use tcgen05 kind::f16 tensor cores, E4M3 kind::f8f6f4, all with
- * FP32 accumulation per split of the m range and an FP64 sum of the splits;
- * F32 and F64 use CUDA cores in that precision.
+ * F16/BF16 use tcgen05 kind::f16 tensor cores, BF16X3 the same on the three
+ * BF16 terms of A, E4M3 kind::f8f6f4, all with FP32 accumulation per split of
+ * the m range and an FP64 sum of the splits; F32 and F64 use CUDA cores in
+ * that precision.  The FP32 accumulation adds a relative error of about
+ * 2^-24 sqrt(k/2) per entry of Y for splits of k rows (k is near m / 5 at the
+ * largest m): negligible against the cast for F16/BF16/E4M3, but for BF16X3
+ * at m in the millions it, not the cast, sets kappa(A R^-1).
  * Out: Y, device FP64, s x (n+1) column-major with leading dimension s; its
  * last column is Omega b (used for x_s = R^-1 Q^T Omega b, Sec. 4).
  */
@@ -201,8 +207,10 @@ lsq_status lsq_lsqr(lsq_handle* h, const double* A, const double* b, int64_t m, 
  * lsq_lsir -- Algorithm 2: LSQR start, then augmented-system refinement:
  * [f; g] = [b; 0] - [[I, A], [A^T, 0]] [r; x] in u_r (F64), h = R^-T g in u_r,
  * split-preconditioned FGMRES (Eq. 1.2; products with Atilde, M_L^-1, M_R^-1
- * in u_w, Arnoldi and Givens in FP64), update in FP64.  Stops when
- * ||dx|| <= u_w ||x|| and ||dr|| <= u_w ||r||, or after opts->ir_maxit steps;
+ * in u_w, Arnoldi and Givens in FP64), update in FP64.  Stops by the rule
+ * of opts->ir_stop (by default ||dx|| <= u_w ||x|| and ||dr|| <= u_w ||r||,
+ * or the contraction estimate puts the remaining error within 4 u_w), or
+ * after opts->ir_maxit steps;
  * then, if not converged and kappa < 1/u_s (kappa_hint, else kappa_est(R)),
  * re-runs the refinement from the LSQR result with the FGMRES products in
  * FP64 (Sec. 5).
