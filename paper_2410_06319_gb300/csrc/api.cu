@@ -39,6 +39,7 @@ struct StatusFail {
   } while (0)
 
 constexpr int kBatch = 8;        // iterations enqueued between host checks
+constexpr size_t kRecMaxBytes = (size_t)4 << 30;   // deferred sketch-correction lists, at most
 constexpr int kMaxGmres = 127;   // cap of the FGMRES basis size
 
 struct Buf {
@@ -367,11 +368,13 @@ void stage_sketch(Ctx& c, double* Y) {
     if (!encode_bt_tmap(&tm, Bt, fmt, (int64_t)p.nt * rows, c.m, ldb, p.bn / p.nsub, p.rowb))
       throw StatusFail{LSQ_E_UNSUPPORTED};
     float* partial = static_cast<float*>(ws(c.h, "partial", (size_t)p.splits * ncols * p.s_pad * 4));
-    bool exact = c.o.sketch_exact != 0;
+    const uint32_t cap = sketch_rec_cap(p);
+    const int64_t lists = sketch_rec_lists(p);
+    // the correction lists grow with s * m * (column groups); past kRecMaxBytes the
+    // in-pipeline exact mode (no lists) is used instead
+    bool exact = c.o.sketch_exact != 0 || (size_t)lists * cap * 8 > kRecMaxBytes;
     if (!exact) {
       // deferred correction of the near-midpoint entries (timed together with the GEMM)
-      const uint32_t cap = sketch_rec_cap(p);
-      const int64_t lists = sketch_rec_lists(p);
       auto* rec = static_cast<uint64_t*>(ws(c.h, "sk_rec", (size_t)lists * cap * 8));
       auto* cnt = static_cast<uint32_t*>(ws(c.h, "sk_cnt", (size_t)lists * 4));
       int* ovf = static_cast<int*>(ws(c.h, "sk_ovf", 64));
