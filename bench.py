@@ -54,6 +54,9 @@ def select_us(kappa):
 
 WL["u_s"] = select_us(WL["kappa"])
 FALLBACK_HBM = 6800.0
+#: how the oracle uses the host's cores (numpy: BLAS products on its thread pool)
+THREADS_NOTE = ("matrix products on numpy's BLAS thread pool (all cores unless OMP_NUM_THREADS says "
+                "otherwise); the Philox/Box-Muller generation and the other elementwise work on one thread")
 
 
 def peaks():
@@ -238,6 +241,7 @@ def run_reference(args):
             "ms_per_step": wall / args.steps * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WL,
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "ms", "cores": os.cpu_count(),
+                             "threads": THREADS_NOTE,
                              "sample": f"first {m_sample} rows; 4 LSQR + 4 FGMRES iterations timed and "
                                        f"scaled to m={WL['m']} and to the oracle's own iteration counts on "
                                        f"this workload ({iters['lsqr']} LSQR, {iters['fgmres']} FGMRES; "
@@ -468,6 +472,7 @@ def run_ours(args):
         v, detail = oracle_step(P, iters, 4000)
         detail["gpu_iterations"] = {"lsqr": last["lsqr_its"], "fgmres": last["gmres_its_total"]}
         line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                                "threads": THREADS_NOTE,
                                 "sample": f"first 4000 rows: {WL['u_s']} sketch, FP32 QR, 4 LSQR + 4 "
                                           f"FGMRES iterations, scaled to m=1e5 and to the oracle's own "
                                           f"iteration counts ({iters['lsqr']} LSQR, {iters['fgmres']} FGMRES; "
