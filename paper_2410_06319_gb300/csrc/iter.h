@@ -26,6 +26,8 @@ struct GmState {
   int nreorth;    // second passes run so far
 };
 
+// LSQR pass over A (FP32 copy or FP64): q_i = (A t)_i + cu * u_i (cu read from *cu_ptr
+// times cu_mul); u_out = q; Pblk[blk][c] = sum_rows q_i A_ic; sq[blk] = sum q_i^2.
 template <typename TP>
 cudaError_t launch_pass_lsqr_any(const TP* A, int64_t lda, int64_t m, int64_t n, const TP* t,
                                  const TP* u_in, const double* cu_ptr, double cu_mul, TP* u_out,
@@ -36,11 +38,6 @@ cudaError_t launch_lsqr_colsum(const T* P, int nblk, int64_t n, const double* sq
 template <typename T>
 cudaError_t launch_lsqr_step(const Tri<T>& f, const T* s, T* v, T* w, T* z, T* t, LsqrState* st,
                              bool init, cudaStream_t strm);
-cudaError_t launch_lsqr_beta(const double* sq, int nblk, LsqrState* st, bool init, cudaStream_t s);
-template <typename T>
-cudaError_t launch_lsqr_init(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s);
-template <typename T>
-cudaError_t launch_lsqr_update(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s);
 
 template <typename TX, typename TY, typename TO>
 cudaError_t launch_axpby(const TX* x, double a, const TY* y, double b, TO* out, int64_t len,

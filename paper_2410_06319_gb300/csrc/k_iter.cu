@@ -521,12 +521,6 @@ cudaError_t launch_pass_lsqr_t(const T* A, int64_t lda, int64_t m, int64_t n, co
   }
 }
 
-cudaError_t launch_pass_lsqr(const float* A32, int64_t lda32, int64_t m, int64_t n, const float* t,
-                             const float* u_in, const double* cu_ptr, double cu_mul, float* u_out,
-                             float* Pblk, double* sq, int nblk, const int* done, cudaStream_t st) {
-  return launch_pass_lsqr_t<float>(A32, lda32, m, n, t, u_in, cu_ptr, cu_mul, u_out, Pblk, sq, nblk,
-                                   done, st);
-}
 
 template <typename TA>
 cudaError_t launch_pass_fgm(const TA* A, int64_t lda, int64_t m, int64_t n, const TA* z,
@@ -635,125 +629,6 @@ template cudaError_t launch_colsum<float, double>(const float*, int, int64_t, co
                                                   double*, const int*, cudaStream_t);
 
 // ============================================================ LSQR kernels
-// beta = sqrt(sum sq); us = 1/beta.
-__global__ void lsqr_beta_kernel(const double* sq, int nblk, LsqrState* st, bool init) {
-  if (!init && st->done) return;
-  __shared__ double red[33];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += sq[b];
-  s = block_sum_d(s, red);
-  if (threadIdx.x == 0) {
-    const double beta = sqrt(s);
-    st->beta = beta;
-    st->us = beta > 0.0 ? 1.0 / beta : 0.0;
-    if (init) st->phibar = beta;
-  }
-}
-
-template <typename T>
-__global__ void lsqr_init_kernel(const T* vt, int n, T* v, T* w, T* z, LsqrState* st) {
-  __shared__ double red[33];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)vt[i] * (double)vt[i];
-  s = block_sum_d(s, red);
-  const double alpha = sqrt(s);
-  const T ia = alpha > 0.0 ? (T)(1.0 / alpha) : T(0);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const T vi = vt[i] * ia;
-    v[i] = vi;
-    w[i] = vi;
-    z[i] = T(0);
-  }
-  if (threadIdx.x == 0) {
-    st->alpha = alpha;
-    st->rhobar = alpha;
-    st->anorm2 = 0.0;
-    st->its = 0;
-    st->flag = 0;
-    st->normr = st->beta;
-    st->normar = alpha * st->beta;
-    st->normA = 0.0;
-    st->cu = -alpha * st->us;
-    st->done = (st->beta == 0.0 || alpha == 0.0 || st->maxit <= 0) ? 1 : 0;
-    if (st->beta == 0.0 || alpha == 0.0) st->flag = 3;
-  }
-}
-
-// vv = vt - beta v ; alpha = ||vv|| ; v = vv / alpha ; plane rotation ; z, w
-// updates ; stopping tests (Paige-Saunders, with the S1/S2 tests of this build).
-template <typename T>
-__global__ void lsqr_update_kernel(const T* vt, int n, T* v, T* w, T* z, LsqrState* st) {
-  if (st->done) return;
-  __shared__ double red[33];
-  __shared__ double coef[2];
-  const double beta = st->beta;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const T vv = vt[i] - (T)beta * v[i];
-    s += (double)vv * (double)vv;
-  }
-  s = block_sum_d(s, red);
-  const double alpha_old = st->alpha;
-  const double alpha = sqrt(s);
-  if (threadIdx.x == 0) {
-    const double anorm2 = st->anorm2 + alpha_old * alpha_old + beta * beta;
-    const double rhobar = st->rhobar;
-    const double rho = sqrt(rhobar * rhobar + beta * beta);
-    const double c = rhobar / rho, sn = beta / rho;
-    const double theta = sn * alpha;
-    const double phi = c * st->phibar;
-    const double phibar = sn * st->phibar;
-    coef[0] = phi / rho;
-    coef[1] = theta / rho;
-    st->rhobar = -c * alpha;
-    st->phibar = phibar;
-    st->anorm2 = anorm2;
-    st->alpha = alpha;
-    st->its += 1;
-    st->normr = fabs(phibar);
-    st->normar = fabs(phibar * alpha * c);
-    st->normA = sqrt(anorm2);
-    st->cu = -alpha * st->us;
-    int flag = 0;
-    if (st->normr <= st->tol * st->normb) flag = 1;
-    else if (st->normar <= st->tol * st->normA * st->normr) flag = 2;
-    else if (beta == 0.0 || alpha == 0.0) flag = 3;
-    st->flag = flag;
-    st->done = (flag != 0 || st->its >= st->maxit) ? 1 : 0;
-  }
-  __syncthreads();
-  const T ia = alpha > 0.0 ? (T)(1.0 / alpha) : T(0);
-  const T c0 = (T)coef[0], c1 = (T)coef[1];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const T vn = (vt[i] - (T)beta * v[i]) * ia;
-    const T wi = w[i];
-    z[i] = z[i] + c0 * wi;
-    w[i] = vn - c1 * wi;
-    v[i] = vn;
-  }
-}
-
-
-template <typename T>
-cudaError_t launch_lsqr_init(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s) {
-  lsqr_init_kernel<T><<<1, 1024, 0, s>>>(vt, (int)n, v, w, z, st);
-  return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_lsqr_update(const T* vt, int64_t n, T* v, T* w, T* z, LsqrState* st, cudaStream_t s) {
-  lsqr_update_kernel<T><<<1, 1024, 0, s>>>(vt, (int)n, v, w, z, st);
-  return cudaGetLastError();
-}
-template cudaError_t launch_lsqr_init<float>(const float*, int64_t, float*, float*, float*, LsqrState*, cudaStream_t);
-template cudaError_t launch_lsqr_init<double>(const double*, int64_t, double*, double*, double*, LsqrState*, cudaStream_t);
-template cudaError_t launch_lsqr_update<float>(const float*, int64_t, float*, float*, float*, LsqrState*, cudaStream_t);
-template cudaError_t launch_lsqr_update<double>(const double*, int64_t, double*, double*, double*, LsqrState*, cudaStream_t);
-
-cudaError_t launch_lsqr_beta(const double* sq, int nblk, LsqrState* st, bool init, cudaStream_t s) {
-  lsqr_beta_kernel<<<1, 1024, 0, s>>>(sq, nblk, st, init);
-  return cudaGetLastError();
-}
-
 template <typename TP>
 cudaError_t launch_pass_lsqr_any(const TP* A, int64_t lda, int64_t m, int64_t n, const TP* t,
                                  const TP* u_in, const double* cu_ptr, double cu_mul, TP* u_out,

@@ -110,11 +110,6 @@ cudaError_t launch_prepare_r(const double* R, int64_t n, Tri<float>* f32, Tri<do
 
 // ---------------------------------------------------------------- passes
 int pass_blocks(int num_sms);
-// LSQR pass over A32: q_i = cd * (A t)_i + cu * u_i (cu read from *cu_ptr times cu_mul);
-// u_out = q; Pblk[blk][c] = sum_rows q_i A_ic; sq[blk] = sum q_i^2.
-cudaError_t launch_pass_lsqr(const float* A32, int64_t lda32, int64_t m, int64_t n, const float* t,
-                             const float* u_in, const double* cu_ptr, double cu_mul, float* u_out,
-                             float* Pblk, double* sq, int nblk, const int* done, cudaStream_t st);
 // FGMRES pass: az = A z ; Pblk = block sums of v_i A_i (rows of A streamed with
 // cp.async.bulk).  With jp, z and v are offset on the device by (*jp) * zs and
 // (*jp) * vstr.  Requires A 16-byte aligned with 16-byte rows.
