@@ -101,7 +101,8 @@ for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "l
 
 def declared_functions():
     """Names of the functions declared in include/lsq.h."""
-    text = open(HEADER).read()
+    with open(HEADER) as fh:
+        text = fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lsq_[a-z_0-9]+)\s*\(", text)))
 

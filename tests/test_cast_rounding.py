@@ -116,7 +116,8 @@ def test_integer_cast_matches_oracle_rounding(harness, fmt):
         with np.errstate(over="ignore"):
             terms = [v.astype(np.float32).astype(np.float64)]
     elif fmt == "bf16x3":
-        terms = list(rng.split3(np.where(finite_in, v, 0.0), "bf16"))
+        with np.errstate(invalid="ignore"):      # terms of overflowing edge values (declined below)
+            terms = list(rng.split3(np.where(finite_in, v, 0.0), "bf16"))
     else:
         terms = [rng.round_to_format(np.where(finite_in, v, 0.0), fmt)]
     expect_ok = finite_in.copy()
