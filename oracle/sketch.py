@@ -15,6 +15,11 @@ Test infrastructure only (see ``oracle/__init__.py``).
 * The sketch operand is fl_s(G) from ``oracle.rng``; Omega = s^-1/2 fl_s(G).
 * The product of the rounded operands is accumulated in FP64 here (a library
   matmul is one step); the scale s^-1/2 and D^-1 are applied afterwards.
+  ``accumulate="us"`` is instead the model of Sec. 3.2's error bound, the
+  product formed in u_s: every product and every partial sum is rounded to
+  the sketch format, summing over the rows of A in order.  Its columns are
+  scaled to a largest entry in [1, 2) so that partial sums stay in range.
+  It loops over the m rows (paper-sized problems only).
 """
 import numpy as np
 
@@ -58,14 +63,17 @@ def cast_scaled(A, b, fmt):
     return As[:, :-1], As[:, -1], k[:-1], int(k[-1])
 
 
-def sketch(A, b, s, seed, fmt):
+def sketch(A, b, s, seed, fmt, accumulate="f64"):
     """Y = Omega [A | b] with Omega = s^-1/2 fl_s(G), A and b cast to ``fmt``.
 
     Returns Y (s x (n+1), FP64) already unscaled: column j is divided by the
     power of two 2^k_j used for the cast, so Y approximates Omega [A | b].
+    ``accumulate``: "f64" (default) or "us" (see the module docstring).
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
+    if accumulate == "us":
+        return _sketch_accumulated_in_us(A, b, s, seed, fmt)
     As, bs, kA, kb = cast_scaled(A, b, fmt)
     Ab = np.concatenate([As, bs.reshape(-1, 1)], axis=1)
     Y = np.zeros((s, n + 1))
@@ -77,3 +85,19 @@ def sketch(A, b, s, seed, fmt):
     Y *= 1.0 / np.sqrt(float(s))
     k = np.concatenate([kA, [kb]])
     return np.ldexp(Y, -k[None, :])
+
+
+def _sketch_accumulated_in_us(A, b, s, seed, fmt):
+    """Sec. 3.2's model: fl_s of every product and of every partial sum, rows in order."""
+    m, n = A.shape
+    Ab = np.concatenate([A, np.asarray(b, dtype=np.float64).reshape(-1, 1)], axis=1)
+    cmax = np.abs(Ab).max(axis=0)
+    _, ex = np.frexp(cmax)
+    k = np.where(cmax == 0, 0, -(ex.astype(np.int64) - 1))      # largest entry in [1, 2)
+    opf = rng.OPERAND_FORMAT[fmt]
+    As = rng.round_to_format(np.ldexp(Ab, k[None, :]), opf)
+    Gs = rng.sketch_operand(s, 0, m, seed, fmt)
+    acc = np.zeros((s, n + 1))
+    for j in range(m):
+        acc = rng.round_to_format(acc + rng.round_to_format(np.outer(Gs[:, j], As[j]), opf), opf)
+    return np.ldexp(acc / np.sqrt(float(s)), -k[None, :])

@@ -4,10 +4,10 @@
   E4M3 (column-scaled) against FP16 sketches, FP64 QR; where kappa u_s
   leaves the regime of Sec. 3 the preconditioner fails (kappa(A R^-1) grows
   in proportion to kappa u_s, Fig. 3a) and LSQR slows down.  Fig. 3a puts
-  the constant near 3; with per-column power-of-two scaling each entry's cast
-  error is relative to that entry, and the constant is 0.1 to 0.3 (oracle
-  sketches of the same recipe at m = 3e4), so the bounds below span
-  [0.03, 3] kappa u_s.
+  the constant near 3 for a product formed in u_s; the tensor cores
+  accumulate in FP32, which leaves only the cast error, and the constant is
+  0.1 to 0.3 (oracle sketches of the same recipe at m = 3e4), so the bounds
+  below span [0.03, 3] kappa u_s.
 * m = 4e6, n = 1000, s = 4n, kappa = 1e7, ||r_perp|| / ||b|| = 1e-6: BF16
   sketch (broken there, kappa u_s = 3.9e4) and the three-term BF16 split
   (single precision), FP64 QR.  Here the FP32 accumulation of the tensor

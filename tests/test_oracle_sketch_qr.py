@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from lsq_synth import randsvd_problem, paper_problem
-from oracle import qr, rng, sketch, theory
+from oracle import lsqr, qr, rng, sketch, theory
 
 
 def _explicit_omega(s, m, seed, fmt="f64"):
@@ -169,3 +169,44 @@ def test_split_sketch_restores_the_good_regime():
     Rb, _ = qr.householder_qr(Yb, 100)
     svb = np.linalg.svd(P.A @ np.linalg.inv(Rb), compute_uv=False)
     assert svb[0] / svb[-1] > 10 * sv[0] / sv[-1]
+
+
+def _kappa_AR(A, R):
+    sv = np.linalg.svd(np.linalg.solve(np.asarray(R, np.float64).T, A.T).T, compute_uv=False)
+    return sv[0] / sv[-1]
+
+
+def test_half_sketch_accumulated_in_us_reproduces_fig3a(golden):
+    """Fig. 3(a): with the product formed in half precision (Sec. 3.2's model) the oracle's
+    kappa(A R^-1) follows the printed values (one draw each: within 25 %); with the product
+    accumulated in FP64 only the cast error is left, and kappa(A R^-1) is ten times smaller
+    or more once kappa u_s >> 1 -- the regime the FP32-accumulating tensor cores are in."""
+    for src, kappa, val in golden("paper_half_sketch.txt"):
+        if src != "fig3a":
+            continue
+        kappa, val = float(kappa), float(val)
+        P = paper_problem(kappa, seed=0)
+        Yh = sketch.sketch(P.A, P.b, 400, 0, "f16", accumulate="us")
+        Rh, _ = qr.householder_qr(Yh, 100, dtype=np.float32)
+        kh = _kappa_AR(P.A, Rh)
+        assert 0.75 * val <= kh <= 1.25 * val, (kappa, kh, val)
+        if kappa >= 1e5:
+            Y64 = sketch.sketch(P.A, P.b, 400, 0, "f16")
+            R64, _ = qr.householder_qr(Y64, 100, dtype=np.float32)
+            assert _kappa_AR(P.A, R64) <= 0.1 * val
+
+
+def test_half_sketch_accumulated_in_us_lsqr_counts_table1(golden):
+    """Table 1, half column: LSQR slows down and hits its cap as kappa u_s grows."""
+    for src, kappa, its in golden("paper_half_sketch.txt"):
+        if src != "T1":
+            continue
+        kappa, its = float(kappa), int(its)
+        got = []
+        for seed in range(2):
+            P = paper_problem(kappa, seed=seed)
+            Y = sketch.sketch(P.A, P.b, 400, seed, "f16", accumulate="us")
+            R, c = qr.householder_qr(Y, 100, dtype=np.float32)
+            _, info = lsqr.lsqr(P.A, P.b, R, qr.sketch_and_solve(R, c), 1e-6, 200, dtype=np.float32)
+            got.append(info["its"])
+        assert abs(np.mean(got) - its) <= max(2, 0.2 * its), (kappa, got, its)
