@@ -181,7 +181,7 @@ def test_half_sketch_accumulated_in_us_reproduces_fig3a(golden):
     kappa(A R^-1) follows the printed values (one draw each: within 25 %); with the product
     accumulated in FP64 only the cast error is left, and kappa(A R^-1) is ten times smaller
     or more once kappa u_s >> 1 -- the regime the FP32-accumulating tensor cores are in."""
-    for src, kappa, val in golden("paper_half_sketch.txt"):
+    for src, kappa, val, *_ in golden("paper_half_sketch.txt"):
         if src != "fig3a":
             continue
         kappa, val = float(kappa), float(val)
@@ -198,7 +198,7 @@ def test_half_sketch_accumulated_in_us_reproduces_fig3a(golden):
 
 def test_half_sketch_accumulated_in_us_lsqr_counts_table1(golden):
     """Table 1, half column: LSQR slows down and hits its cap as kappa u_s grows."""
-    for src, kappa, its in golden("paper_half_sketch.txt"):
+    for src, kappa, its, *_ in golden("paper_half_sketch.txt"):
         if src != "T1":
             continue
         kappa, its = float(kappa), int(its)
@@ -210,3 +210,25 @@ def test_half_sketch_accumulated_in_us_lsqr_counts_table1(golden):
             _, info = lsqr.lsqr(P.A, P.b, R, qr.sketch_and_solve(R, c), 1e-6, 200, dtype=np.float32)
             got.append(info["its"])
         assert abs(np.mean(got) - its) <= max(2, 0.2 * its), (kappa, got, its)
+
+
+def test_half_sketch_accumulated_in_us_lsir_table3(golden):
+    """Table 3, half column: one refinement step of 45 FGMRES iterations at kappa = 1e3; no
+    convergence in 30 steps at 1e5, and no escalation since kappa >= 1/u_s (Sec. 5)."""
+    from oracle import exact, lsir
+    for src, kappa, *vals in golden("paper_half_sketch.txt"):
+        if src != "T3":
+            continue
+        steps, gm = vals
+        kappa = float(kappa)
+        P = paper_problem(kappa, seed=0)
+        xstar, rstar = exact.reference_solution(P.A, P.b)
+        Y = sketch.sketch(P.A, P.b, 400, 0, "f16", accumulate="us")
+        R, c = qr.householder_qr(Y, 100, dtype=np.float32)
+        x, r, info = lsir.lsir(P.A, P.b, R, qr.sketch_and_solve(R, c), 2.0 ** -24, 1e-6, w_dtype=np.float32,
+                               us=2.0 ** -11, kappa=kappa, xstar=xstar, rstar=rstar)
+        if steps == "-":
+            assert not info["converged"] and not info["escalated"] and info["its"] == 30
+        else:
+            assert info["converged"] and info["its"] == int(steps)
+            assert abs(info["gmres_total"] - int(gm)) <= 3, info
