@@ -213,20 +213,23 @@ def test_fig3a_printed_columns_satisfy_eq41(golden):
         assert abs(theory.kappa_prec_aug(1.0, nar, 1 / narp) - kaug) <= 0.015 * kaug, (kappa, kaug)
 
 
-def test_half_sketch_accumulated_in_us_lsqr_counts_table1(golden):
-    """Table 1, half column: LSQR slows down and hits its cap as kappa u_s grows."""
-    for src, kappa, its, *_ in golden("paper_half_sketch.txt"):
-        if src != "T1":
+def test_sketch_accumulated_in_us_lsqr_counts_tables_1_2(golden):
+    """Tables 1-2: LSQR slows down and hits its cap as kappa u_s grows (u single, tol 1e-6;
+    u double, tol 1e-12), with the sketch product formed in u_s."""
+    for src, kappa, its, *rest in golden("paper_half_sketch.txt"):
+        if src not in ("T1", "T2"):
             continue
         kappa, its = float(kappa), int(its)
+        fmt = {"half": "f16", "single": "f32"}[rest[0]]
+        dt, tol = (np.float32, 1e-6) if src == "T1" else (np.float64, 1e-12)
         got = []
         for seed in range(2):
             P = paper_problem(kappa, seed=seed)
-            Y = sketch.sketch(P.A, P.b, 400, seed, "f16", accumulate="us")
-            R, c = qr.householder_qr(Y, 100, dtype=np.float32)
-            _, info = lsqr.lsqr(P.A, P.b, R, qr.sketch_and_solve(R, c), 1e-6, 200, dtype=np.float32)
+            Y = sketch.sketch(P.A, P.b, 400, seed, fmt, accumulate="us")
+            R, c = qr.householder_qr(Y, 100, dtype=dt)
+            _, info = lsqr.lsqr(P.A, P.b, R, qr.sketch_and_solve(R, c), tol, 200, dtype=dt)
             got.append(info["its"])
-        assert abs(np.mean(got) - its) <= max(2, 0.2 * its), (kappa, got, its)
+        assert abs(np.mean(got) - its) <= max(2, 0.2 * its), (src, kappa, got, its)
 
 
 def test_half_sketch_accumulated_in_us_lsir_table3(golden):
