@@ -232,23 +232,26 @@ def test_sketch_accumulated_in_us_lsqr_counts_tables_1_2(golden):
         assert abs(np.mean(got) - its) <= max(2, 0.2 * its), (src, kappa, got, its)
 
 
-def test_half_sketch_accumulated_in_us_lsir_table3(golden):
-    """Table 3, half column: one refinement step of 45 FGMRES iterations at kappa = 1e3; no
-    convergence in 30 steps at 1e5, and no escalation since kappa >= 1/u_s (Sec. 5)."""
+def test_sketch_accumulated_in_us_lsir_tables_3_4(golden):
+    """Tables 3-4: with the sketch product formed in u_s, one refinement step of 45 FGMRES
+    iterations for the half sketch at kappa = 1e3 (u single); no convergence in 30 steps,
+    and no escalation since kappa >= 1/u_s (Sec. 5), where the tables print "-"."""
     from oracle import exact, lsir
     for src, kappa, *vals in golden("paper_half_sketch.txt"):
-        if src != "T3":
+        if src not in ("T3", "T4"):
             continue
-        steps, gm = vals
+        steps, gm, prec = vals
         kappa = float(kappa)
+        fmt = {"half": "f16", "single": "f32"}[prec]
+        dt, u, tol = (np.float32, 2.0 ** -24, 1e-6) if src == "T3" else (np.float64, 2.0 ** -53, 1e-12)
         P = paper_problem(kappa, seed=0)
         xstar, rstar = exact.reference_solution(P.A, P.b)
-        Y = sketch.sketch(P.A, P.b, 400, 0, "f16", accumulate="us")
-        R, c = qr.householder_qr(Y, 100, dtype=np.float32)
-        x, r, info = lsir.lsir(P.A, P.b, R, qr.sketch_and_solve(R, c), 2.0 ** -24, 1e-6, w_dtype=np.float32,
-                               us=2.0 ** -11, kappa=kappa, xstar=xstar, rstar=rstar)
+        Y = sketch.sketch(P.A, P.b, 400, 0, fmt, accumulate="us")
+        R, c = qr.householder_qr(Y, 100, dtype=dt)
+        x, r, info = lsir.lsir(P.A, P.b, R, qr.sketch_and_solve(R, c), u, tol, w_dtype=dt,
+                               us=rng.UNIT_ROUNDOFF[fmt], kappa=kappa, xstar=xstar, rstar=rstar)
         if steps == "-":
-            assert not info["converged"] and not info["escalated"] and info["its"] == 30
+            assert not info["converged"] and not info["escalated"] and info["its"] == 30, (src, kappa)
         else:
             assert info["converged"] and info["its"] == int(steps)
             assert abs(info["gmres_total"] - int(gm)) <= 3, info
