@@ -216,3 +216,26 @@ def test_lsir_computable_stop_rule_reaches_target():
     assert info["converged"]
     ex, er = exact.forward_errors(x, r, xstar, rstar)
     assert ex <= 4 * 2.0 ** -24 and er <= 4 * 2.0 ** -24
+
+
+def test_escalation_rule_of_sec5():
+    """Sec. 5: a refinement that does not converge is re-run from (x0, r0) with the FGMRES
+    products in FP64 when kappa < 1/u_s, and not otherwise.  A cap of one step of two
+    FGMRES iterations forces the first run to fail; the re-run, with the same caps, then
+    starts from the same point with more accurate products."""
+    P = paper_problem(1e2, seed=0)
+    Y = sketch.sketch(P.A, P.b, 400, 0, "f16")
+    R, c = qr.householder_qr(Y, 100, dtype=np.float32)
+    xs = qr.sketch_and_solve(R, c)
+    kw = dict(w_dtype=np.float32, ir_maxit=1, gm_maxit=2, us=2.0 ** -11)
+    _, _, low = lsir.lsir(P.A, P.b, R, xs, 2.0 ** -24, 1e-6, kappa=1e2, escalate=False, **kw)
+    assert not low["converged"] and not low["escalated"]
+    # kappa u_s < 1: re-run with FP64 products; its steps equal an FP64-product run from the start
+    xe, re, esc = lsir.lsir(P.A, P.b, R, xs, 2.0 ** -24, 1e-6, kappa=1e2, **kw)
+    assert esc["escalated"] and esc["its"] == 1
+    x64, r64, ref = lsir.lsir(P.A, P.b, R, xs, 2.0 ** -24, 1e-6, kappa=1e2, escalate=False,
+                              op_dtype=np.float64, **kw)
+    assert np.array_equal(xe, x64) and np.array_equal(re, r64)
+    # kappa u_s >= 1 (1/u_s = 2048): no re-run
+    _, _, no = lsir.lsir(P.A, P.b, R, xs, 2.0 ** -24, 1e-6, kappa=4096.0, **kw)
+    assert not no["escalated"] and not no["converged"]
