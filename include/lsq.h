@@ -232,6 +232,20 @@ typedef struct lsq_problem {
 } lsq_problem;
 
 /*
+ * lsq_lsir_host -- lsq_lsir on HOST arrays (the paper has no counterpart: it is
+ * the same Algorithm 2 for callers whose data live in host memory).  A (m rows,
+ * row stride opts->lda, (m-1)*lda + n elements read) and b (m) are copied into
+ * the handle's workspace on its stream (page-locked host memory copies fastest),
+ * lsq_lsir runs there, and x (n) and r (m; may be NULL) are copied back to host
+ * memory before the call returns.  The workspace keeps a device copy of A until
+ * lsq_destroy.  Statuses as lsq_lsir; on an error x and r are not written.
+ */
+lsq_status lsq_lsir_host(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                         int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
+                         double tol, uint64_t seed, const lsq_opts* opts, double* x, double* r,
+                         lsq_info* info);
+
+/*
  * lsq_lsir_batched -- lsq_lsir on nprob independent problems of uneven sizes
  * (probs is a HOST array of descriptors).  The problems run concurrently on
  * up to four internal streams (one worker thread and one workspace per

@@ -6,11 +6,12 @@ R-preconditioned LSQR and FGMRES-based augmented-system refinement).
 
 The functions ``lsq_sketch``, ``lsq_qr_r``, ``lsq_lsqr``, ``lsq_lsir`` and
 ``lsq_omega`` keep the C names and arguments; they only marshal arguments
-(torch CUDA tensors or raw device pointers) and call the library, whose
+(torch CUDA tensors or raw device pointers; host arrays for
+``lsq_lsir_host``) and call the library, whose
 kernels do all the work.  Importing this module fails loudly if the CUDA
 library has not been built; there is no fallback.
 """
 from ._lib import (  # noqa: F401
-    KERNELS, PREC, STATUS, Handle, Info, LsqError, Opts, Problem, lib, lsq_lsir, lsq_lsir_batched,
+    KERNELS, PREC, STATUS, Handle, Info, LsqError, Opts, Problem, lib, lsq_lsir, lsq_lsir_batched, lsq_lsir_host,
     lsq_lsqr, lsq_omega, lsq_qr_r, lsq_qr_r_noalloc, lsq_sketch, library_path, declared_functions,
 )

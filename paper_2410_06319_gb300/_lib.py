@@ -89,12 +89,13 @@ lib.lsq_sketch.argtypes = _TUPLE + [_P]
 lib.lsq_qr_r.argtypes = _TUPLE + [_P, _P]
 lib.lsq_lsqr.argtypes = _TUPLE + [_P, ctypes.POINTER(Info)]
 lib.lsq_lsir.argtypes = _TUPLE + [_P, _P, ctypes.POINTER(Info)]
+lib.lsq_lsir_host.argtypes = _TUPLE + [_P, _P, ctypes.POINTER(Info)]
 lib.lsq_omega.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_uint64, _P]
 lib.lsq_lsir_batched.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
 lib.lsq_qr_r_noalloc.argtypes = [_P, _I64, _I64, ctypes.c_int, _P, _P, _P]
-for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir",
+for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir", "lsq_lsir_host",
            "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc"):
     getattr(lib, _f).restype = ctypes.c_int
 
@@ -208,6 +209,29 @@ def lsq_lsir(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, x, r, info=N
     info = info if info is not None else Info()
     st = _check(h, lib.lsq_lsir(*args, _ptr(x), _ptr(r), ctypes.byref(info)), "lsq_lsir")
     return st, info
+
+
+def _host_ptr(x):
+    """Host pointer of a contiguous FP64 numpy array or CPU torch tensor (or a raw int)."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "is_cuda"):
+        if x.is_cuda or not x.is_contiguous() or x.element_size() != 8:
+            raise ValueError("expected a contiguous FP64 CPU tensor")
+        return x.data_ptr()
+    if x.dtype.itemsize != 8 or not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous FP64 array")
+    return x.ctypes.data
+
+
+def lsq_lsir_host(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, x, r, info=None):
+    """lsq_lsir on host arrays (numpy or CPU tensors; page-locked tensors copy fastest)."""
+    o = _opts(opts)
+    info = info if info is not None else Info()
+    st = lib.lsq_lsir_host(h.ptr, _host_ptr(A), _host_ptr(b), m, n, s, _prec(u_s), _prec(u_p), _prec(u_w),
+                           _prec(u_r), float(tol), int(seed), ctypes.byref(o), _host_ptr(x), _host_ptr(r),
+                           ctypes.byref(info))
+    return _check(h, st, "lsq_lsir_host"), info
 
 
 def lsq_lsir_batched(h, problems, u_s, u_p, u_w, u_r, tol, opts=None):

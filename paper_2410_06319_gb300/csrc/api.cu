@@ -1123,4 +1123,42 @@ lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_pre
   });
 }
 
+lsq_status lsq_lsir_host(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+                         lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol, uint64_t seed,
+                         const lsq_opts* opts, double* x, double* r, lsq_info* info) {
+  if (!h || !A || !b || !x || n < 1 || m < n || m > ((int64_t)1 << 36)) return LSQ_E_INVAL;
+  const int64_t lda = (opts && opts->lda > 0) ? opts->lda : n;
+  if (lda < n) return LSQ_E_INVAL;
+  const size_t a_elems = (size_t)(m - 1) * (size_t)lda + (size_t)n;   // rows end at column n
+  double *dA = nullptr, *db = nullptr, *dx = nullptr, *dr = nullptr;
+  try {
+    dA = static_cast<double*>(ws(h, "host_A", a_elems * 8));
+    db = static_cast<double*>(ws(h, "host_b", (size_t)m * 8));
+    dx = static_cast<double*>(ws(h, "host_x", (size_t)n * 8));
+    if (r) dr = static_cast<double*>(ws(h, "host_r", (size_t)m * 8));
+    // inputs onto the work stream, after whatever the caller's stream has queued
+    CK(cudaEventRecord(h->ev_in, h->user_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+    CK(cudaMemcpyAsync(dA, A, a_elems * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(db, b, (size_t)m * 8, cudaMemcpyHostToDevice, h->stream));
+  } catch (const CudaFail& f) {
+    h->last_cuda = std::string(f.what) + ": " + cudaGetErrorString(f.e);
+    cudaGetLastError();
+    return LSQ_E_CUDA;
+  } catch (const StatusFail& f) {
+    return f.st;
+  }
+  const lsq_status st = lsq_lsir(h, dA, db, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, dx, dr, info);
+  if (st != LSQ_OK && st != LSQ_NOT_CONVERGED) return st;
+  cudaError_t e = cudaMemcpyAsync(x, dx, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && r) e = cudaMemcpyAsync(r, dr, (size_t)m * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    h->last_cuda = std::string("lsq_lsir_host result copy: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return LSQ_E_CUDA;
+  }
+  return st;
+}
+
 }  // extern "C"

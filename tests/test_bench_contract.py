@@ -9,9 +9,10 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _line(*args):
+def _line(*args, env=None):
     res = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "bench_mock_run.py"), *args],
-                         capture_output=True, text=True, timeout=900, cwd=ROOT)
+                         capture_output=True, text=True, timeout=900, cwd=ROOT,
+                         env=dict(os.environ, **(env or {})))
     assert res.returncode == 0, res.stderr[-2000:]
     lines = [l for l in res.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1, res.stdout[-2000:]
@@ -43,6 +44,13 @@ def test_gpu_arm_line_follows_the_contract():
     m, n = d["config"]["m"], d["config"]["n"]
     assert e["unit"] == "ms" and e["value"] > 0
     assert e["h2d_bytes_per_step"] == 8 * m * n + 8 * m and e["d2h_bytes_per_step"] > 0
+    assert e["path"].startswith("lsq_lsir_host")       # host buffers through the C ABI
     for k in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert k in d["clocks"], k
     assert d["gpu_launches"] > 0
+
+
+def test_e2e_falls_back_to_device_copies_and_says_so():
+    d = _line("--steps", "1", "--warmup", "3", env={"BENCH_MOCK_HOST_CALL_FAILS": "1"})
+    assert d["e2e"]["path"].startswith("torch copies around lsq_lsir (lsq_lsir_host: RuntimeError")
+    assert d["e2e"]["value"] > 0 and d["value"] == 10.0
