@@ -177,21 +177,21 @@ def _kappa_AR(A, R):
 
 
 def test_sketch_accumulated_in_us_reproduces_fig3(golden):
-    """Fig. 3(a), (b): with the product formed in u_s (Sec. 3.2's model) the oracle's
+    """Fig. 3(a), (b), 4(a): with the product formed in u_s (Sec. 3.2's model) the oracle's
     ||A R^-1||, ||(A R^-1)^+||, kappa(A R^-1) and the preconditioned augmented condition
     number (Eq. 4.1) follow the printed values (one draw each: norms within 15 %, condition
     numbers within 25 %); with the product accumulated in FP64 only the cast error is left,
     and kappa(A R^-1) is ten times smaller or more once kappa u_s >> 1 -- the regime the
     FP32-accumulating tensor cores are in."""
     for src, kappa, *vals in golden("paper_half_sketch.txt"):
-        if src not in ("fig3a", "fig3b"):
+        if src not in ("fig3a", "fig3b", "fig4a"):
             continue
-        fmt = "f16" if src == "fig3a" else "f32"
+        fmt = "f32" if src == "fig3b" else "f16"
         kappa = float(kappa)
         kar, kaug, nar, narp = (float(v) for v in vals)
         P = paper_problem(kappa, seed=0)
         Yh = sketch.sketch(P.A, P.b, 400, 0, fmt, accumulate="us")
-        Rh, _ = qr.householder_qr(Yh, 100, dtype=np.float32)
+        Rh, _ = qr.householder_qr(Yh, 100, dtype=np.float64 if src == "fig4a" else np.float32)
         sv = np.linalg.svd(np.linalg.solve(np.asarray(Rh, np.float64).T, P.A.T).T, compute_uv=False)
         ctx = (kappa, sv[0], 1 / sv[-1])
         assert 0.85 * nar <= sv[0] <= 1.15 * nar and 0.85 * narp <= 1 / sv[-1] <= 1.15 * narp, ctx
@@ -204,10 +204,10 @@ def test_sketch_accumulated_in_us_reproduces_fig3(golden):
 
 
 def test_fig3a_printed_columns_satisfy_eq41(golden):
-    """The printed kappa(M_L^-1 Atilde M_R^-1) of Fig. 3(a) is Eq. 4.1 of the printed
+    """The printed kappa(M_L^-1 Atilde M_R^-1) of Figs. 3-4 is Eq. 4.1 of the printed
     ||A R^-1|| and ||(A R^-1)^+|| in the broken regime too (to the printed digits)."""
     for src, kappa, *vals in golden("paper_half_sketch.txt"):
-        if src not in ("fig3a", "fig3b"):
+        if src not in ("fig3a", "fig3b", "fig4a"):
             continue
         kar, kaug, nar, narp = (float(v) for v in vals)
         assert abs(theory.kappa_prec_aug(1.0, nar, 1 / narp) - kaug) <= 0.015 * kaug, (kappa, kaug)
