@@ -36,3 +36,18 @@ def test_oracle_and_generators_do_not_import_the_product_path():
     pat_oracle = re.compile(r"^\s*(from|import)\s+(\.\.)?oracle\b", re.M)
     for path, text in _sources("lsq_synth", (".py",)):
         assert not pat_oracle.search(text), path
+
+
+def test_binding_fails_loudly_without_the_cuda_library(tmp_path):
+    """Without liblsq.so the package does not import: there is no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2410_06319_gb300"
+    pkg.mkdir()
+    for f in ("__init__.py", "_lib.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2410_06319_gb300", f), pkg / f)
+    res = subprocess.run([sys.executable, "-c", "import paper_2410_06319_gb300"], cwd=str(tmp_path),
+                         capture_output=True, text=True, env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert res.returncode != 0
+    assert "ImportError" in res.stderr and "no non-CUDA fallback" in res.stderr
