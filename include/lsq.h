@@ -24,9 +24,9 @@
  *   LSQ_NOT_CONVERGED with the last iterate written; device-side waits that
  *   run out give LSQ_E_TIMEOUT; CUDA errors give LSQ_E_CUDA.
  * - The common argument tuple is (A, b, m, n, s, u_s, u_p, u_w, u_r, tol,
- *   seed): u_s = sketch precision (Alg. 1 step 1), u_p = QR precision u_QR
- *   (Alg. 1 step 2), u_w = working precision u (Alg. 2), u_r = residual
- *   precision (Alg. 2 lines 5-6), tol = LSQR and FGMRES tolerance (Sec. 5),
+ *   seed): u_s = sketch precision (Alg. 1 (sketch)), u_p = QR precision u_QR
+ *   (Alg. 1 (QR)), u_w = working precision u (Alg. 2), u_r = residual
+ *   precision (Alg. 2 (refinement residual and h = R^-T g)), tol = LSQR and FGMRES tolerance (Sec. 5),
  *   seed = key of the Philox4x32-10 stream that defines the sketch matrix.
  *   A call ignores the members of the tuple it does not use.
  *
@@ -161,7 +161,7 @@ const char* lsq_status_string(lsq_status st);
 const char* lsq_last_cuda_error(const lsq_handle* h);
 
 /*
- * lsq_sketch -- Algorithm 1 step 1 (Sec. 3): Y = Omega [A | b] in precision
+ * lsq_sketch -- Algorithm 1 (the sketch) (Sec. 3): Y = Omega [A | b] in precision
  * u_s, with the one-sided power-of-two column scaling of Sec. 3.2 (on unless
  * opts->no_colscale) applied before the cast and removed from Y afterwards.
  * F16/BF16 use tcgen05 kind::f16 tensor cores, BF16X3 the same on the three
@@ -179,7 +179,7 @@ lsq_status lsq_sketch(lsq_handle* h, const double* A, const double* b, int64_t m
                       double tol, uint64_t seed, const lsq_opts* opts, double* Y);
 
 /*
- * lsq_qr_r -- Algorithm 1 step 2: Householder QR of Y[:, :n] in precision
+ * lsq_qr_r -- Algorithm 1 (the QR of the sketch): Householder QR of Y[:, :n] in precision
  * u_p (F32 or F64), reflectors also applied to Y[:, n].  R is normalised to a
  * non-negative diagonal.  Y is computed by lsq_sketch unless opts->Y_in.
  * Out: R, device FP64 n x n column-major (ld = n), upper triangular, values
@@ -191,7 +191,7 @@ lsq_status lsq_qr_r(lsq_handle* h, const double* A, const double* b, int64_t m, 
                     double tol, uint64_t seed, const lsq_opts* opts, double* R, double* xs);
 
 /*
- * lsq_lsqr -- Algorithm 2 line 1: LSQR (Paige & Saunders 1982) on A R^-1
+ * lsq_lsqr -- Algorithm 2 (the LSQR start): LSQR (Paige & Saunders 1982) on A R^-1
  * in working precision u_w (F32 or F64), started from x_s (or opts->x0_in),
  * at most opts->lsqr_maxit (2n) iterations, stopping tests
  * ||r|| <= tol ||b|| or ||Ahat^T r|| <= tol ||Ahat||_est ||r||.
@@ -270,7 +270,7 @@ lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_pre
                      uint64_t seed, double* out);
 
 /*
- * lsq_qr_r_noalloc -- the QR of lsq_qr_r (Algorithm 1 step 2) for callers
+ * lsq_qr_r_noalloc -- the QR of lsq_qr_r (Algorithm 1 (the QR of the sketch)) for callers
  * that cannot allocate.  The paper has no counterpart: this is an interface
  * of this library only.
  *

@@ -13,12 +13,12 @@ and its application in GMRES-based iterative refinement" (arXiv 2410.06319):
 * ``rng``      -- Philox4x32-10 counter stream and the FP64 Box-Muller
                   Gaussian used for the sketch matrix (Sec. 2: Gaussian
                   embedding with N(0, 1/s) entries; Sec. 5: Omega = s^-1/2 G).
-* ``sketch``   -- Algorithm 1 step 1 (Y = Omega A in u_s), with the one-sided
+* ``sketch``   -- Algorithm 1 (the sketch) (Y = Omega A in u_s), with the one-sided
                   power-of-two column scaling of Sec. 3.2.
-* ``qr``       -- Algorithm 1 step 2 (Householder QR of Y; R only) and the
+* ``qr``       -- Algorithm 1 (the QR of the sketch) (Householder QR of Y; R only) and the
                   sketch-and-solve start x_s = R^-1 Q^T Omega b (Sec. 4).
-* ``lsqr``     -- Algorithm 2 line 1: LSQR right-preconditioned by R.
-* ``fgmres``   -- Algorithm 2 line 7: split-preconditioned FGMRES, Eq. (1.2).
+* ``lsqr``     -- Algorithm 2 (the LSQR start): LSQR right-preconditioned by R.
+* ``fgmres``   -- Algorithm 2 (the FGMRES solve): split-preconditioned FGMRES, Eq. (1.2).
 * ``lsir``     -- Algorithm 2 (augmented-system iterative refinement) with
                   the precision-escalation rule of Sec. 5.
 * ``exact``    -- double-double residuals (Dot2) and a refined reference

@@ -9,7 +9,7 @@ solve.  This oracle plays that role for the stored FP64 data (A, b):
   split exactly into two doubles (Dekker's TwoProduct with Veltkamp's
   splitting) and every sum taken by ``math.fsum`` (Shewchuk's exactly
   rounded summation), so each entry is the correctly rounded value of the
-  exact expression.  This is the residual in precision u_r of Alg. 2 line 5
+  exact expression.  This is the residual in precision u_r of Alg. 2 (refinement residual)
   with u_r below double.
 * ``reference_solution`` solves the LS problem by Householder QR of A
   (LAPACK through numpy, FP64) and refines it on the augmented system with

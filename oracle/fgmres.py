@@ -1,4 +1,4 @@
-"""Oracle: Algorithm 2 line 7 -- split-preconditioned FGMRES on the augmented system.
+"""Oracle: Algorithm 2 (the FGMRES solve) -- split-preconditioned FGMRES on the augmented system.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 

@@ -2,22 +2,22 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Steps in the paper's order (Alg. 2, Sec. 4):
-  1. x_0 = LSQR(A, b) right-preconditioned by R, started at x_s      (u)
-  2. r_0 = b - A x_0                                                (u)
-  loop i = 0, 1, ...:
-  5. [f_i; g_i] = [b; 0] - [[I, A], [A^T, 0]] [r_i; x_i]             (u_r)
-  6. h_i = R^-T g_i                                                 (u_r)
-  7. FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f_i; h_i], dx = R^-1 dz
-                                                   (u, u_A, u_L, u_R)
-  8. [r_{i+1}; x_{i+1}] = [r_i; x_i] + [dr; dx]                       (u)
+The steps, in the paper's order (Alg. 2, Sec. 4):
+  - x_0 = LSQR(A, b) right-preconditioned by R, started at x_s       (u)
+  - r_0 = b - A x_0                                                 (u)
+  - then, for i = 0, 1, ... until the stopping rule holds:
+      [f_i; g_i] = [b; 0] - [[I, A], [A^T, 0]] [r_i; x_i]             (u_r)
+      h_i = R^-T g_i                                                 (u_r)
+      FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f_i; h_i], dx = R^-1 dz
+                                                     (u, u_A, u_L, u_R)
+      [r_{i+1}; x_{i+1}] = [r_i; x_i] + [dr; dx]                       (u)
 Sec. 5: at most 30 refinement steps; FGMRES at most 50 iterations with the
 LSQR tolerance; if the loop does not converge and kappa(A) < u_s^-1, the
 loop is run again from (x_0, r_0) with u_A = u_L = u_R = u^2.
 
 Stopping.  The paper stops when both forward errors against the true x*, r*
 are <= 4u; ``lsir`` does exactly that when (xstar, rstar) are given.
-Otherwise it uses the computable rule of this build: stop after step i if
+Otherwise it uses a computable rule: stop after step i if
 ||dx_i|| <= u ||x_{i+1}|| and ||dr_i|| <= u ||r_{i+1}||, or if (i >= 1) the
 contraction estimates rho = ||d_i|| / ||d_{i-1}|| are below 1/2 and
 rho ||dx_i|| <= 4u ||x_{i+1}||, rho ||dr_i|| <= 4u ||r_{i+1}|| (the next
@@ -45,7 +45,7 @@ def _residual(A, b, r, x, ur):
 
 def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None, rstar=None,
            gm_work_dtype=np.float64):
-    """Steps 4-11 of Alg. 2 from (x0, r0).  Returns (x, r, info)."""
+    """The refinement loop of Alg. 2 from (x0, r0).  Returns (x, r, info)."""
     x = np.array(x0, np.float64, copy=True)
     r = np.array(r0, np.float64, copy=True)
     its, gm_total, converged = 0, 0, False

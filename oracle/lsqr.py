@@ -1,4 +1,4 @@
-"""Oracle: Algorithm 2 line 1 -- LSQR right-preconditioned by R.
+"""Oracle: Algorithm 2 (the LSQR start) -- LSQR right-preconditioned by R.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
@@ -8,7 +8,7 @@ it solves min_z || (b - A x0) - Ahat z || and returns x = x0 + R^-1 z.
 
 Stopping (the paper runs MATLAB's lsqr for at most 2n iterations with tol
 1e-6 for single and 1e-12 for double working precision, Sec. 5; MATLAB's
-tests are the two Paige-Saunders tests).  This build's reading:
+tests are the two Paige-Saunders tests).  The reading taken here:
   S1: ||r_k|| <= tol ||b||,
   S2: ||Ahat^T r_k|| <= tol * ||Ahat||_est * ||r_k||,
 where r_k = b - A x_k (= phibar), ||Ahat^T r_k|| = phibar * alpha * |c|, and

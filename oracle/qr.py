@@ -1,4 +1,4 @@
-"""Oracle: Algorithm 1 step 2 -- Householder QR of the sketch, R only.
+"""Oracle: Algorithm 1 (the QR of the sketch) -- Householder QR of the sketch, R only.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 

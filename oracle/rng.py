@@ -4,7 +4,7 @@ Test infrastructure only (see ``oracle/__init__.py``).
 
 The paper draws Omega with i.i.d. N(0, 1/s) entries (Sec. 2, Gaussian
 embedding; Sec. 5 uses Omega = (4n)^-1/2 G with G standard normal).  It does
-not say how G is drawn.  This build's reading: G is never stored; entry
+not say how G is drawn.  The reading taken here: G is never stored; entry
 G[i, j] (i = sketch row in [0, s), j = row of A in [0, m)) is a pure function
 of (i, j, seed), defined as follows.
 

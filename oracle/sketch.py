@@ -1,10 +1,10 @@
-"""Oracle: Algorithm 1 step 1 -- the sketch Y = Omega [A | b] in precision u_s.
+"""Oracle: Algorithm 1 (the sketch) -- the sketch Y = Omega [A | b] in precision u_s.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
 * Sec. 3.2 (one-sided diagonal scaling): each column is scaled before the
   cast to the low precision, so the largest entry sits near the top of the
-  format's range; the preconditioner becomes R S^-1.  This build's reading
+  format's range; the preconditioner becomes R S^-1.  The reading taken here
   uses a power of two d_j per column (exact, so S^-1 is exact), chosen so
   that max_i |a_ij| d_j lies in [T, 2T) with T = 2^14 for f16/bf16 and
   T = 2^7 for e4m3 (T = 1, no scaling, for f32/f64).
@@ -48,7 +48,7 @@ def column_scale_exponents(M, fmt):
 def cast_scaled(A, b, fmt):
     """Return (A_s, b_s, kA, kb): fl_s(A 2^kA), fl_s(b 2^kb) as FP64 arrays.
 
-    For ``bf16x3`` (this build's split-term reading of a single-precision
+    For ``bf16x3`` (a split-term reading of a single-precision
     sketch on BF16 tensor cores) A_s is the exact sum hi + lo + lo2 of the
     three BF16 terms of ``rng.split3``.
     """

@@ -343,7 +343,7 @@ float* stage_cast(Ctx& c) {
   return a32;
 }
 
-// Alg. 1 step 1 -> Y (s x (n+1), column-major, FP64).
+// Alg. 1 (sketch) -> Y (s x (n+1), column-major, FP64).
 void stage_sketch(Ctx& c, double* Y) {
   const int fmt = fmt_of(c.us);
   const int64_t ncols = c.n + 1;
@@ -442,7 +442,7 @@ RCopies stage_prepare_r(Ctx& c, const double* R) {
   return r;
 }
 
-// Alg. 1 step 2 -> R (n x n) and c; then x_s = R^-1 c in u_QR.
+// Alg. 1 (QR) -> R (n x n) and c; then x_s = R^-1 c in u_QR.
 void stage_qr(Ctx& c, const double* Y, double* R, double* xs, RCopies* rc) {
   {
     StageTimer t(c.h, ST_QR);
@@ -465,7 +465,7 @@ struct LsqrOut {
   LsqrState st;
 };
 
-// Alg. 2 line 1: preconditioned LSQR in working precision W from x0 -> x.
+// Alg. 2 (LSQR start): preconditioned LSQR in working precision W from x0 -> x.
 template <typename W>
 LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const Tri<W>& tri, const double* x0,
                      double* x) {
@@ -550,7 +550,7 @@ struct GmOut {
   double dr2, r2, dx2, x2;
 };
 
-// Alg. 2 line 7: FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (operator
+// Alg. 2 (FGMRES): FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (operator
 // products in TOP), x0 = 0; r += dr, x += dx.
 template <typename TOP>
 GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, const double* f,
@@ -664,7 +664,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   return go;
 }
 
-// Steps 4-11 of Alg. 2 from (x0, r0), FGMRES products in TOP.
+// The refinement loop of Alg. 2 from (x0, r0), FGMRES products in TOP.
 template <typename TOP>
 bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const RCopies& rc, double* x, double* r,
                   lsq_info* info) {
@@ -989,7 +989,7 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     Front fr = run_front(c, x0, inf);
     double* rr = r ? r : static_cast<double*>(ws(c.h, "ir_r", c.m * 8));
     double* r0 = static_cast<double*>(ws(c.h, "ir_r0", c.m * 8));
-    // r0 = b - A x0 in the working precision (Alg. 2 line 2)
+    // r0 = b - A x0 in the working precision (Alg. 2 (initial residual))
     {
       StageTimer t(c.h, ST_RES);
       const int64_t nvec = round_up(c.n, 4) + 4;

@@ -2,9 +2,9 @@
 //
 // Passes (one coalesced, 128-bit vectorised read of A per call, a warp per
 // row, the row kept in registers for both products):
-//   LSQR   (Alg. 2 line 1):  q = A t + cu u ; P = A^T q ; sum q^2
-//   FGMRES (Alg. 2 line 7):  w_top = v_top + A z_bot ; P = A^T v_top
-//   residual (line 5, u_r):  f = b - r - A x ; P = A^T (-r)
+//   LSQR (Alg. 2, LSQR start):  q = A t + cu u ; P = A^T q ; sum q^2
+//   FGMRES (Alg. 2, FGMRES):  w_top = v_top + A z_bot ; P = A^T v_top
+//   residual (refinement, u_r):  f = b - r - A x ; P = A^T (-r)
 // P is reduced per CTA (fixed order) and then across CTAs by colsum, so the
 // results are deterministic.
 #include <type_traits>

@@ -1,4 +1,4 @@
-// Algorithm 1 step 2: Householder QR of the sketch Y (s x n) in precision
+// Algorithm 1 (the QR of the sketch): Householder QR of the sketch Y (s x n) in precision
 // u_QR (FP32 or FP64), R factor only; the reflectors are also applied to the
 // sketched right-hand side (column n), giving c = (Q^T Omega b)[:n] for the
 // sketch-and-solve start x_s = R^-1 c (Sec. 4).

@@ -1,4 +1,4 @@
-// Algorithm 1 step 1 (Sec. 3): the sketch Y = Omega [A | b] in precision u_s.
+// Algorithm 1 (the sketch) (Sec. 3): the sketch Y = Omega [A | b] in precision u_s.
 //
 //  * cast pass (Sec. 3.2 one-sided scaling): column maxima of [A | b] -> a
 //    power-of-two exponent per column -> A_s = fl_s(2^k A) written K-major

@@ -1,4 +1,4 @@
-// lsq_qr_r_noalloc: the Householder QR of a sketch (Algorithm 1 step 2) run
+// lsq_qr_r_noalloc: the Householder QR of a sketch (Algorithm 1 (the QR of the sketch)) run
 // entirely in a fixed, file-scope device scratch array, for callers that must
 // not allocate (see include/lsq.h).  The factorization itself is the same
 // launch sequence lsq_qr_r uses; only where its scratch lives differs.

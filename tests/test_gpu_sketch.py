@@ -1,4 +1,4 @@
-"""lsq_sketch (tcgen05 / CUDA-core) against the oracle's Algorithm 1 step 1."""
+"""lsq_sketch (tcgen05 / CUDA-core) against the oracle's Algorithm 1 (the sketch)."""
 import numpy as np
 import pytest
 import torch

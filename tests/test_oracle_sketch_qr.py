@@ -1,4 +1,4 @@
-"""Pins for the oracle's Algorithm 1: sketch (step 1) and Householder R (step 2)."""
+"""Pins for the oracle's Algorithm 1: the sketch and its Householder R."""
 import numpy as np
 import pytest
 
