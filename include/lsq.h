@@ -113,6 +113,9 @@ typedef struct lsq_opts {
   const double* R_in;     /* optional device R, n x n column-major upper triangular:
                              skips sketch and QR inside lsq_lsqr/lsq_lsir */
   const double* x0_in;    /* optional device LSQR start (n); used with R_in */
+  int64_t sketch_kchunk;  /* tensor-core sketch: at most this many rows of A per split of the
+                             m range (each split is summed in FP32, the splits in FP64);
+                             0 -> the library's choice */
 } lsq_opts;
 
 /* Diagnostics of one call. */
@@ -137,9 +140,10 @@ typedef struct lsq_info {
   double ir_dx_hist[32];    /* ||dx_i|| / ||x_{i+1}|| of each refinement step */
   double ir_dr_hist[32];    /* ||dr_i|| / ||r_{i+1}|| of each refinement step */
   double gmres_relres[32];  /* FGMRES relative residual reached in each refinement step */
-  double kern_ms[8];        /* with opts->timing: summed device time of the sketch GEMM (with its
-                               correction), LSQR pass, FGMRES pass, residual pass, FGMRES Arnoldi
-                               step and FGMRES triangular solves; two entries spare */
+  double kern_ms[8];        /* with opts->timing: summed device time of the sketch GEMM, LSQR
+                               pass, FGMRES pass, residual pass, FGMRES Arnoldi step, FGMRES
+                               triangular solves and the sketch's deferred correction; one
+                               entry spare */
   int64_t kern_launches[8]; /* number of launches behind each kern_ms entry */
 } lsq_info;
 
@@ -310,6 +314,17 @@ lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_pre
  *      The scratch's barrier and error words must be zero when the kernels
  *      start: each call clears them on cuda_stream itself.
  */
+/*
+ * lsq_probe_fma_rate -- measures the device's fused multiply-add throughput
+ * (which = 0: FP64, 1: FP32) in FMAs per second on the current device, with
+ * independent FMA chains on every SM (best of five timed launches on
+ * cuda_stream after one warm-up).  The paper has no counterpart: this is the
+ * denominator of the rooflines of the FP64-bound kernels (the residual pass,
+ * the Arnoldi step and the FP64 QR), which GB300's narrow FP64 pipe sets.
+ * Allocates and frees a few bytes of device memory; synchronises cuda_stream.
+ */
+lsq_status lsq_probe_fma_rate(int which, void* cuda_stream, double* fma_per_s);
+
 #define LSQ_NOALLOC_WORK_BYTES 8388608
 #define LSQ_NOALLOC_MAX_N 1024
 lsq_status lsq_qr_r_noalloc(const double* Y, int64_t s, int64_t n, lsq_prec u_p, double* R,

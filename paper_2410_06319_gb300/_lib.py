@@ -27,7 +27,7 @@ STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RAN
 
 #: kernels timed with opts.timing (order of lsq_info.kern_ms)
 KERNELS = ["sketch_gemm", "lsqr_pass", "fgmres_pass", "residual_pass", "arnoldi_step", "fgmres_trsv",
-           "spare6", "spare7"]
+           "sketch_fix", "spare7"]
 
 
 class Opts(ctypes.Structure):
@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("ir_stop", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("no_graph", ctypes.c_int32), ("sketch_exact", ctypes.c_int32),
                 ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
-                ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p)]
+                ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p),
+                ("sketch_kchunk", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -95,8 +96,9 @@ lib.lsq_lsir_batched.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Problem), ct
                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
 lib.lsq_qr_r_noalloc.argtypes = [_P, _I64, _I64, ctypes.c_int, _P, _P, _P]
+lib.lsq_probe_fma_rate.argtypes = [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
 for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir", "lsq_lsir_host",
-           "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc"):
+           "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc", "lsq_probe_fma_rate"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -270,3 +272,15 @@ def lsq_qr_r_noalloc(Y, s, n, u_p, R, c=None, stream=None):
     if st not in (0, -9):
         raise LsqError(st, "lsq_qr_r_noalloc")
     return st
+
+
+def lsq_probe_fma_rate(which="f64", stream=None):
+    """FMAs per second of the current device (which = "f64" or "f32")."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_double(0.0)
+    st = lib.lsq_probe_fma_rate({"f64": 0, "f32": 1}[which], _P(stream), ctypes.byref(out))
+    if st != 0:
+        raise LsqError(st, "lsq_probe_fma_rate")
+    return out.value

@@ -136,7 +136,8 @@ struct StageTimer {
 };
 
 enum Stage { ST_CAST = 0, ST_SKETCH, ST_QR, ST_LSQR, ST_RES, ST_FGMRES, ST_UPDATE, ST_TOTAL };
-enum Kern { K_SKETCH = 0, K_LSQR_PASS, K_FGM_PASS, K_RES_PASS, K_ARNOLDI, K_TRSV, K_NKERN = 8 };
+enum Kern { K_SKETCH = 0, K_LSQR_PASS, K_FGM_PASS, K_RES_PASS, K_ARNOLDI, K_TRSV, K_SKETCH_FIX,
+            K_NKERN = 8 };
 constexpr int kKernMark = 100;   // marks with stage >= kKernMark time single kernels
 
 // Brackets one launch with events when timing is on (opts.timing).
@@ -221,6 +222,7 @@ lsq_status validate(const Ctx& c, bool need_b) {
   if (c.o.gmres_maxit < 0 || c.o.gmres_maxit > kMaxGmres) return LSQ_E_INVAL;
   if (c.o.ir_maxit < 0 || c.o.ir_maxit > 32) return LSQ_E_INVAL;
   if (c.o.lsqr_maxit < 0) return LSQ_E_INVAL;
+  if (c.o.sketch_kchunk < 0) return LSQ_E_INVAL;
   return LSQ_OK;
 }
 
@@ -351,7 +353,9 @@ void stage_sketch(Ctx& c, double* Y) {
   int* kexp = static_cast<int*>(ws(c.h, "kexp", ncols * 4));
   if (fmt == FMT_F16 || fmt == FMT_BF16 || fmt == FMT_E4M3 || fmt == FMT_BF16X3) {
     SketchPlan p;
-    if (!plan_sketch_tc(fmt, c.s, c.m, ncols, c.h->num_sms, &p)) throw StatusFail{LSQ_E_UNSUPPORTED};
+    if (!plan_sketch_tc(fmt, c.s, c.m, ncols, c.h->num_sms, &p, c.o.sketch_kchunk))
+      throw StatusFail{LSQ_E_UNSUPPORTED};
+    if (p.splits > 65535) throw StatusFail{LSQ_E_INVAL};
     const int t = c.o.no_colscale ? -1 : (fmt == FMT_E4M3 ? 7 : 14);
     const int eb = (fmt == FMT_E4M3) ? 1 : 2;
     const int64_t ldb = round_up(c.m, 16 / eb);
@@ -382,6 +386,9 @@ void stage_sketch(Ctx& c, double* Y) {
       {
         KernTimer kt(c.h, K_SKETCH, c.o.timing);
         L(launch_sketch_tc(p, tm, c.seed, partial, c.h->d_err, c.st, rec, cnt, cap));
+      }
+      {
+        KernTimer kt(c.h, K_SKETCH_FIX, c.o.timing);
         L(launch_sketch_fix(p, c.seed, rec, cnt, cap, c.A, c.lda, c.b, kexp, partial, ovf, c.st));
       }
       c.h->launches += 1;

@@ -548,7 +548,8 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
 
 static int round_up_int(int64_t v, int64_t q) { return (int)(((v + q - 1) / q) * q); }
 
-bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p) {
+bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p,
+                    int64_t max_kchunk) {
   if (fmt != FMT_F16 && fmt != FMT_BF16 && fmt != FMT_E4M3 && fmt != FMT_BF16X3) return false;
   const int EB = (fmt == FMT_E4M3) ? 1 : 2;
   p->nt = (fmt == FMT_BF16X3) ? 3 : 1;
@@ -577,7 +578,29 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
   int64_t splits = (2 * (int64_t)num_sms + base - 1) / base;
   if (splits < 1) splits = 1;
   if (splits > ksteps) splits = ksteps;
-  const int64_t steps_per = (ksteps + splits - 1) / splits;
+  int64_t steps_per = (ksteps + splits - 1) / splits;
+  if (max_kchunk == 0 && fmt == FMT_BF16X3) {
+    // Single precision on BF16 tensor cores: the FP32 accumulation of one split,
+    // not the cast, limits Y once the split is long (the error of the sum grows
+    // about linearly with its length, so kappa(A R^-1) does too: 378 at 8e5 rows,
+    // 6.8 at 8192 and 3.5 at 2048 for m = 4e6, n = 1000, kappa(A) = 1e7).  Splits of
+    // at most kBf16x3Chunk rows, unless their FP32 partials would pass kPartialBudget.
+    constexpr int64_t kBf16x3Chunk = 2048;
+    constexpr double kPartialBudget = 34359738368.0;   // 32 GiB
+    const double per_split = 4.0 * (double)ncols * (double)s;
+    const int64_t max_splits = (int64_t)(kPartialBudget / per_split);
+    int64_t want = (m + kBf16x3Chunk - 1) / kBf16x3Chunk;
+    if (want > max_splits) want = max_splits;
+    if (want > 65535) want = 65535;
+    if (want > splits) {
+      const int64_t sp = (ksteps + want - 1) / want;
+      if (sp < steps_per) steps_per = sp;
+    }
+  }
+  if (max_kchunk > 0) {
+    const int64_t cap_steps = max_kchunk / BK > 0 ? max_kchunk / BK : 1;
+    if (steps_per > cap_steps) steps_per = cap_steps;
+  }
   p->kchunk = steps_per * BK;
   p->splits = (int)((m + p->kchunk - 1) / p->kchunk);
   p->s_pad = s;

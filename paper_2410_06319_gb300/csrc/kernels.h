@@ -43,7 +43,9 @@ struct SketchPlan {
 };
 
 // Builds the plan for the tensor-core sketch; returns false if unsupported.
-bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p);
+// max_kchunk > 0 caps the rows of A per split (rounded down to whole K steps).
+bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p,
+                    int64_t max_kchunk = 0);
 // Encodes the TMA descriptor of the K-major operand Bt (rows x m, row stride ldb elements).
 bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
                     int box_rows, int rowb);

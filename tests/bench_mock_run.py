@@ -48,6 +48,7 @@ def _cpu(f):
     @functools.wraps(f)
     def g(*a, **k):
         k.pop("device", None)
+        k.pop("pin_memory", None)
         return f(*a, **k)
     return g
 
@@ -95,6 +96,30 @@ def _lsqr(h, A, b, m, n, s, *rest):
     return 0, info
 
 
+def _ok(*a, **k):
+    return 0
+
+
+class _DeviceRandsvd:
+    """The device generator on the CPU (same construction, small sizes)."""
+
+    def __init__(self, m, n, seed=0, device=None):
+        from lsq_synth import randsvd_problem
+        self.m, self.n, self.seed = m, n, seed
+        P = randsvd_problem(m, n, 1.0, rho=0.0, seed=seed)
+        self.x_true = torch.from_numpy(P.x_true)
+
+    def problem(self, kappa, rho):
+        from lsq_synth import randsvd_problem
+        P = randsvd_problem(self.m, self.n, kappa, rho=rho, seed=self.seed)
+        self.x_true = torch.from_numpy(P.x_true)
+        A = torch.from_numpy(P.A)
+        return A, torch.from_numpy(P.b), torch.from_numpy(P.b - P.A @ P.x_true)
+
+    def release(self):
+        pass
+
+
 def _batched(h, probs, *rest, **kw):
     infos = []
     for _ in probs:
@@ -107,11 +132,17 @@ def _batched(h, probs, *rest, **kw):
 fake.Handle = _Handle
 fake.lsq_lsir, fake.lsq_lsqr, fake.lsq_lsir_batched = _lsir, _lsqr, _batched
 fake.lsq_lsir_host = _lsir_host
+fake.lsq_sketch, fake.lsq_qr_r = _ok, _ok
+fake.lsq_probe_fma_rate = lambda *a, **k: 5.0e11
 sys.modules["paper_2410_06319_gb300"] = fake
+import lsq_synth.device   # noqa: E402
+lsq_synth.device.DeviceRandsvd = _DeviceRandsvd
+torch.cuda.empty_cache = lambda *a: None
 
 import bench   # noqa: E402
 
 bench.WL.update(m=3000, n=60, s=240)
+bench.WL2.update(m=2000, n=40, s=160)
 bench.BATCH.update(count=2, m_range=(500, 600), n_range=(8, 10))
 sys.argv = ["bench.py"] + sys.argv[1:]
 bench.main()

@@ -32,10 +32,13 @@ def test_gpu_arm_line_follows_the_contract():
     # one N = 1 job: K solves in the timed region, each event pair 10 ms
     assert d["value"] == d["ms_per_step"] == 10.0 / steps
     r = d["roofline"]
-    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel"):
         assert k in r, k
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["frac"] - r["achieved"] / r["peak"]) <= 1e-12 * r["frac"]
+    # the roofline names the kernel with the largest device time per solve
+    ks = d["kernels"]
+    assert r["kernel"] == max(ks, key=lambda k: ks[k]["total_ms"])
+    assert d["tts_roofline"]["frac"] > 0
     c = d["cpu_baseline"]
     for k in ("value", "unit", "cores", "kind", "sample"):
         assert k in c, k
@@ -50,7 +53,7 @@ def test_gpu_arm_line_follows_the_contract():
     assert d["gpu_launches"] > 0
 
 
-def test_e2e_falls_back_to_device_copies_and_says_so():
+def test_e2e_failure_is_reported_not_fatal():
     d = _line("--steps", "1", "--warmup", "3", env={"BENCH_MOCK_HOST_CALL_FAILS": "1"})
-    assert d["e2e"]["path"].startswith("torch copies around lsq_lsir (lsq_lsir_host: RuntimeError")
-    assert d["e2e"]["value"] > 0 and d["value"] == 10.0
+    assert d["e2e"]["value"] is None and d["e2e"]["error"].startswith("RuntimeError")
+    assert d["value"] == 10.0
