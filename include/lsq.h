@@ -145,6 +145,7 @@ typedef struct lsq_info {
                                triangular solves and the sketch's deferred correction; one
                                entry spare */
   int64_t kern_launches[8]; /* number of launches behind each kern_ms entry */
+  int64_t arnoldi_second_passes; /* FGMRES Arnoldi steps that ran the second Gram-Schmidt pass */
 } lsq_info;
 
 /* sizeof(lsq_opts) for which = 0, sizeof(lsq_info) for which = 1, else 0: lets

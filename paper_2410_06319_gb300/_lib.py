@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
                 ("stage_ms", ctypes.c_double * 8), ("gpu_launches", ctypes.c_int64),
                 ("ir_dx_hist", ctypes.c_double * 32), ("ir_dr_hist", ctypes.c_double * 32),
                 ("gmres_relres", ctypes.c_double * 32),
-                ("kern_ms", ctypes.c_double * 8), ("kern_launches", ctypes.c_int64 * 8)]
+                ("kern_ms", ctypes.c_double * 8), ("kern_launches", ctypes.c_int64 * 8),
+                ("arnoldi_second_passes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

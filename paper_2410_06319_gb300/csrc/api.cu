@@ -357,19 +357,17 @@ void stage_sketch(Ctx& c, double* Y) {
       throw StatusFail{LSQ_E_UNSUPPORTED};
     if (p.splits > 65535) throw StatusFail{LSQ_E_INVAL};
     const int t = c.o.no_colscale ? -1 : (fmt == FMT_E4M3 ? 7 : 14);
-    const int eb = (fmt == FMT_E4M3) ? 1 : 2;
-    const int64_t ldb = round_up(c.m, 16 / eb);
     const int64_t rows = (int64_t)p.ngroups * p.bn;
     void* Bt;
     {
       StageTimer tt(c.h, ST_CAST);
       L(launch_scale_exps(cmax, ncols, t, kexp, c.st));
-      Bt = ws(c.h, "bt", (size_t)p.nt * rows * ldb * eb);
-      L(launch_cast_transpose(fmt, c.A, c.lda, c.b, c.m, c.n, kexp, Bt, ldb, rows, c.st));
+      Bt = ws(c.h, "bt", bt_bytes(fmt, c.m, rows));
+      L(launch_cast_transpose(fmt, c.A, c.lda, c.b, c.m, c.n, kexp, Bt, rows, c.st));
     }
     StageTimer tt(c.h, ST_SKETCH);
     CUtensorMap tm;
-    if (!encode_bt_tmap(&tm, Bt, fmt, (int64_t)p.nt * rows, c.m, ldb, p.bn / p.nsub, p.rowb))
+    if (!encode_bt_tmap(&tm, Bt, fmt, (int64_t)p.nt * rows, c.m, p.bn / p.nsub, p.rowb))
       throw StatusFail{LSQ_E_UNSUPPORTED};
     float* partial = static_cast<float*>(ws(c.h, "partial", (size_t)p.splits * ncols * p.s_pad * 4));
     const uint32_t cap = sketch_rec_cap(p);
@@ -553,6 +551,7 @@ LsqrState stage_lsqr(Ctx& c, const W* Aw, int64_t ldw, const Tri<W>& tri, const 
 
 struct GmOut {
   int its;
+  int reorth;
   double relres;
   double dr2, r2, dx2, x2;
 };
@@ -663,6 +662,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   std::memcpy(hn, c.h->h_pinned, 32);
   GmOut go;
   go.its = out.j;
+  go.reorth = out.nreorth;
   go.relres = out.relres;
   go.dr2 = hn[0];
   go.r2 = hn[1];
@@ -701,6 +701,7 @@ bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const RCopies& rc, doubl
     GmOut go = stage_fgmres<TOP>(c, Aop, ldop, rc.get<TOP>(), f, hv, gtol, gmax, r, x);
     info->gmres_its[i] = go.its;
     info->gmres_its_total += go.its;
+    info->arnoldi_second_passes += go.reorth;
     info->ir_its = i + 1;
     const double dxr = go.x2 > 0 ? go.dx2 / go.x2 : 0.0;
     const double drr = go.r2 > 0 ? go.dr2 / go.r2 : 0.0;

@@ -53,9 +53,9 @@ cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, doub
 cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
                              int nblk, cudaStream_t s);
 // The whole Arnoldi step in one cooperative launch (classical Gram-Schmidt with the
-// twice-is-enough second pass, Givens step, new column; blocks synchronised by a
-// bounded grid barrier on bar[0..1], which must be zero before the first launch; each
-// launch leaves it reusable): needs maxc <= 128 and num_sms >= maxc + 1.
+// twice-is-enough second pass, Givens step, new column; blocks synchronised by a bounded
+// last-arrival reduction on bar[0..1], which must be zero before the first launch; each
+// launch leaves it reusable).  Dp holds (maxc + 1) x 2 num_sms doubles; maxc <= 128.
 template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,

@@ -863,32 +863,32 @@ __global__ void gm_init_kernel(const double* sq_partial, int nblk, GmState* st, 
   }
 }
 
-// h_{j+1,j} = sqrt(s) ; Givens rotations on column j ; residual estimate ; j++.
-// One block (block 0 of the Arnoldi step).
-__device__ void gm_finish_block(double s, GmState* st, double* H, int ldh, double* cs, double* sn,
-                                double* g) {
-  __shared__ double hcs[130], css[130], sns[130];
+// h_{j+1,j} = sqrt(s); Givens rotations on column j; residual estimate; j++.
+// One warp (warp 0 of block 0 of the Arnoldi step), with the unrotated column h_{0..j, j}
+// in shared memory (hcol, rotated in place): the other warps of the block keep working.
+__device__ void gm_finish_warp(double s, GmState* st, double* hcol, double* H, int ldh, double* cs,
+                               double* sn, double* g) {
+  __shared__ double css[130], sns[130];
+  const int lane = threadIdx.x & 31;
   const int j = st->j;
-  double* hc = H + (int64_t)j * ldh;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    hcs[i] = __ldcg(hc + i);
+  for (int i = lane; i < j; i += 32) {
     css[i] = cs[i];
     sns[i] = sn[i];
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  __syncwarp();
+  if (lane == 0) {
     const double hn = sqrt(s);
-    hcs[j + 1] = hn;
+    hcol[j + 1] = hn;
     for (int i = 0; i < j; ++i) {
-      const double t = css[i] * hcs[i] + sns[i] * hcs[i + 1];
-      hcs[i + 1] = -sns[i] * hcs[i] + css[i] * hcs[i + 1];
-      hcs[i] = t;
+      const double t = css[i] * hcol[i] + sns[i] * hcol[i + 1];
+      hcol[i + 1] = -sns[i] * hcol[i] + css[i] * hcol[i + 1];
+      hcol[i] = t;
     }
-    const double den = hypot(hcs[j], hcs[j + 1]);
-    cs[j] = den > 0.0 ? hcs[j] / den : 1.0;
-    sn[j] = den > 0.0 ? hcs[j + 1] / den : 0.0;
-    hcs[j] = den;
-    hcs[j + 1] = 0.0;
+    const double den = hypot(hcol[j], hcol[j + 1]);
+    cs[j] = den > 0.0 ? hcol[j] / den : 1.0;
+    sn[j] = den > 0.0 ? hcol[j + 1] / den : 0.0;
+    hcol[j] = den;
+    hcol[j + 1] = 0.0;
     g[j + 1] = -sn[j] * g[j];
     g[j] = cs[j] * g[j];
     st->relres = fabs(g[j + 1]) / st->beta0;
@@ -896,26 +896,29 @@ __device__ void gm_finish_block(double s, GmState* st, double* H, int ldh, doubl
     st->j = j + 1;
     st->done = (st->relres <= st->tol || st->j >= st->maxit || hn == 0.0) ? 1 : 0;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = hcs[i];
+  __syncwarp();
+  double* hc = H + (int64_t)j * ldh;
+  for (int i = lane; i <= j + 1; i += 32) hc[i] = hcol[i];
 }
 
 // ---------------------------------------------------------------- fused Arnoldi step
 // One cooperative launch per FGMRES iteration, one 512-thread CTA per SM, each owning a
-// contiguous row range of the length-(m+n) vectors:
-//   sweep 1: w_top = v_top + A z; partials of h = V^T w and of ||w||^2
-//   [grid barrier] CTA c sums column c of the partials (CTA ncols sums ||w||^2), in a
-//   fixed order  [grid barrier]  every CTA reads h and ||w||^2
+// contiguous row range of the length-(m+n) vectors; FP64 throughout.
+//   w_top = v_top + A z; partials of h = V^T w and of ||w||^2 (eight basis columns per
+//   sweep over the rows, so w is read once per eight columns)
+//   [sync 1: the last CTA to arrive sums every column of the partials in a fixed order]
 //   Kahan's "twice is enough": the first pass loses more than half of ||w||^2 iff
-//   ||h||^2 > ||w||^2 / 2 (Pythagoras; decided before the update, exact at the
-//   threshold up to rounding); then
-//   one pass:  w -= V h, partial ||w||^2 [barrier]
-//   two passes: w -= V h, partials of h2 = V^T w [barrier] column sums [barrier]
-//               w -= V h2, partial ||w||^2 [barrier]
-//   every CTA sums the ||w||^2 partials in the same order; CTA 0 applies the Givens
-//   rotations; the new column V[:, j+1] = w / ||w|| (and its FP32 top copy) is written.
-// FP64 throughout; all grid barriers have bounded waits.
+//   ||h||^2 > ||w||^2 / 2 (Pythagoras, decided before the update).  Otherwise
+//   ||w - V h||^2 = ||w||^2 - ||h||^2 within a few units of FP64 rounding (V orthonormal
+//   to working accuracy, no cancellation below one half), so the update writes the new
+//   column v_{j+1} = (w - V h) / h_{j+1,j} directly: one sync per step.
+//   With the second pass: w1 = w - V h; partials of h2 = V^T w1 and ||w1||^2 [sync 2];
+//   v_{j+1} = (w1 - V h2) / sqrt(||w1||^2 - ||h2||^2) (h2 is of rounding size).
+//   CTA 0 adds h (and h2) to the Hessenberg column and applies the Givens rotations.
+// The syncs wait with a bounded spin; an expired wait records DEV_TIMEOUT_GRID and the
+// kernel returns.
 constexpr int kGmThreads = 512;
+constexpr int kGmGroup = 8;   // basis columns per sweep of the partial dot products
 template <typename TAZ>
 struct GmStepArgs {
   double* V;
@@ -924,77 +927,213 @@ struct GmStepArgs {
   const TAZ* az;
   GmState* st;
   int maxc, ldh;
-  double* Dp;     // [nblk][maxc + 1] partials (column maxc: ||w||^2)
-  double* sq;     // [nblk] partials of the final ||w||^2
+  double* Dp;     // [maxc + 1][ldd] partials, one column per block (row ncols: the squared norm)
+  double* sq;     // unused (kept for the launch signature)
   double* hsum;   // [maxc + 1] column sums
   double* H;
   double* cs;
   double* sn;
   double* g;
   float* v32;
-  unsigned* bar;
+  unsigned* bar;  // [0]: arrivals, [1]: generation
   int* err;
+  int ldd;        // leading dimension of Dp (>= the grid size)
 };
 
-// partial dots of V[:, 0..ncols) with w over rows [r0, r1) (warp per column), and
-// optionally of ||w||^2, into Dp[b][.]
-__device__ __forceinline__ void gm_partials(const double* V, int64_t ld, const double* w, int64_t r0, int64_t r1,
-                                            int ncols, double* Dpb, bool with_norm, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = warp; c < ncols; c += nw) {
-    const double* vc = V + (int64_t)c * ld;
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    int64_t i = r0 + lane;
-    for (; i + 96 < r1; i += 128) {
-      t0 += vc[i] * w[i];
-      t1 += vc[i + 32] * w[i + 32];
-      t2 += vc[i + 64] * w[i + 64];
-      t3 += vc[i + 96] * w[i + 96];
-    }
-    for (; i < r1; i += 32) t0 += vc[i] * w[i];
-    const double t = warp_sum((t0 + t1) + (t2 + t3));
-    if (lane == 0) Dpb[c] = t;
+// Sums of eight values over a warp by a reduce-scatter butterfly: at each exchange a
+// lane keeps half of its values and adds its partner's copies of them, so a lane adds
+// 4 + 2 + 1 + 1 + 1 FP64 numbers instead of 8 x 5 (GB300's FP64 pipe is narrow).
+// Lane L returns the warp total of value (L >> 2) & 7, in a fixed order.
+__device__ __forceinline__ double warp_reduce8(const double (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  double u[4], x[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double keep = b4 ? v[4 + k] : v[k], send = b4 ? v[k] : v[4 + k];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  if (with_norm) {
-    double q = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) q += w[i] * w[i];
-    q = block_sum_d(q, red);
-    if (threadIdx.x == 0) Dpb[ncols] = q;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double keep = b3 ? u[2 + k] : u[k], send = b3 ? u[k] : u[2 + k];
+    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
+  double y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  return y;
 }
 
-// w[i] -= sum_c V[c][i] h[c] over rows [r0, r1); returns this thread's sum of w[i]^2
-__device__ __forceinline__ double gm_update(const double* V, int64_t ld, double* w, int64_t r0, int64_t r1,
-                                            int ncols, const double* hs) {
-  double sqp = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-    int c = 0;
-    for (; c + 3 < ncols; c += 4) {
-      p0 += V[(int64_t)c * ld + i] * hs[c];
-      p1 += V[(int64_t)(c + 1) * ld + i] * hs[c + 1];
-      p2 += V[(int64_t)(c + 2) * ld + i] * hs[c + 2];
-      p3 += V[(int64_t)(c + 3) * ld + i] * hs[c + 3];
+// Dp[c][block] = sum over rows [r0, r1) of V[c][i] w[i] for c < ncols; Dp[ncols][block] = sum of w[i]^2.
+// The (ncols + 1) sums form G groups of eight; the CTA's rows are cut into S slices with
+// G x S close to the warp count, and each warp takes one (group, slice) task: its lanes
+// stride over the slice two rows at a time (18 loads in flight), one butterfly reduces
+// the eight sums over the warp, and one thread per column adds the S slice sums in slice
+// order.  Every partial is reduced once, whatever the number of rows per CTA.
+constexpr int kGmRed = 160;   // doubles of the slice-sum buffer (>= max(16, G) x 8 with G <= 17)
+__device__ __forceinline__ void gm_partials(const double* __restrict__ V, int64_t ld,
+                                            const double* __restrict__ w, int64_t r0, int64_t r1,
+                                            int ncols, double* Dp, int ldd, double* red /* [kGmRed] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = (ncols + kGmGroup) / kGmGroup;   // groups covering ncols + 1 sums
+  const int S = G >= nw ? 1 : nw / G;
+  const int64_t per = (r1 - r0 + S - 1) / S;
+  for (int task = warp; task < G * S; task += nw) {
+    const int g = task % G, sl = task / G, c0 = g * kGmGroup;
+    const int64_t s0 = r0 + (int64_t)sl * per, s1 = min(r1, s0 + per);
+    double t[kGmGroup];
+#pragma unroll
+    for (int k = 0; k < kGmGroup; ++k) t[k] = 0.0;
+    int64_t i = s0 + lane;
+    if (c0 + kGmGroup <= ncols) {   // eight basis columns, no norm
+      for (; i + 32 < s1; i += 64) {
+        const double wa = w[i], wb = w[i + 32];
+        double va[kGmGroup], vb[kGmGroup];
+#pragma unroll
+        for (int k = 0; k < kGmGroup; ++k) {
+          va[k] = V[(int64_t)(c0 + k) * ld + i];
+          vb[k] = V[(int64_t)(c0 + k) * ld + i + 32];
+        }
+#pragma unroll
+        for (int k = 0; k < kGmGroup; ++k) t[k] = fma(vb[k], wb, fma(va[k], wa, t[k]));
+      }
     }
-    for (; c < ncols; ++c) p0 += V[(int64_t)c * ld + i] * hs[c];
-    const double acc = w[i] - ((p0 + p1) + (p2 + p3));
-    w[i] = acc;
-    sqp += acc * acc;
+    for (; i < s1; i += 32) {
+      const double wi = w[i];
+#pragma unroll
+      for (int k = 0; k < kGmGroup; ++k) {
+        const int c = c0 + k;
+        if (c < ncols) t[k] = fma(V[(int64_t)c * ld + i], wi, t[k]);
+        else if (c == ncols) t[k] = fma(wi, wi, t[k]);
+      }
+    }
+    static_assert(kGmGroup == 8, "warp_reduce8 reduces eight sums");
+    const double tot = warp_reduce8(t);
+    if ((lane & 3) == 0) red[(sl * G + g) * kGmGroup + ((lane >> 2) & 7)] = tot;
   }
-  return sqp;
+  __syncthreads();
+  for (int c = threadIdx.x; c <= ncols; c += blockDim.x) {
+    const int g = c / kGmGroup, k = c % kGmGroup;
+    double s = 0.0;
+    for (int sl = 0; sl < S; ++sl) s += red[(sl * G + g) * kGmGroup + k];
+    Dp[(int64_t)c * ldd + blockIdx.x] = s;   // column-major: [column][block]
+  }
+  __syncthreads();
+}
+
+// The last CTA to arrive sums the partials Dp[.][0..cols) (column c by one warp, in
+// block order) into hsum and releases the others; every CTA then copies hsum into hs.
+// Returns false if the wait ran out.
+__device__ __forceinline__ bool gm_sync_sums(double* Dp, int ldd, double* hsum, int cols, unsigned* cnt,
+                                             unsigned* gen, int* err, double* hs, int* s_flag) {
+  const unsigned nb = gridDim.x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned ticket = atomicAdd(cnt, 1u);
+    s_flag[0] = (ticket == nb - 1) ? 1 : 0;
+    s_flag[1] = (int)g;
+  }
+  __syncthreads();
+  int ok = 1;
+  if (s_flag[0]) {
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < cols; c += nw) {
+      const double* col = Dp + (int64_t)c * ldd;
+      double t0 = 0.0, t1 = 0.0;
+      unsigned q = lane;
+      for (; q + 32 < nb; q += 64) {
+        t0 += __ldcg(col + q);
+        t1 += __ldcg(col + q + 32);
+      }
+      if (q < nb) t0 += __ldcg(col + q);
+      const double t = warp_sum(t0 + t1);
+      if (lane == 0) hsum[c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gen;
+    const unsigned g = (unsigned)s_flag[1];
+    const uint64_t t0 = globaltimer_ns();
+    while (*vgen == g) {
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        set_error(err, DEV_TIMEOUT_GRID);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  if (__syncthreads_and(ok) == 0) return false;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) hs[c] = __ldcg(hsum + c);
+  __syncthreads();
+  return true;
+}
+
+// w[i] - sum_c V[c][i] h[c] for row i
+__device__ __forceinline__ double gm_row_update(const double* __restrict__ V, int64_t ld, double wi,
+                                                int64_t i, int ncols, const double* hs) {
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+  int c = 0;
+  for (; c + 3 < ncols; c += 4) {
+    p0 = fma(V[(int64_t)c * ld + i], hs[c], p0);
+    p1 = fma(V[(int64_t)(c + 1) * ld + i], hs[c + 1], p1);
+    p2 = fma(V[(int64_t)(c + 2) * ld + i], hs[c + 2], p2);
+    p3 = fma(V[(int64_t)(c + 3) * ld + i], hs[c + 3], p3);
+  }
+  for (; c < ncols; ++c) p0 = fma(V[(int64_t)c * ld + i], hs[c], p0);
+  return wi - ((p0 + p1) + (p2 + p3));
+}
+
+// The same for rows i and i2 at once (same summation order as gm_row_update): 16 loads
+// in flight per thread.
+__device__ __forceinline__ void gm_row_update2(const double* __restrict__ V, int64_t ld, int64_t i,
+                                               int64_t i2, int ncols, const double* hs, double& wa,
+                                               double& wb) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+  int c = 0;
+  for (; c + 3 < ncols; c += 4) {
+    const double* v0 = V + (int64_t)c * ld;
+    const double va0 = v0[i], va1 = v0[ld + i], va2 = v0[2 * ld + i], va3 = v0[3 * ld + i];
+    const double vb0 = v0[i2], vb1 = v0[ld + i2], vb2 = v0[2 * ld + i2], vb3 = v0[3 * ld + i2];
+    a0 = fma(va0, hs[c], a0);
+    a1 = fma(va1, hs[c + 1], a1);
+    a2 = fma(va2, hs[c + 2], a2);
+    a3 = fma(va3, hs[c + 3], a3);
+    b0 = fma(vb0, hs[c], b0);
+    b1 = fma(vb1, hs[c + 1], b1);
+    b2 = fma(vb2, hs[c + 2], b2);
+    b3 = fma(vb3, hs[c + 3], b3);
+  }
+  for (; c < ncols; ++c) {
+    a0 = fma(V[(int64_t)c * ld + i], hs[c], a0);
+    b0 = fma(V[(int64_t)c * ld + i2], hs[c], b0);
+  }
+  wa = wa - ((a0 + a1) + (a2 + a3));
+  wb = wb - ((b0 + b1) + (b2 + b3));
 }
 
 template <typename TAZ>
-__global__ void __launch_bounds__(kGmThreads) gm_step_kernel(const GmStepArgs<TAZ> a) {
-  if (a.st->done) return;   // uniform: read before any grid barrier
-  __shared__ double hs[129];
-  __shared__ double red[33];
+__global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs<TAZ> a) {
+  if (a.st->done) return;   // uniform: read before any grid sync
+  __shared__ double hs[130];
+  __shared__ double red[kGmRed];
+  __shared__ double hcol[130];   // block 0: the column j of the Hessenberg matrix
+  __shared__ int s_flag[2];
   const int j = a.st->j, ncols = j + 1;
   const int nb = gridDim.x, b = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t chunk = (a.len + nb - 1) / nb;
   const int64_t r0 = (int64_t)b * chunk, r1 = min(a.len, r0 + chunk);
-  const int ldp = a.maxc + 1;
+  const int ldd = a.ldd;
   double* w = a.w;
   const double* V = a.V;
   if (a.az) {   // w_top = v_top + A z (the pass left A z in az)
@@ -1002,59 +1141,84 @@ __global__ void __launch_bounds__(kGmThreads) gm_step_kernel(const GmStepArgs<TA
     for (int64_t i = r0 + threadIdx.x; i < min(r1, a.m); i += blockDim.x) w[i] = vj[i] + (double)a.az[i];
     __syncthreads();
   }
-  // column sums of the partials: CTA c takes column c, in a fixed order
-  auto column_sums = [&](int cols) -> bool {
-    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return false;
-    if (b < cols && warp == 0) {
-      double t = 0.0;
-      for (int q = lane; q < nb; q += 32) t += __ldcg(a.Dp + (int64_t)q * ldp + b);
-      t = warp_sum(t);
-      if (lane == 0) a.hsum[b] = t;
-    }
-    if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return false;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) hs[c] = __ldcg(a.hsum + c);
-    __syncthreads();
-    return true;
-  };
   // ---- first pass: h and ||w||^2
-  gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp + (int64_t)b * ldp, true, red);
-  if (!column_sums(ncols + 1)) return;
+  gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red);
+  if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, hs, s_flag)) return;
   const double wn2 = hs[ncols];
-  double hh = 0.0;
-  for (int c = 0; c < ncols; ++c) hh += hs[c] * hs[c];   // same order in every thread
+  if (threadIdx.x == 0) {   // ||h||^2 in the same order in every CTA
+    double q = 0.0;
+    for (int c = 0; c < ncols; ++c) q = fma(hs[c], hs[c], q);
+    red[0] = q;
+  }
+  __syncthreads();
+  const double hh = red[0];
+  __syncthreads();
   const bool second = hh > 0.5 * wn2;
+  const int64_t step = blockDim.x;
   if (b == 0) {
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) a.H[(int64_t)j * a.ldh + c] += hs[c];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hcol[c] = hs[c];
     if (threadIdx.x == 0) {
       a.st->reorth = second ? 1 : 0;
       a.st->nreorth += second ? 1 : 0;
     }
   }
-  double sqp = gm_update(V, a.ld, w, r0, r1, ncols, hs);
-  if (second) {
-    __syncthreads();   // this CTA's rows of w are final for the second pass
-    gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp + (int64_t)b * ldp, false, red);
-    if (!column_sums(ncols)) return;
+  double hn2;
+  if (!second) {
+    hn2 = wn2 - hh;
+  } else {
+    int64_t i = r0 + threadIdx.x;
+    for (; i + step < r1; i += 2 * step) {
+      double wa = w[i], wb = w[i + step];
+      gm_row_update2(V, a.ld, i, i + step, ncols, hs, wa, wb);
+      w[i] = wa;
+      w[i + step] = wb;
+    }
+    for (; i < r1; i += step) w[i] = gm_row_update(V, a.ld, w[i], i, ncols, hs);
+    __syncthreads();   // this CTA's rows of w1 are final for the second pass
+    gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red);
+    if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, hs, s_flag)) return;
     if (b == 0)
-      for (int c = threadIdx.x; c < ncols; c += blockDim.x) a.H[(int64_t)j * a.ldh + c] += hs[c];
-    sqp = gm_update(V, a.ld, w, r0, r1, ncols, hs);
+      for (int c = threadIdx.x; c < ncols; c += blockDim.x) hcol[c] += hs[c];
+    if (threadIdx.x == 0) {
+      double q = 0.0;
+      for (int c = 0; c < ncols; ++c) q = fma(hs[c], hs[c], q);
+      red[0] = q;
+    }
+    __syncthreads();
+    hn2 = hs[ncols] - red[0];
+    __syncthreads();
   }
-  sqp = block_sum_d(sqp, red);
-  if (threadIdx.x == 0) a.sq[b] = sqp;
-  if (!grid_barrier(a.bar, a.bar + 1, nb, a.err)) return;
-  double t = 0.0;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) t += __ldcg(a.sq + q);
-  const double s = block_sum_d(t, red);
-  // ---- new column (every block, own rows) and the Givens step (block 0)
-  const double hn = sqrt(s);
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (!(hn2 > 0.0)) hn2 = 0.0;
+  // ---- new column (every block, own rows) and the Givens step (warp 0 of block 0,
+  // while the block's other warps take its rows)
+  const double inv = hn2 > 0.0 ? 1.0 / sqrt(hn2) : 0.0;
   double* vn = a.V + (int64_t)(j + 1) * a.ld;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    const double v = w[i] * inv;
-    vn[i] = v;
-    if (a.v32 && i < a.m) a.v32[i] = (float)v;
+  __syncthreads();   // block 0: hcol is complete
+  if (b == 0 && threadIdx.x < 32) {
+    gm_finish_warp(hn2, a.st, hcol, a.H, a.ldh, a.cs, a.sn, a.g);
+    return;
   }
-  if (b == 0) gm_finish_block(s, a.st, a.H, a.ldh, a.cs, a.sn, a.g);
+  {
+    const int64_t step = (b == 0) ? blockDim.x - 32 : blockDim.x;
+    int64_t i = r0 + threadIdx.x - ((b == 0) ? 32 : 0);
+    for (; i + step < r1; i += 2 * step) {
+      double wa = w[i], wb = w[i + step];
+      gm_row_update2(V, a.ld, i, i + step, ncols, hs, wa, wb);
+      wa *= inv;
+      wb *= inv;
+      vn[i] = wa;
+      vn[i + step] = wb;
+      if (a.v32) {
+        if (i < a.m) a.v32[i] = (float)wa;
+        if (i + step < a.m) a.v32[i + step] = (float)wb;
+      }
+    }
+    for (; i < r1; i += step) {
+      const double v = gm_row_update(V, a.ld, w[i], i, ncols, hs) * inv;
+      vn[i] = v;
+      if (a.v32 && i < a.m) a.v32[i] = (float)v;
+    }
+  }
 }
 
 template <typename TAZ>
@@ -1069,10 +1233,12 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGmThreads, 0);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int nblk = num_sms;
-  if (nblk < maxc + 1) return cudaErrorInvalidConfiguration;   // one block per column of h and ||w||^2
+  // co-resident CTAs (cooperative launch): two per SM for long vectors (more loads in
+  // flight), one per SM otherwise (fewer partials to sum)
+  const int nblk = num_sms * ((occ >= 2 && len >= ((int64_t)1 << 20)) ? 2 : 1);
   GmStepArgs<TAZ> a{V, ld, len, m, w, az, st, maxc, 0, Dp, sq, hsum, H, cs, sn, g, v32, bar, err};
   a.ldh = ldh;
+  a.ldd = 2 * num_sms;   // the caller's Dp holds (maxc + 1) x 2 num_sms values
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
   cfg.blockDim = dim3(kGmThreads);

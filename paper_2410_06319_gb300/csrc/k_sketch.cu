@@ -182,11 +182,16 @@ __device__ __forceinline__ void cast_bits(uint64_t u, int k, uint32_t (&t)[3]) {
   }
 }
 
+// Bt layout: blocks of kBtBlock data rows; within a block, [plane][row][k] with
+// rows = the padded columns of [A | b] (one row per column) and k contiguous, so a
+// sketch CTA's K chunk of its column group lies in one contiguous stretch of a
+// few MB (a K-major layout with m-long rows puts every row of a stage on its
+// own page once m is in the millions).
 template <int FMT>
 __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
                                       const double* __restrict__ b, int64_t m, int64_t n,
                                       const int* __restrict__ kexp, void* __restrict__ Bt,
-                                      int64_t ldb, int64_t plane_rows) {
+                                      int64_t plane_rows, int planes) {
   __shared__ uint64_t tile[32][33];
   const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
   const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
@@ -203,52 +208,58 @@ __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t c = c0 + r, j = j0 + threadIdx.x;
-    if (c <= n && j < m) {
-      const uint64_t u = tile[threadIdx.x][r];
-      const int k = kexp[c];
-      if constexpr (FMT == FMT_F32) {
-        const double v = ldexp(__longlong_as_double((long long)u), k);
-        reinterpret_cast<float*>(Bt)[c * ldb + j] = __double2float_rn(v);
+    if (c >= plane_rows) continue;
+    // every (row, k) of the padded blocks is written: zeros past column n and row m
+    const int64_t blk = j / kBtBlock, kk = j % kBtBlock;
+    const int64_t base = (blk * planes * plane_rows + c) * kBtBlock + kk;
+    const int64_t pstride = plane_rows * kBtBlock;
+    const bool live = c <= n && j < m;
+    const uint64_t u = tile[threadIdx.x][r];
+    const int k = live ? kexp[c] : 0;
+    if constexpr (FMT == FMT_F32) {
+      const double v = ldexp(__longlong_as_double((long long)u), k);
+      reinterpret_cast<float*>(Bt)[base] = live ? __double2float_rn(v) : 0.0f;
+    } else {
+      uint32_t tt[3] = {0u, 0u, 0u};
+      if (live) cast_bits<FMT>(u, k, tt);
+      if constexpr (FMT == FMT_BF16X3) {
+        // three BF16 terms hi + lo + lo2, one plane each
+        uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
+        P[base] = (uint16_t)tt[0];
+        P[base + pstride] = (uint16_t)tt[1];
+        P[base + 2 * pstride] = (uint16_t)tt[2];
+      } else if constexpr (FMT == FMT_E4M3) {
+        reinterpret_cast<uint8_t*>(Bt)[base] = (uint8_t)tt[0];
       } else {
-        uint32_t t[3];
-        cast_bits<FMT>(u, k, t);
-        if constexpr (FMT == FMT_BF16X3) {
-          // three BF16 terms hi + lo + lo2, one plane each
-          uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
-          P[c * ldb + j] = (uint16_t)t[0];
-          P[(plane_rows + c) * ldb + j] = (uint16_t)t[1];
-          P[(2 * plane_rows + c) * ldb + j] = (uint16_t)t[2];
-        } else if constexpr (FMT == FMT_E4M3) {
-          reinterpret_cast<uint8_t*>(Bt)[c * ldb + j] = (uint8_t)t[0];
-        } else {
-          reinterpret_cast<uint16_t*>(Bt)[c * ldb + j] = (uint16_t)t[0];
-        }
+        reinterpret_cast<uint16_t*>(Bt)[base] = (uint16_t)tt[0];
       }
     }
   }
 }
 
-cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
-                                  int64_t n, const int* kexp, void* Bt, int64_t ldb,
-                                  int64_t nrows_pad, cudaStream_t st) {
+int64_t bt_blocks(int64_t m) { return (m + kBtBlock - 1) / kBtBlock; }
+
+size_t bt_bytes(int fmt, int64_t m, int64_t plane_rows) {
   const int esz = (fmt == FMT_E4M3) ? 1 : (fmt == FMT_F32 ? 4 : 2);
   const int planes = (fmt == FMT_BF16X3) ? 3 : 1;
-  if (nrows_pad > n + 1) {
-    for (int pl = 0; pl < planes; ++pl) {
-      cudaError_t e = cudaMemsetAsync(
-          static_cast<uint8_t*>(Bt) + ((size_t)pl * nrows_pad + (size_t)(n + 1)) * ldb * esz, 0,
-          (size_t)(nrows_pad - n - 1) * ldb * esz, st);
-      if (e != cudaSuccess) return e;
-    }
-  }
-  dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 1 + 31) / 32));
+  return (size_t)bt_blocks(m) * planes * plane_rows * kBtBlock * esz;
+}
+
+cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
+                                  int64_t n, const int* kexp, void* Bt, int64_t plane_rows,
+                                  cudaStream_t st) {
+  if (plane_rows < n + 1) return cudaErrorInvalidValue;
+  const int planes = (fmt == FMT_BF16X3) ? 3 : 1;
+  const int64_t gx = bt_blocks(m) * kBtBlock / 32;
+  if (gx > 2147483647LL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gx, (unsigned)((plane_rows + 31) / 32));
   dim3 block(32, 8);
   switch (fmt) {
-    case FMT_F16: cast_transpose_kernel<FMT_F16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
-    case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
-    case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
-    case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
-    case FMT_BF16X3: cast_transpose_kernel<FMT_BF16X3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, ldb, nrows_pad); break;
+    case FMT_F16: cast_transpose_kernel<FMT_F16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
+    case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
+    case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
+    case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
+    case FMT_BF16X3: cast_transpose_kernel<FMT_BF16X3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -374,11 +385,12 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
         if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
         mbar_arrive_expect_tx(full0 + 8 * st, (uint32_t)NT * b_bytes);
         const uint32_t sb = smem_u32(smem + st * stage_bytes + S_BYTES);
-        const int32_t kx = (int32_t)(k_begin + (int64_t)ks * BK);
+        const int64_t kx = k_begin + (int64_t)ks * BK;
+        const int32_t kin = (int32_t)(kx % kBtBlock), kblk = (int32_t)(kx / kBtBlock);
         for (int t = 0; t < NT; ++t)
           for (int c = 0; c < a.nsub; ++c)
-            tma_load_2d(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB), &tmB, kx,
-                        (int32_t)(t * a.rows_per_plane + ng * a.bn + c * chunk), full0 + 8 * st);
+            tma_load_3d(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB), &tmB, kin,
+                        (int32_t)(t * a.rows_per_plane + ng * a.bn + c * chunk), kblk, full0 + 8 * st);
       }
     }
   } else if (warp == 1) {
@@ -590,6 +602,17 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
     const double per_split = 4.0 * (double)ncols * (double)s;
     const int64_t max_splits = (int64_t)(kPartialBudget / per_split);
     int64_t want = (m + kBf16x3Chunk - 1) / kBf16x3Chunk;
+    // at most 25 % more splits, so that the grid fills its last wave of CTAs best
+    int64_t best = want, best_idle = -1;
+    for (int64_t w = want; w <= want + want / 4; ++w) {
+      const int64_t ctas = base * w, waves = (ctas + num_sms - 1) / num_sms;
+      const int64_t idle = waves * num_sms - ctas;
+      if (best_idle < 0 || idle < best_idle) {
+        best = w;
+        best_idle = idle;
+      }
+    }
+    want = best;
     if (want > max_splits) want = max_splits;
     if (want > 65535) want = 65535;
     if (want > splits) {
@@ -607,8 +630,8 @@ bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, S
   return true;
 }
 
-bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
-                    int box_rows, int rowb) {
+bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int box_rows,
+                    int rowb) {
   // looked up once (thread-safe static initialisation; batched solves call this
   // from several host threads)
   static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
@@ -622,11 +645,13 @@ bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int6
   }();
   if (!fn) return false;
   const int EB = (fmt == FMT_E4M3) ? 1 : 2;
-  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ldb * EB)};
-  cuuint32_t box[2] = {(cuuint32_t)(rowb / EB), (cuuint32_t)box_rows};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(tm, EB == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+  if (kBtBlock % (rowb / EB) != 0) return false;   // a stage never straddles two blocks
+  // (k within the block, row over all planes, block)
+  cuuint64_t dims[3] = {(cuuint64_t)kBtBlock, (cuuint64_t)rows, (cuuint64_t)bt_blocks(m)};
+  cuuint64_t strides[2] = {(cuuint64_t)(kBtBlock * EB), (cuuint64_t)(rows * kBtBlock * EB)};
+  cuuint32_t box[3] = {(cuuint32_t)(rowb / EB), (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(tm, EB == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
                   const_cast<void*>(Bt), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -19,12 +19,17 @@ cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int
 // Power-of-two exponents k_j (int) from the column maxima (target 2^t, t < 0: none).
 cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols, int t, int* kexp,
                               cudaStream_t st);
-// Pass 2 over A: Bt[c][j] = fl_s(2^k_c [A | b][j][c]) (K-major operand), rows c in
-// [n+1, nrows_pad) zeroed.  fmt in {F16, BF16, E4M3, F32, BF16X3}; element size
-// 2, 2, 1, 4, 2.  BF16X3 writes three planes of nrows_pad rows (hi, lo, lo2).
+// Pass 2 over A: the K-major tensor-core operand Bt: fl_s(2^k_c [A | b][j][c]) for
+// column c and data row j, stored in blocks of kBtBlock data rows, each block
+// [plane][row c < plane_rows][j % kBtBlock]; rows past n and data rows past m are
+// zero.  fmt in {F16, BF16, E4M3, F32, BF16X3}; element size 2, 2, 1, 4, 2;
+// BF16X3 has three planes (hi, lo, lo2).  plane_rows >= n + 1.
+constexpr int64_t kBtBlock = 2048;
+int64_t bt_blocks(int64_t m);
+size_t bt_bytes(int fmt, int64_t m, int64_t plane_rows);
 cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
-                                  int64_t n, const int* kexp, void* Bt, int64_t ldb,
-                                  int64_t nrows_pad, cudaStream_t st);
+                                  int64_t n, const int* kexp, void* Bt, int64_t plane_rows,
+                                  cudaStream_t st);
 
 struct SketchPlan {
   int fmt;             // FMT_F16, FMT_BF16, FMT_E4M3 (tensor cores) or FMT_F32/F64
@@ -46,9 +51,10 @@ struct SketchPlan {
 // max_kchunk > 0 caps the rows of A per split (rounded down to whole K steps).
 bool plan_sketch_tc(int fmt, int64_t s, int64_t m, int64_t ncols, int num_sms, SketchPlan* p,
                     int64_t max_kchunk = 0);
-// Encodes the TMA descriptor of the K-major operand Bt (rows x m, row stride ldb elements).
-bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int64_t ldb,
-                    int box_rows, int rowb);
+// Encodes the 3-D TMA descriptor (k within a block, row over all planes, block) of Bt
+// (`rows` = planes x plane_rows).
+bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int64_t m, int box_rows,
+                    int rowb);
 // rec == nullptr: exact mode (FP64 fallbacks resolved inside the kernel).  Otherwise
 // deferred mode: the uncertain pairs go to sketch_rec_lists(p) lists of
 // sketch_rec_cap(p) entries (counts in rec_cnt) and launch_sketch_fix corrects the
