@@ -69,7 +69,7 @@ typedef enum lsq_status {
   LSQ_E_RANK = -2,         /* R has a zero (or non-finite) diagonal entry */
   LSQ_E_BREAKDOWN = -3,    /* reserved, not returned: a Krylov breakdown ends the method
                               with its current iterate */
-  LSQ_E_NONFINITE = -4,    /* non-finite value met in a stage output */
+  LSQ_E_NONFINITE = -4,    /* a NaN or an infinity in A or b, or a non-finite stage output */
   LSQ_E_CUDA = -5,         /* a CUDA call failed (see lsq_last_cuda_error) */
   LSQ_E_TIMEOUT = -6,      /* a bounded device-side wait ran out */
   LSQ_E_NOMEM = -7,        /* workspace allocation failed */
@@ -116,6 +116,12 @@ typedef struct lsq_opts {
   int64_t sketch_kchunk;  /* tensor-core sketch: at most this many rows of A per split of the
                              m range (each split is summed in FP32, the splits in FP64);
                              0 -> the library's choice */
+  int32_t wait_limit_us;  /* limit of each grid-sync wait of the FGMRES Arnoldi step in
+                             microseconds; 0 -> 2 s */
+  int32_t expire_sync;    /* 1: the Arnoldi step's grid-sync arrival count starts past its
+                             completion value, so the first wait runs out after wait_limit_us
+                             and the call returns LSQ_E_TIMEOUT (tests the timeout path; the
+                             handle stays usable) */
 } lsq_opts;
 
 /* Diagnostics of one call. */
@@ -225,6 +231,24 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
                     int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
                     double tol, uint64_t seed, const lsq_opts* opts, double* x, double* r,
                     lsq_info* info);
+
+/*
+ * lsq_ir_step -- one refinement step of Algorithm 2 from the caller's (x, r):
+ * [f; g] = [b - r - A x; -A^T r] in u_r (F64), h = R^-T g in u_r, FGMRES on
+ * M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (Eq. 1.2; products in u_w, Arnoldi and
+ * Givens in FP64, x0 = 0, at most opts->gmres_maxit iterations, tolerance
+ * opts->gmres_tol or tol), then x += R^-1 dz and r += dr.  R is a DEVICE n x n
+ * column-major upper-triangular FP64 matrix (e.g. from lsq_qr_r); x (n) and r (m)
+ * are DEVICE FP64 vectors, read and overwritten.  info receives the FGMRES
+ * iteration count and relative residual (gmres_its[0], gmres_relres[0]) and the
+ * relative corrections (ir_dx_rel, ir_dr_rel).  Returns LSQ_OK if FGMRES met its
+ * tolerance, LSQ_NOT_CONVERGED if it stopped at its cap (x and r are updated in
+ * both cases), or an error status as lsq_lsir (x and r unspecified).
+ */
+lsq_status lsq_ir_step(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                       int64_t s, lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r,
+                       double tol, uint64_t seed, const lsq_opts* opts, const double* R, double* x,
+                       double* r, lsq_info* info);
 
 /* One problem of a batch (all pointers are device pointers owned by the caller). */
 typedef struct lsq_problem {

@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
                 ("no_graph", ctypes.c_int32), ("sketch_exact", ctypes.c_int32),
                 ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
                 ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p),
-                ("sketch_kchunk", ctypes.c_int64)]
+                ("sketch_kchunk", ctypes.c_int64), ("wait_limit_us", ctypes.c_int32),
+                ("expire_sync", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -92,13 +93,14 @@ lib.lsq_qr_r.argtypes = _TUPLE + [_P, _P]
 lib.lsq_lsqr.argtypes = _TUPLE + [_P, ctypes.POINTER(Info)]
 lib.lsq_lsir.argtypes = _TUPLE + [_P, _P, ctypes.POINTER(Info)]
 lib.lsq_lsir_host.argtypes = _TUPLE + [_P, _P, ctypes.POINTER(Info)]
+lib.lsq_ir_step.argtypes = _TUPLE + [_P, _P, _P, ctypes.POINTER(Info)]
 lib.lsq_omega.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, ctypes.c_uint64, _P]
 lib.lsq_lsir_batched.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
 lib.lsq_qr_r_noalloc.argtypes = [_P, _I64, _I64, ctypes.c_int, _P, _P, _P]
 lib.lsq_probe_fma_rate.argtypes = [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
-for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir", "lsq_lsir_host",
+for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir", "lsq_lsir_host", "lsq_ir_step",
            "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc", "lsq_probe_fma_rate"):
     getattr(lib, _f).restype = ctypes.c_int
 
@@ -211,6 +213,14 @@ def lsq_lsir(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, x, r, info=N
     args, _o = _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts)
     info = info if info is not None else Info()
     st = _check(h, lib.lsq_lsir(*args, _ptr(x), _ptr(r), ctypes.byref(info)), "lsq_lsir")
+    return st, info
+
+
+def lsq_ir_step(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, R, x, r, info=None):
+    """One refinement step of Algorithm 2 from (x, r), both overwritten (device tensors)."""
+    args, _o = _tuple(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts)
+    info = info if info is not None else Info()
+    st = _check(h, lib.lsq_ir_step(*args, _ptr(R), _ptr(x), _ptr(r), ctypes.byref(info)), "lsq_ir_step")
     return st, info
 
 

@@ -15,6 +15,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "common.cuh"
 #include "gauss.cuh"
 #include "iter.h"
 #include "kernels.h"
@@ -254,6 +255,8 @@ Ctx make_ctx(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t
   return c;
 }
 
+// Reads the handle's device error word; a recorded error is cleared and thrown
+// (a NaN or infinity in the input: LSQ_E_NONFINITE; an expired wait: LSQ_E_TIMEOUT).
 void check_dev_error(lsq_handle* h) {
   int e = 0;
   CK(cudaMemcpyAsync(h->h_pinned, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -261,7 +264,7 @@ void check_dev_error(lsq_handle* h) {
   std::memcpy(&e, h->h_pinned, sizeof(int));
   if (e != 0) {
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-    throw StatusFail{LSQ_E_TIMEOUT};
+    throw StatusFail{e == DEV_NONFINITE ? LSQ_E_NONFINITE : LSQ_E_TIMEOUT};
   }
 }
 
@@ -341,7 +344,7 @@ float* stage_cast(Ctx& c) {
   auto* cmax = static_cast<unsigned long long*>(ws(c.h, "cmax", (c.n + 1) * 8, true));
   float* a32 = nullptr;
   if (c.uw == LSQ_F32) a32 = static_cast<float*>(ws(c.h, "a32", (size_t)c.m * c.lda32 * 4));
-  L(launch_colmax_a32(c.A, c.lda, c.b, c.m, c.n, cmax, a32, c.lda32, c.st));
+  L(launch_colmax_a32(c.A, c.lda, c.b, c.m, c.n, cmax, a32, c.lda32, c.h->d_err, c.st));
   return a32;
 }
 
@@ -590,6 +593,14 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   GmState* gst = static_cast<GmState*>(ws(c.h, "gm_state", sizeof(GmState)));
   unsigned* gbar = static_cast<unsigned*>(ws(c.h, "gm_bar", 64));
   CK(cudaMemsetAsync(gbar, 0, 64, c.st));
+  if (c.o.expire_sync) {
+    // the arrival count starts where no arrival completes the Arnoldi step's grid sync:
+    // its bounded waits run out (a test of the timeout path)
+    const unsigned preset = 1u << 30;
+    std::memcpy(c.h->h_pinned + 3072, &preset, sizeof(preset));
+    CK(cudaMemcpyAsync(gbar, c.h->h_pinned + 3072, sizeof(preset), cudaMemcpyHostToDevice, c.st));
+  }
+  const uint64_t wait_ns = c.o.wait_limit_us > 0 ? (uint64_t)c.o.wait_limit_us * 1000ull : 0ull;
   GmState hs{};
   hs.tol = tol;
   hs.maxit = maxit;
@@ -622,7 +633,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
       {
         KernTimer kt(c.h, K_ARNOLDI, c.o.timing);
         L(launch_gm_step<TOP>(V, ld, wv, ld, m, az, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, v32, gbar,
-                              c.h->d_err, c.h->num_sms, c.st));
+                              c.h->d_err, c.h->num_sms, c.st, wait_ns));
       }
     }
   };
@@ -631,7 +642,8 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
           ? nullptr
           : get_graph(c,
                              graph_key(sizeof(TOP) == 4 ? "fgm32" : "fgm64",
-                                       {PV(Aop), ldop, m, n, maxit, PV(V), PV(Zb), PV(wv), PV(P), PV(az), PV(v32),
+                                       {PV(Aop), ldop, m, n, maxit, (int64_t)wait_ns, PV(V), PV(Zb), PV(wv), PV(P),
+                                        PV(az), PV(v32),
                                         PV(sb), PV(H), PV(cs), PV(sn), PV(g), PV(hh), PV(Dp), PV(sqp),
                                         PV(gst), PV(gbar), PV(tri.R), PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk,
                                         c.nblk2}),
@@ -651,6 +663,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
     j = out.j;
     if (out.done || j >= maxit) break;
   }
+  check_dev_error(c.h);   // an expired wait ends the solve here (its iterate is not used)
   StageTimer tu(c.h, ST_UPDATE);
   L(launch_gm_solve(gst, H, ldh, g, y, c.st));
   L(launch_gm_apply<double>(V, ld, m, gst, y, r, p4, p4 + c.nblk2, c.nblk2, c.st));
@@ -825,6 +838,7 @@ Front run_front(Ctx& c, double* x, lsq_info* info) {
     if (c.o.x0_in) CK(cudaMemcpyAsync(fr.x0, c.o.x0_in, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
   }
   const double kap = read_scalar(c, fr.rc.kappa);
+  check_dev_error(c.h);   // a NaN or an infinity in A or b (column-max pass)
   info->kappa_R_est = kap;
   if (!(kap < INFINITY)) throw StatusFail{LSQ_E_RANK};
   if (kap * unit_roundoff(c.us) >= 1.0) info->flags |= LSQ_WARN_COND;
@@ -838,6 +852,21 @@ Front run_front(Ctx& c, double* x, lsq_info* info) {
   info->lsqr_normar = fr.ls.normar;
   info->lsqr_normA = fr.ls.normA;
   return fr;
+}
+
+// FP64 products stream A in 16-byte pieces: an odd row stride (or an unaligned A)
+// gets an even-stride, zero-padded copy first
+const double* a64_rows(Ctx& c, int64_t* ld) {
+  if ((reinterpret_cast<uintptr_t>(c.A) & 15) == 0 && c.lda % 2 == 0) {
+    *ld = c.lda;
+    return c.A;
+  }
+  const int64_t lp = round_up(c.n, 2);
+  double* Ap = static_cast<double*>(ws(c.h, "A64p", (size_t)c.m * lp * 8));
+  CK(cudaMemsetAsync(Ap, 0, (size_t)c.m * lp * 8, c.st));
+  CK(cudaMemcpy2DAsync(Ap, lp * 8, c.A, c.lda * 8, c.n * 8, c.m, cudaMemcpyDeviceToDevice, c.st));
+  *ld = lp;
+  return Ap;
 }
 
 }  // namespace
@@ -1025,18 +1054,7 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
     // FP64 products stream A in 16-byte pieces: an odd row stride (or an unaligned A)
     // gets an even-stride, zero-padded copy first
-    auto a64 = [&](int64_t* ld) -> const double* {
-      if ((reinterpret_cast<uintptr_t>(c.A) & 15) == 0 && c.lda % 2 == 0) {
-        *ld = c.lda;
-        return c.A;
-      }
-      const int64_t lp = round_up(c.n, 2);
-      double* Ap = static_cast<double*>(ws(c.h, "A64p", (size_t)c.m * lp * 8));
-      CK(cudaMemsetAsync(Ap, 0, (size_t)c.m * lp * 8, c.st));
-      CK(cudaMemcpy2DAsync(Ap, lp * 8, c.A, c.lda * 8, c.n * 8, c.m, cudaMemcpyDeviceToDevice, c.st));
-      *ld = lp;
-      return Ap;
-    };
+    auto a64 = [&](int64_t* ld) -> const double* { return a64_rows(c, ld); };
     bool conv;
     if (c.uw == LSQ_F32) {
       conv = stage_refine<float>(c, fr.a32, c.lda32, fr.rc, x, rr, inf);
@@ -1058,6 +1076,37 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     }
     inf->ir_converged = conv ? 1 : 0;
     return conv ? LSQ_OK : LSQ_NOT_CONVERGED;
+  });
+}
+
+lsq_status lsq_ir_step(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, int64_t s,
+                       lsq_prec u_s, lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol, uint64_t seed,
+                       const lsq_opts* opts, const double* R, double* x, double* r, lsq_info* info) {
+  Ctx c = make_ctx(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts);
+  lsq_status v = validate(c, true);
+  if (v != LSQ_OK) return v;
+  if (!R || !x || !r) return LSQ_E_INVAL;
+  c.o.ir_maxit = 1;
+  lsq_info local;
+  lsq_info* inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  return run_guarded(h, inf, [&]() {
+    StageTimer tt(c.h, ST_TOTAL);
+    float* a32 = stage_cast(c);
+    RCopies rc = stage_prepare_r(c, R);
+    const double kap = read_scalar(c, rc.kappa);
+    check_dev_error(c.h);   // a NaN or an infinity in A or b
+    inf->kappa_R_est = kap;
+    if (!(kap < INFINITY)) throw StatusFail{LSQ_E_RANK};
+    if (c.uw == LSQ_F32) {
+      stage_refine<float>(c, a32, c.lda32, rc, x, r, inf);
+    } else {
+      int64_t ldp;
+      const double* Ap = a64_rows(c, &ldp);
+      stage_refine<double>(c, Ap, ldp, rc, x, r, inf);
+    }
+    const double gtol = c.o.gmres_tol > 0 ? c.o.gmres_tol : c.tol;
+    return inf->gmres_relres[0] <= gtol ? LSQ_OK : LSQ_NOT_CONVERGED;
   });
 }
 

@@ -14,6 +14,7 @@ enum DevErr : int {
   DEV_TIMEOUT_DONE = 3,    // sketch: epilogue waited too long for the accumulator
   DEV_TIMEOUT_GRID = 4,    // grid-wide barrier ran out
   DEV_BAD_ARG = 5,
+  DEV_NONFINITE = 6,       // the column-max pass met a NaN or an infinity in A or b
 };
 
 // Wall-clock limit of every device-side wait (nanoseconds).

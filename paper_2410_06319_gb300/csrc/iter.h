@@ -56,11 +56,13 @@ cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* 
 // twice-is-enough second pass, Givens step, new column; blocks synchronised by a bounded
 // last-arrival reduction on bar[0..1], which must be zero before the first launch; each
 // launch leaves it reusable).  Dp holds (maxc + 1) x 2 num_sms doubles; maxc <= 128.
+// Each sync waits at most wait_ns (0: the library's limit); a wait that runs out records
+// DEV_TIMEOUT_GRID in *err and sets st->done, so the rest of the batch is skipped.
 template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
-                           int num_sms, cudaStream_t s);
+                           int num_sms, cudaStream_t s, uint64_t wait_ns = 0);
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
                             cudaStream_t s);
 template <typename TB>

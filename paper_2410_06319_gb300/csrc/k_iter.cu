@@ -938,6 +938,7 @@ struct GmStepArgs {
   unsigned* bar;  // [0]: arrivals, [1]: generation
   int* err;
   int ldd;        // leading dimension of Dp (>= the grid size)
+  uint64_t wait_ns;   // limit of each grid-sync wait
 };
 
 // Sums of eight values over a warp by a reduce-scatter butterfly: at each exchange a
@@ -1025,7 +1026,8 @@ __device__ __forceinline__ void gm_partials(const double* __restrict__ V, int64_
 // block order) into hsum and releases the others; every CTA then copies hsum into hs.
 // Returns false if the wait ran out.
 __device__ __forceinline__ bool gm_sync_sums(double* Dp, int ldd, double* hsum, int cols, unsigned* cnt,
-                                             unsigned* gen, int* err, double* hs, int* s_flag) {
+                                             unsigned* gen, int* err, uint64_t wait_ns, double* hs,
+                                             int* s_flag) {
   const unsigned nb = gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1065,7 +1067,7 @@ __device__ __forceinline__ bool gm_sync_sums(double* Dp, int ldd, double* hsum, 
     const unsigned g = (unsigned)s_flag[1];
     const uint64_t t0 = globaltimer_ns();
     while (*vgen == g) {
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > wait_ns) {
         set_error(err, DEV_TIMEOUT_GRID);
         ok = 0;
         break;
@@ -1143,7 +1145,10 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs
   }
   // ---- first pass: h and ||w||^2
   gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red);
-  if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, hs, s_flag)) return;
+  if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, a.wait_ns, hs, s_flag)) {
+    if (threadIdx.x == 0) a.st->done = 1;   // later launches of the batch skip; the host reads err
+    return;
+  }
   const double wn2 = hs[ncols];
   if (threadIdx.x == 0) {   // ||h||^2 in the same order in every CTA
     double q = 0.0;
@@ -1176,7 +1181,10 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs
     for (; i < r1; i += step) w[i] = gm_row_update(V, a.ld, w[i], i, ncols, hs);
     __syncthreads();   // this CTA's rows of w1 are final for the second pass
     gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red);
-    if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, hs, s_flag)) return;
+    if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, a.wait_ns, hs, s_flag)) {
+    if (threadIdx.x == 0) a.st->done = 1;   // later launches of the batch skip; the host reads err
+    return;
+  }
     if (b == 0)
       for (int c = threadIdx.x; c < ncols; c += blockDim.x) hcol[c] += hs[c];
     if (threadIdx.x == 0) {
@@ -1225,7 +1233,7 @@ template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
-                           int num_sms, cudaStream_t s) {
+                           int num_sms, cudaStream_t s, uint64_t wait_ns) {
   static_assert(sizeof(GmStepArgs<TAZ>) < 4096, "kernel parameter block");
   if (maxc > 128) return cudaErrorInvalidValue;
   auto kern = gm_step_kernel<TAZ>;
@@ -1239,6 +1247,7 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
   GmStepArgs<TAZ> a{V, ld, len, m, w, az, st, maxc, 0, Dp, sq, hsum, H, cs, sn, g, v32, bar, err};
   a.ldh = ldh;
   a.ldd = 2 * num_sms;   // the caller's Dp holds (maxc + 1) x 2 num_sms values
+  a.wait_ns = wait_ns > 0 ? wait_ns : kWaitLimitNs;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
   cfg.blockDim = dim3(kGmThreads);
@@ -1252,10 +1261,11 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
 }
 template cudaError_t launch_gm_step<float>(double*, int64_t, double*, int64_t, int64_t, const float*, GmState*,
                                            int, double*, double*, double*, double*, int, double*, double*,
-                                           double*, float*, unsigned*, int*, int, cudaStream_t);
+                                           double*, float*, unsigned*, int*, int, cudaStream_t, uint64_t);
 template cudaError_t launch_gm_step<double>(double*, int64_t, double*, int64_t, int64_t, const double*,
                                             GmState*, int, double*, double*, double*, double*, int, double*,
-                                            double*, double*, float*, unsigned*, int*, int, cudaStream_t);
+                                            double*, double*, float*, unsigned*, int*, int, cudaStream_t,
+                                            uint64_t);
 
 // y = H[:k,:k]^-1 g[:k]  (k = st->j): one warp, column-oriented back substitution
 __global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, const double* g, double* y) {

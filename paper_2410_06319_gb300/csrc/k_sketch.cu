@@ -90,7 +90,7 @@ __device__ __forceinline__ float f64bits_to_f32(uint64_t u) {
 __global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
                                   const double* __restrict__ b, int64_t m, int64_t n,
                                   unsigned long long* cmax, float* __restrict__ a32, int64_t lda32,
-                                  int64_t rows_per_block) {
+                                  int64_t rows_per_block, int* err) {
   const int64_t r0 = blockIdx.x * rows_per_block;
   const int64_t r1 = min(m, r0 + rows_per_block);
   const int64_t cend = a32 ? max(n + 1, lda32) : n + 1;
@@ -116,15 +116,17 @@ __global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
       for (int64_t i = r0; i < r1; ++i) a32[i * lda32 + c] = 0.0f;
     }
     if (c <= n && mx > 0) atomicMax(cmax + c, (unsigned long long)mx);
+    // |v| bits at or above those of +infinity: an infinity or a NaN in the column
+    if (c <= n && mx >= 0x7FF0000000000000ull) set_error(err, DEV_NONFINITE);
   }
 }
 
 cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int64_t m, int64_t n,
-                              unsigned long long* cmax_bits, float* a32, int64_t lda32,
+                              unsigned long long* cmax_bits, float* a32, int64_t lda32, int* err,
                               cudaStream_t st) {
   const int64_t rows_per_block = 64;
   const unsigned blocks = (unsigned)((m + rows_per_block - 1) / rows_per_block);
-  colmax_a32_kernel<<<blocks, 256, 0, st>>>(A, lda, b, m, n, cmax_bits, a32, lda32, rows_per_block);
+  colmax_a32_kernel<<<blocks, 256, 0, st>>>(A, lda, b, m, n, cmax_bits, a32, lda32, rows_per_block, err);
   return cudaGetLastError();
 }
 

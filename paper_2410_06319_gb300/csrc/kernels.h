@@ -12,9 +12,10 @@ cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t 
                          cudaStream_t st);
 
 // Pass 1 over A: column maxima of [A | b] (as FP64 bit patterns, atomicMax) and,
-// when a32 != nullptr, the FP32 working copy (row stride lda32, zero padded).
+// when a32 != nullptr, the FP32 working copy (row stride lda32, zero padded).  A NaN
+// or an infinity in A or b records DEV_NONFINITE in *err.
 cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int64_t m, int64_t n,
-                              unsigned long long* cmax_bits, float* a32, int64_t lda32,
+                              unsigned long long* cmax_bits, float* a32, int64_t lda32, int* err,
                               cudaStream_t st);
 // Power-of-two exponents k_j (int) from the column maxima (target 2^t, t < 0: none).
 cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols, int t, int* kexp,
