@@ -151,11 +151,17 @@ class Clocks:
         return out
 
 
+#: committed ncu summaries with the DRAM traffic of a kernel (at n = 1000, smaller m)
+TRAFFIC_PROFILES = {"fgmres_pass": "pass_bulk_fgmres_m200000_n1000.md"}
+
+
 def measured_traffic(kernel, m):
     """DRAM bytes per launch (read + write) of `kernel` at m rows, from its committed
     ncu summary (captured on a smaller m and scaled by the rows, the unit the pass
     streams), or None if there is none or the kernel's source changed since."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_n1000.md")
+    if kernel not in TRAFFIC_PROFILES:
+        return None
+    path = os.path.join(ROOT, "profiles", TRAFFIC_PROFILES[kernel])
     try:
         text = open(path).read()
         tb = float(re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M).group(1))
@@ -653,13 +659,70 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- single cases for profilers
+CASES = ("lsir_m4e6", "fgmres_pass_m2e5_n1000", "arnoldi_m1e6_n1000", "sketch_m2e5_n1000")
+
+
+def run_case(name):
+    """One untimed call of a small named workload (for ncu captures); prints one status line.
+
+    lsir_m4e6: one lsq_lsir of the bench workload.  fgmres_pass_m2e5_n1000: one
+    refinement step (six FGMRES iterations, CUDA graphs off) on a 200000 x 1000
+    Gaussian A.  arnoldi_m1e6_n1000: one refinement step of up to 40 FGMRES
+    iterations on a 1e6 x 1000, kappa = 1e7 problem.  sketch_m2e5_n1000: one
+    lsq_sketch (s = 4000, BF16X3) of a 200000 x 1000 Gaussian A.
+    """
+    import torch
+    import paper_2410_06319_gb300 as lsq
+    from lsq_synth.device import DeviceRandsvd
+    torch.manual_seed(0)
+    h = lsq.Handle()
+
+    def randn(m, n):
+        return (torch.randn(m, n, dtype=torch.float64, device="cuda"),
+                torch.randn(m, dtype=torch.float64, device="cuda"))
+
+    if name == "lsir_m4e6" or name == "arnoldi_m1e6_n1000":
+        m = WL["m"] if name == "lsir_m4e6" else 1_000_000
+        n, s = WL["n"], WL["s"]
+        gen = DeviceRandsvd(m, n, seed=WL["data_seed"])
+        A, b, _ = gen.problem(WL["kappa"], WL["rho"])
+        gen.release()
+        opts = None if name == "lsir_m4e6" else {"no_graph": 1, "ir_maxit": 1, "gmres_maxit": 40}
+    elif name == "fgmres_pass_m2e5_n1000":
+        m, n, s = 200_000, 1000, 4000
+        A, b = randn(m, n)
+        opts = {"no_graph": 1, "ir_maxit": 1, "gmres_maxit": 6, "lsqr_maxit": 3}
+    else:
+        m, n, s = 200_000, 1000, 4000
+        A, b = randn(m, n)
+        Y = torch.zeros(s * (n + 1), dtype=torch.float64, device="cuda")
+        st = lsq.lsq_sketch(h, A, b, m, n, s, "bf16x3", "f64", "f32", "f64", 1e-6, 0, None, Y)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "status": st}), flush=True)
+        return
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    st, info = lsq.lsq_lsir(h, A, b, m, n, s, WL["u_s"], WL["u_p"], WL["u_w"], WL["u_r"], WL["tol"],
+                            WL["seed"], opts, x, r)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "status": st, "lsqr_its": info.lsqr_its, "ir_its": info.ir_its,
+                      "fgmres_its": info.gmres_its_total, "launches": info.gpu_launches}), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default=None, choices=CASES,
+                    help="run one small named workload once (no timing; for profilers)")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

@@ -8,6 +8,11 @@ device in FP64 with torch's seeded generator (a different stream than the
 host generator's: same law, different draws).  U is kept so that several
 kappa values share one draw; the factors sigma and V stay available, which
 gives exact properties such as sigma(A R^-1) = sigma(Sigma V^T R^-1).
+
+Only products and elementwise work run on the device: the n x n factorisations
+(Cholesky of the Gram matrix, QR for V) run on the host with numpy, so the
+generator needs no device linear-algebra library (torch loads its own lazily,
+which fails under some profilers).
 """
 import numpy as np
 
@@ -21,12 +26,14 @@ class DeviceRandsvd:
         g.manual_seed(int(seed))
         Q = torch.randn(self.m, self.n, generator=g, device=device, dtype=torch.float64)
         for _ in range(2):                                   # CholeskyQR2: Q <- Q C^-T
-            C = torch.linalg.cholesky(Q.T @ Q)
-            Q = torch.linalg.solve_triangular(C.T, Q, upper=True, left=False)
+            C = np.linalg.cholesky((Q.T @ Q).cpu().numpy())  # Q^T Q = C C^T (C well conditioned)
+            CiT = torch.from_numpy(np.ascontiguousarray(np.linalg.inv(C).T)).to(device)
+            Q = Q @ CiT
         self.U = Q
-        Z = torch.randn(self.n, self.n, generator=g, device=device, dtype=torch.float64)
-        V, Rz = torch.linalg.qr(Z)
-        self.V = V * torch.where(torch.diagonal(Rz) < 0, -1.0, 1.0)[None, :]
+        Z = torch.randn(self.n, self.n, generator=g, device=device, dtype=torch.float64).cpu().numpy()
+        V, Rz = np.linalg.qr(Z)
+        V = V * np.where(np.diag(Rz) < 0, -1.0, 1.0)[None, :]
+        self.V = torch.from_numpy(np.ascontiguousarray(V)).to(device)
         self.x_true = torch.randn(self.n, generator=g, device=device, dtype=torch.float64)
         gv = torch.randn(self.m, generator=g, device=device, dtype=torch.float64)
         for _ in range(2):

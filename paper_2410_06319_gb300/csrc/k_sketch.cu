@@ -967,6 +967,11 @@ cudaError_t launch_sketch_cc(int fmt, const double* A, int64_t lda, const double
 }
 
 // ============================================================ split reduce
+// FP64 partials: an FP64 sum.  FP32 partials (the tensor-core splits): Knuth's TwoSum
+// in FP32, an error-free transformation of each addition, with the rounding errors
+// collected in a second FP32 word; hi + lo carries the sum of the splits to about
+// 2^-48 relative (double-float), on the FP32 pipe instead of GB300's narrow FP64 pipe
+// (the sum over thousands of 2048-row splits at m = 4e6 is 8e9 additions).
 template <typename TP>
 __global__ void sketch_reduce_kernel(const TP* __restrict__ partial, int splits, int64_t ncols,
                                      int64_t s, int64_t s_pad, const int* __restrict__ kexp,
@@ -974,8 +979,24 @@ __global__ void sketch_reduce_kernel(const TP* __restrict__ partial, int splits,
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = blockIdx.y;
   if (i >= s) return;
-  double acc = 0.0;
-  for (int sp = 0; sp < splits; ++sp) acc += (double)partial[((int64_t)sp * ncols + c) * s_pad + i];
+  double acc;
+  if constexpr (sizeof(TP) == 8) {
+    acc = 0.0;
+    for (int sp = 0; sp < splits; ++sp) acc += (double)partial[((int64_t)sp * ncols + c) * s_pad + i];
+  } else {
+    float hi = 0.0f, lo = 0.0f;
+    const TP* p = partial + c * s_pad + i;
+    const int64_t stride = ncols * s_pad;
+    for (int sp = 0; sp < splits; ++sp) {
+      const float x = __ldcs(p + (int64_t)sp * stride);
+      const float t = __fadd_rn(hi, x);
+      const float xb = __fsub_rn(t, hi);
+      const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, xb)), __fsub_rn(x, xb));
+      hi = t;
+      lo = __fadd_rn(lo, err);
+    }
+    acc = (double)hi + (double)lo;
+  }
   const int k = kexp ? kexp[c] : 0;
   Y[c * s + i] = ldexp(acc * inv_sqrt_s, -k);
 }

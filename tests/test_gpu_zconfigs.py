@@ -10,8 +10,11 @@
   below span [0.03, 3] kappa u_s.
 * m = 4e6, n = 1000, s = 4n, kappa = 1e7, ||r_perp|| / ||b|| = 1e-6: BF16
   sketch (broken there, kappa u_s = 3.9e4) and the three-term BF16 split
-  (single precision), FP64 QR.  Here the FP32 accumulation of the tensor
-  cores, not the cast, bounds the split sketch.
+  (single precision), FP64 QR; with the split sketch summed in FP32 over
+  2048-row splits, kappa(A R^-1) stays near its good-sketch value, and the full
+  Algorithm 2 (FP32 LSQR, FGMRES-LSIR with FP64 residuals) reaches forward errors
+  within 4u in x and r, measured against the generator's x and r_perp (they differ
+  from the stored-data solution by about 1e-9 relative at this kappa and rho).
 
 Checked against the oracle on sampled outputs (rows of Omega from its own
 Philox and Box-Muller, sampled columns of A) and against properties that hold
@@ -142,14 +145,22 @@ def test_m4e6_n1000_kappa1e7_bf16_and_split_sketch(lsq, big_handle):
     # proportion to kappa u_s (Fig. 3a)
     ku = kappa * U_S["bf16"]
     assert 0.03 * ku <= kars["bf16"] <= 3 * ku
-    # The split sketch casts A to single precision, but the tensor cores add the
-    # products in FP32: the product term of Sec. 3.2's bound on the sketching error
-    # (m^1/2 gamma_m) with FP32 for the accumulation, about 2^-24 sqrt(k/2) relative
-    # per entry for split-K chunks of k rows of A (a random walk of roundings),
-    # which kappa turns into kappa(A R^-1) of the order of kappa 2^-24 sqrt(k/2):
-    # far below BF16's, above the good-sketch value at this kappa and m
-    assert 0.9 * kappa_mp(n, s) <= kars["bf16x3"] <= min(kars["bf16"] / 5,
-                                                           2 * kappa * 2.0 ** -24 * np.sqrt(m / 2))
-    del A, b, rperp
+    # The split sketch casts A to single precision; the tensor cores add the products in
+    # FP32, whose error (the product term of Sec. 3.2's bound with FP32 for the sum)
+    # grows with the rows summed in one split: with 2048-row splits summed in
+    # double-float kappa(A R^-1) stays within 30 % of the good-sketch value
+    # (8e5-row splits gave 378 here)
+    assert 0.9 * kappa_mp(n, s) <= kars["bf16x3"] <= 1.3 * kappa_mp(n, s)
+    # Algorithm 2 end to end on this configuration
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    st, info = lsq.lsq_lsir(big_handle, A, b, m, n, s, "bf16x3", "f64", "f32", "f64", 1e-6, 0, None, x, r)
+    xt = gen.x_true
+    fx = (torch.linalg.norm(x - xt) / torch.linalg.norm(xt)).item()
+    fr = (torch.linalg.norm(r - rperp) / torch.linalg.norm(rperp)).item()
+    print("LSIR m=4e6: status", st, "its", info.lsqr_its, info.ir_its, info.gmres_its_total, "fe", fx, fr)
+    assert st == 0 and info.ir_converged == 1 and info.escalated == 0
+    assert fx <= 4 * 2.0 ** -24 and fr <= 4 * 2.0 ** -24, (fx, fr)
+    del A, b, rperp, x, r
     gen.release()
     torch.cuda.empty_cache()
