@@ -332,7 +332,9 @@ lsq_status lsq_omega(lsq_handle* h, int64_t s, int64_t j0, int64_t cols, lsq_pre
  *      synchronises cuda_stream once to read the scratch's error word).
  * Set-up: the first call on a device, with that device current, looks up the
  *      address of the device's scratch array (cudaGetSymbolAddress); make that
- *      first call before any stream capture begins on the device.
+ *      first call before any stream capture begins on the device.  The address
+ *      is kept for the life of the process: resetting the device
+ *      (cudaDeviceReset) after that first call is not supported.
  * Concurrency: all calls on one device share one scratch array.  Calls that
  *      overlap in time on the same device (from several host threads, or on
  *      several streams) race on it and give wrong results; serialise them.
