@@ -54,6 +54,12 @@ extern "C" {
  * three BF16 terms hi + lo + lo2 (24 significant bits), all products
  * accumulated in FP32; its unit roundoff is taken as 2^-24. */
 typedef enum lsq_prec {
+  LSQ_AUTO = -1,   /* sketch precision only (lsq_lsqr, lsq_lsir and their host/batched forms):
+                      the cheapest of BF16, BF16X3, F64 whose sketch gives kappa_est(R) u_s < 1/4
+                      (Sec. 3.4: u_s kappa(A) < 1 with kappa(A) estimated from R; kappa_est is the
+                      diagonal ratio, a lower bound; a sketch in u_s of an A with kappa(A) > 1/u_s
+                      is regularised, its R saturates at a few times 1/u_s and fails the test);
+                      info->us_used and info->sketches report the choice */
   LSQ_F64 = 0,
   LSQ_F32 = 1,
   LSQ_F16 = 2,
@@ -152,6 +158,8 @@ typedef struct lsq_info {
                                entry spare */
   int64_t kern_launches[8]; /* number of launches behind each kern_ms entry */
   int64_t arnoldi_second_passes; /* FGMRES Arnoldi steps that ran the second Gram-Schmidt pass */
+  int32_t us_used;          /* the sketch precision used (the choice of LSQ_AUTO) */
+  int32_t sketches;         /* sketches taken (more than one when LSQ_AUTO moved up its ladder) */
 } lsq_info;
 
 /* sizeof(lsq_opts) for which = 0, sizeof(lsq_info) for which = 1, else 0: lets

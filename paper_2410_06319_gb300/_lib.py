@@ -19,7 +19,7 @@ if not os.path.exists(library_path()):
 
 lib = ctypes.CDLL(library_path())
 
-PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "bf16x3": 5}
+PREC = {"auto": -1, "f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "bf16x3": 5}
 STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RANK",
           -3: "LSQ_E_BREAKDOWN", -4: "LSQ_E_NONFINITE", -5: "LSQ_E_CUDA", -6: "LSQ_E_TIMEOUT",
           -7: "LSQ_E_NOMEM", -8: "LSQ_E_UNSUPPORTED", -9: "LSQ_E_SIZE"}
@@ -55,7 +55,8 @@ class Info(ctypes.Structure):
                 ("ir_dx_hist", ctypes.c_double * 32), ("ir_dr_hist", ctypes.c_double * 32),
                 ("gmres_relres", ctypes.c_double * 32),
                 ("kern_ms", ctypes.c_double * 8), ("kern_launches", ctypes.c_int64 * 8),
-                ("arnoldi_second_passes", ctypes.c_int64)]
+                ("arnoldi_second_passes", ctypes.c_int64), ("us_used", ctypes.c_int32),
+                ("sketches", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

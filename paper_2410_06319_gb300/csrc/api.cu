@@ -216,7 +216,7 @@ lsq_status validate(const Ctx& c, bool need_b) {
   if (c.m > ((int64_t)1 << 36)) return LSQ_E_INVAL;
   if (c.lda < c.n) return LSQ_E_INVAL;
   if (!(c.tol > 0.0) || !std::isfinite(c.tol)) return LSQ_E_INVAL;
-  if (fmt_of(c.us) < 0) return LSQ_E_INVAL;
+  if (fmt_of(c.us) < 0 && c.us != LSQ_AUTO) return LSQ_E_INVAL;
   if (c.up != LSQ_F32 && c.up != LSQ_F64) return LSQ_E_INVAL;
   if (c.uw != LSQ_F32 && c.uw != LSQ_F64) return LSQ_E_INVAL;
   if (c.ur != LSQ_F64) return LSQ_E_INVAL;
@@ -826,22 +826,44 @@ Front run_front(Ctx& c, double* x, lsq_info* info) {
     fr.rc = stage_prepare_r(c, R);
     if (c.o.x0_in) CK(cudaMemcpyAsync(fr.x0, c.o.x0_in, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
     else CK(cudaMemsetAsync(fr.x0, 0, c.n * 8, c.st));
+  } else if (c.us == LSQ_AUTO && !c.o.Y_in) {
+    // Sec. 3.4 / Sec. 6: choose u_s with kappa(A) u_s < 1.  kappa(A) is estimated by
+    // kappa_est(R) = max|r_ii| / min|r_ii| of the sketch just taken (a lower bound,
+    // 3 to 30 times below kappa(R) on geometric spectra); a sketch in u_s of an A with
+    // kappa(A) > 1/u_s is regularised and its R saturates at a few times 1/u_s, where
+    // kappa_est u_s came out 1 to 3.  The test kappa_est u_s < 1/4 accepts the good
+    // regime with that margin and rejects the saturated one.  Ladder: BF16, the
+    // three-term BF16 split (single), FP64.
+    double* Yw = static_cast<double*>(ws(c.h, "Y", (size_t)c.s * (c.n + 1) * 8));
+    R = static_cast<double*>(ws(c.h, "R", (size_t)c.n * c.n * 8));
+    for (const lsq_prec f : {LSQ_BF16, LSQ_BF16X3, LSQ_F64}) {
+      c.us = f;
+      info->sketches += 1;
+      stage_sketch(c, Yw);
+      stage_qr(c, Yw, R, fr.x0, &fr.rc);
+      const double k = read_scalar(c, fr.rc.kappa);
+      check_dev_error(c.h);
+      if (!(k < INFINITY) || k * unit_roundoff(f) < 0.25) break;
+    }
+    if (c.o.x0_in) CK(cudaMemcpyAsync(fr.x0, c.o.x0_in, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
   } else {
     const double* Y = c.o.Y_in;
     if (!Y) {
       double* Yw = static_cast<double*>(ws(c.h, "Y", (size_t)c.s * (c.n + 1) * 8));
       stage_sketch(c, Yw);
       Y = Yw;
+      info->sketches += 1;
     }
     R = static_cast<double*>(ws(c.h, "R", (size_t)c.n * c.n * 8));
     stage_qr(c, Y, R, fr.x0, &fr.rc);
     if (c.o.x0_in) CK(cudaMemcpyAsync(fr.x0, c.o.x0_in, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
   }
+  info->us_used = (int32_t)c.us;
   const double kap = read_scalar(c, fr.rc.kappa);
   check_dev_error(c.h);   // a NaN or an infinity in A or b (column-max pass)
   info->kappa_R_est = kap;
   if (!(kap < INFINITY)) throw StatusFail{LSQ_E_RANK};
-  if (kap * unit_roundoff(c.us) >= 1.0) info->flags |= LSQ_WARN_COND;
+  if (c.us != LSQ_AUTO && kap * unit_roundoff(c.us) >= 1.0) info->flags |= LSQ_WARN_COND;
   if (c.uw == LSQ_F32)
     fr.ls = stage_lsqr<float>(c, fr.a32, c.lda32, fr.rc.f32, fr.x0, x);
   else
@@ -959,7 +981,7 @@ lsq_status lsq_sketch(lsq_handle* h, const double* A, const double* b, int64_t m
   Ctx c = make_ctx(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts);
   lsq_status v = validate(c, true);
   if (v != LSQ_OK) return v;
-  if (!Y) return LSQ_E_INVAL;
+  if (!Y || u_s == LSQ_AUTO) return LSQ_E_INVAL;   // AUTO needs the QR that follows the sketch
   c.uw = LSQ_F64;  // no FP32 working copy needed
   return run_guarded(h, nullptr, [&]() {
     stage_cast(c);
@@ -975,6 +997,7 @@ lsq_status lsq_qr_r(lsq_handle* h, const double* A, const double* b, int64_t m, 
   if (c.o.Y_in && !c.A) c.A = c.o.Y_in;  // A is not read when Y is given
   lsq_status v = validate(c, !c.o.Y_in);
   if (v != LSQ_OK) return v;
+  if (u_s == LSQ_AUTO && !c.o.Y_in) return LSQ_E_INVAL;   // the precision choice needs lsq_lsqr/lsq_lsir
   return run_guarded(h, nullptr, [&]() {
     const double* Y = c.o.Y_in;
     if (!Y) {

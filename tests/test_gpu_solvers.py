@@ -299,3 +299,28 @@ def test_batched_uneven_problems_match_single_solves(lsq, handle):
         assert np.array_equal(pr["x"].cpu().numpy(), singles[k][0])
         assert np.array_equal(pr["r"].cpu().numpy(), singles[k][1])
         assert infos[k].ir_converged == 1
+
+
+def test_auto_sketch_precision_follows_the_condition(lsq, handle):
+    """LSQ_AUTO (Sec. 3.4, Sec. 6: u_s kappa(A) < 1 with kappa(A) estimated from R): BF16 where
+    kappa(A) u_s is small, the single-precision split where BF16 is regularised; both reach
+    the 4u level (Table 3 setting)."""
+    out = {}
+    for kappa in (10.0, 1e6):
+        P = paper_problem(kappa, seed=7)
+        m, n, s = 1000, 100, 400
+        x, r = zeros(n), zeros(m)
+        st, info = lsq.lsq_lsir(handle, dev(P.A), dev(P.b), m, n, s, "auto", "f32", "f32", "f64", 1e-6, 0,
+                                None, x, r)
+        xstar, rstar = exact.reference_solution(P.A, P.b)
+        ex, er = exact.forward_errors(x.cpu().numpy(), r.cpu().numpy(), xstar, rstar)
+        out[kappa] = (info.us_used, info.sketches)
+        assert st == 0 and ex <= 4 * 2.0 ** -24 and er <= 4 * 2.0 ** -24, (kappa, ex, er, out[kappa])
+    assert out[10.0] == (lsq.PREC["bf16"], 1), out
+    assert out[1e6] == (lsq.PREC["bf16x3"], 2), out
+    # the choice needs the QR that follows the sketch
+    Y = zeros(400 * 101)
+    P = paper_problem(10.0, seed=7)
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_sketch(handle, dev(P.A), dev(P.b), 1000, 100, 400, "auto", "f32", "f32", "f64", 1e-6, 0, None, Y)
+    assert e.value.status == -1
