@@ -15,6 +15,9 @@ and its application in GMRES-based iterative refinement" (arXiv 2410.06319):
                   embedding with N(0, 1/s) entries; Sec. 5: Omega = s^-1/2 G).
 * ``sketch``   -- Algorithm 1 (the sketch) (Y = Omega A in u_s), with the one-sided
                   power-of-two column scaling of Sec. 3.2.
+* ``sparse``   -- the sparse sign embedding of Sec. 2 as the sketch: zeta
+                  signed rows per data row (Philox, Floyd's sampling), exact
+                  fixed-point sums.
 * ``qr``       -- Algorithm 1 (the QR of the sketch) (Householder QR of Y; R only) and the
                   sketch-and-solve start x_s = R^-1 Q^T Omega b (Sec. 4).
 * ``lsqr``     -- Algorithm 2 (the LSQR start): LSQR right-preconditioned by R.
