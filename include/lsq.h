@@ -128,6 +128,14 @@ typedef struct lsq_opts {
                              completion value, so the first wait runs out after wait_limit_us
                              and the call returns LSQ_E_TIMEOUT (tests the timeout path; the
                              handle stays usable) */
+  int32_t sketch_kind;    /* 0: Gaussian embedding (Sec. 2, generated in the GEMM, precision u_s);
+                             1: sparse sign embedding (Sec. 2): Omega = zeta^-1/2 (omega_1 ..
+                             omega_m), omega_j with sparse_zeta entries +-1 in distinct rows
+                             drawn by Floyd's algorithm from Philox4x32-10 (counter (j lo, j hi,
+                             call, 1), key = seed); each column of [A | b] rounded to a
+                             fixed-point grid 2^-q_c (about 2^-47 of its largest entry) and
+                             summed exactly in integers; u_s is then ignored (treated as F64) */
+  int32_t sparse_zeta;    /* nonzeros per column of the sparse sign embedding, 1..8; 0 -> 8 */
 } lsq_opts;
 
 /* Diagnostics of one call. */

@@ -106,11 +106,21 @@ def sparse_sketch(A, b, s, zeta, seed):
     m, n = A.shape
     Ab = np.concatenate([A, np.asarray(b, dtype=np.float64).reshape(-1, 1)], axis=1)
     rows, signs = sparse_rows(m, s, zeta, seed)
-    q = grid_exponents(Ab, row_counts(rows, s).max())
-    Q = np.stack([to_grid(Ab[:, c], q[c]) for c in range(n + 1)], axis=1)   # (m, n+1) int64
+    counts = row_counts(rows, s)
+    q = grid_exponents(Ab, counts.max())
+    # Exact integer sums: each grid value is hi 2^31 + lo with |hi|, lo < 2^31, and a sketch
+    # row receives at most max(counts) <= 2^22 of them, so the sums of the halves stay below
+    # 2^53 and are exact in FP64 (bincount); acc = hi_sum 2^31 + lo_sum in int64.
+    assert counts.max() <= 1 << 22
+    idx = rows.ravel()
+    sg = signs.ravel()
     acc = np.zeros((s, n + 1), dtype=np.int64)
-    for k in range(zeta):
-        np.add.at(acc, rows[:, k], signs[:, k:k + 1] * Q)
+    for c in range(n + 1):
+        Qc = to_grid(Ab[:, c], q[c])
+        hi, lo = Qc >> 31, Qc & ((1 << 31) - 1)
+        hs = np.bincount(idx, weights=(sg * np.repeat(hi, zeta)).astype(np.float64), minlength=s)
+        ls = np.bincount(idx, weights=(sg * np.repeat(lo, zeta)).astype(np.float64), minlength=s)
+        acc[:, c] = hs.astype(np.int64) * (1 << 31) + ls.astype(np.int64)
     Y = np.ldexp(acc.astype(np.float64), -q[None, :])
     return Y * (1.0 / np.sqrt(float(zeta)))
 

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("gmres_tol", ctypes.c_double), ("kappa_hint", ctypes.c_double),
                 ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p),
                 ("sketch_kchunk", ctypes.c_int64), ("wait_limit_us", ctypes.c_int32),
-                ("expire_sync", ctypes.c_int32)]
+                ("expire_sync", ctypes.c_int32), ("sketch_kind", ctypes.c_int32),
+                ("sparse_zeta", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -224,6 +224,9 @@ lsq_status validate(const Ctx& c, bool need_b) {
   if (c.o.ir_maxit < 0 || c.o.ir_maxit > 32) return LSQ_E_INVAL;
   if (c.o.lsqr_maxit < 0) return LSQ_E_INVAL;
   if (c.o.sketch_kchunk < 0) return LSQ_E_INVAL;
+  if (c.o.sketch_kind < 0 || c.o.sketch_kind > 1) return LSQ_E_INVAL;
+  if (c.o.sparse_zeta < 0 || c.o.sparse_zeta > 8 || c.o.sparse_zeta > c.s) return LSQ_E_INVAL;
+  if (c.o.sketch_kind == 1 && c.o.sparse_zeta == 0 && c.s < 8) return LSQ_E_INVAL;
   return LSQ_OK;
 }
 
@@ -247,6 +250,9 @@ Ctx make_ctx(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t
   else std::memset(&c.o, 0, sizeof(c.o));
   c.lda = c.o.lda > 0 ? c.o.lda : n;
   c.lda32 = round_up(n, 4);
+  // the sparse sign sketch is exact up to a 2^-47 fixed-point grid: it counts as an FP64
+  // sketch in the rules that use u_s (condition warning, escalation, LSQ_AUTO)
+  if (c.o.sketch_kind == 1) c.us = LSQ_F64;
   if (h) {
     c.st = h->stream;
     c.nblk = pass_blocks(h->num_sms);
@@ -353,6 +359,16 @@ void stage_sketch(Ctx& c, double* Y) {
   const int fmt = fmt_of(c.us);
   const int64_t ncols = c.n + 1;
   auto* cmax = static_cast<unsigned long long*>(ws(c.h, "cmax", ncols * 8));
+  if (c.o.sketch_kind == 1) {   // Sec. 2's sparse sign embedding (exact fixed-point sums)
+    StageTimer tt(c.h, ST_SKETCH);
+    const int zeta = c.o.sparse_zeta > 0 ? c.o.sparse_zeta : 8;
+    const SparsePlan sp = plan_sparse(c.m, ncols, (int)c.s, c.h->num_sms);
+    void* work = ws(c.h, "sparse", sparse_workspace(c.m, ncols, (int)c.s, sp.splits));
+    KernTimer kt(c.h, K_SKETCH, c.o.timing);
+    L(launch_sparse_sketch(sp, c.A, c.lda, c.b, c.m, c.n, (int)c.s, zeta, c.seed, cmax, work, Y, c.st));
+    c.h->launches += 3;
+    return;
+  }
   int* kexp = static_cast<int*>(ws(c.h, "kexp", ncols * 4));
   if (fmt == FMT_F16 || fmt == FMT_BF16 || fmt == FMT_E4M3 || fmt == FMT_BF16X3) {
     SketchPlan p;

@@ -78,6 +78,23 @@ cudaError_t launch_sketch_reduce(const void* partial, bool partial_f64, int spli
                                  int64_t s, int64_t s_pad, const int* kexp, double* Y,
                                  cudaStream_t st);
 
+// ---------------------------------------------------------------- sparse sign sketch
+// Sec. 2's sparse sign embedding (zeta <= 8 signed rows per data row, exact fixed-point
+// sums): Y = Omega [A | b], FP64, column-major with ld = s.  cmax_bits: the column maxima
+// of the cast pass.  work: sparse_workspace() bytes.
+struct SparsePlan {
+  int cb;                 // columns per CTA (shared-memory accumulators s x cb int64)
+  int colblocks;
+  int splits;             // slices of the data rows (partials summed exactly)
+  int64_t rows_per_split;
+  size_t smem;
+};
+SparsePlan plan_sparse(int64_t m, int64_t ncols, int s, int num_sms);
+size_t sparse_workspace(int64_t m, int64_t ncols, int s, int splits);
+cudaError_t launch_sparse_sketch(const SparsePlan& p, const double* A, int64_t lda, const double* b, int64_t m,
+                                 int64_t n, int s, int zeta, uint64_t seed,
+                                 const unsigned long long* cmax_bits, void* work, double* Y, cudaStream_t st);
+
 // ---------------------------------------------------------------- QR
 // Householder QR of Y (s x (n+1), col-major) in FP32 (fp64 = false) or FP64.
 // Outputs R (FP64, n x n col-major, diag >= 0) and c (FP64, n).  `work` holds

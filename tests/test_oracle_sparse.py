@@ -107,3 +107,18 @@ def test_kappa_identity_and_embedding_quality():
     su = np.linalg.svd(Om @ U, compute_uv=False)
     assert kar == pytest.approx(su[0] / su[-1], rel=1e-3)
     assert kar <= 1.3 * theory.mp_limits(n, s)[2]
+
+
+def test_split_halves_sum_equals_plain_integer_sum():
+    """The oracle's exact sums (FP64 bincount of 31-bit halves) equal plain int64 scatter-adds."""
+    from lsq_synth import randsvd_problem as rp
+    P = rp(3000, 12, 1e3, seed=1)
+    Y = sparse.sparse_sketch(P.A, P.b, 60, 8, 5)
+    Ab = np.column_stack([P.A, P.b])
+    rows, signs = sparse.sparse_rows(3000, 60, 8, 5)
+    q = sparse.grid_exponents(Ab, sparse.row_counts(rows, 60).max())
+    Q = np.stack([sparse.to_grid(Ab[:, c], q[c]) for c in range(13)], axis=1)
+    acc = np.zeros((60, 13), dtype=np.int64)
+    for k in range(8):
+        np.add.at(acc, rows[:, k], signs[:, k:k + 1] * Q)
+    assert np.array_equal(Y, np.ldexp(acc.astype(np.float64), -q[None, :]) * (1.0 / np.sqrt(8.0)))
