@@ -4,6 +4,7 @@
 // scalars on the device; the host enqueues iterations in batches and reads a
 // small state block once per batch (kernels of an iteration that starts after
 // convergence exit immediately).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -472,7 +473,9 @@ void stage_qr(Ctx& c, const double* Y, double* R, double* xs, RCopies* rc) {
     StageTimer t(c.h, ST_QR);
     const bool f64 = (c.up == LSQ_F64);
     void* work = ws(c.h, "qrwork", (size_t)c.s * (c.n + 1) * (f64 ? 8 : 4));
-    double* aux = static_cast<double*>(ws(c.h, "qraux", (2 * c.n + 8) * 8 + (32 + 32 * 32) * 8));
+    // norms, diag(R), then either tau and T (blocked QR) or n + 1 column flags (FP64 QR)
+    const size_t tail = std::max<size_t>((32 + 32 * 32) * 8, (size_t)(c.n + 1) * 4);
+    double* aux = static_cast<double*>(ws(c.h, "qraux", (2 * c.n + 8) * 8 + tail));
     unsigned* bar = static_cast<unsigned*>(ws(c.h, "qrbar", 64));
     double* cvec = static_cast<double*>(ws(c.h, "qrc", c.n * 8));
     L(launch_qr(f64, Y, c.s, c.n, work, aux, bar, R, cvec, c.h->d_err, c.h->num_sms, c.st));

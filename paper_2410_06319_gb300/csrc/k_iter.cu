@@ -941,30 +941,6 @@ struct GmStepArgs {
   uint64_t wait_ns;   // limit of each grid-sync wait
 };
 
-// Sums of eight values over a warp by a reduce-scatter butterfly: at each exchange a
-// lane keeps half of its values and adds its partner's copies of them, so a lane adds
-// 4 + 2 + 1 + 1 + 1 FP64 numbers instead of 8 x 5 (GB300's FP64 pipe is narrow).
-// Lane L returns the warp total of value (L >> 2) & 7, in a fixed order.
-__device__ __forceinline__ double warp_reduce8(const double (&v)[8]) {
-  const int lane = threadIdx.x & 31;
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-  double u[4], x[2];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double keep = b4 ? v[4 + k] : v[k], send = b4 ? v[k] : v[4 + k];
-    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const double keep = b3 ? u[2 + k] : u[k], send = b3 ? u[k] : u[2 + k];
-    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  double y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
-  y += __shfl_xor_sync(0xffffffffu, y, 2);
-  y += __shfl_xor_sync(0xffffffffu, y, 1);
-  return y;
-}
-
 // Dp[c][block] = sum over rows [r0, r1) of V[c][i] w[i] for c < ncols; Dp[ncols][block] = sum of w[i]^2.
 // The (ncols + 1) sums form G groups of eight; the CTA's rows are cut into S slices with
 // G x S close to the warp count, and each warp takes one (group, slice) task: its lanes

@@ -83,6 +83,270 @@ __global__ void __launch_bounds__(256) qr_kernel(T* __restrict__ W, int64_t s, i
   }
 }
 
+// FP64 variant (u_QR = double) for GB300's narrow FP64 pipe: one 512-thread CTA per SM.
+// Step k: every CTA loads v_k into shared memory; CTA b takes a contiguous share of the
+// trailing columns k+1..n (column n is Omega b) and treats them eight at a time: one sweep
+// over the rows forms the eight dot products v^T y_j (eight independent FMA chains per
+// thread), one reduce-scatter butterfly per warp and sixteen-term sums give w_j, and a
+// second sweep applies y_j -= (w_j tau) v (the owner of column k+1 also sums the squares of
+// its updated rows 1.. for the next norm).  One bounded grid barrier per step, as before;
+// the same reflectors and per-column arithmetic, with blocked sums.
+constexpr int kQr64Threads = 512;
+
+__global__ void __launch_bounds__(kQr64Threads, 1)
+    qr64_kernel(double* __restrict__ W, int64_t s, int64_t n, double* __restrict__ norms,
+                double* __restrict__ diagR, unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  double* vs = reinterpret_cast<double*>(qr_smem);
+  __shared__ double red[16 * 9];
+  __shared__ double wsum[8];
+  __shared__ double nred[17];
+  const unsigned nb = gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (blockIdx.x == 0) {
+    double part = 0.0;
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) part = fma(W[t], W[t], part);
+    part = warp_sum(part);
+    if (lane == 0) nred[warp] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double q = 0.0;
+      for (int w = 0; w < nw; ++w) q += nred[w];
+      norms[0] = q;
+    }
+  }
+  if (!grid_barrier(bar, bar + 1, nb, err)) return;
+  for (int64_t k = 0; k < n; ++k) {
+    const double* colk = W + k * s;
+    const double alpha = sqrt(__ldcg(norms + k));
+    const double x0 = __ldcg(colk + k);
+    const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+    const double tau = (alpha > 0.0) ? 1.0 / (alpha * (alpha + fabs(x0))) : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) diagR[k] = -sgn * alpha;
+    const int64_t len = s - k;
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) vs[t] = (t == 0) ? x0 + sgn * alpha : __ldcg(colk + k + t);
+    __syncthreads();
+    const int64_t ntr = n - k;                       // trailing columns k+1..n
+    const int64_t per = (ntr + nb - 1) / nb;
+    const int64_t j0 = k + 1 + (int64_t)blockIdx.x * per, j1 = min(n + 1, j0 + per);
+    for (int64_t g = j0; g < j1; g += 8) {
+      double d[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d[q] = 0.0;
+      for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+        const double vt = vs[t];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (g + q < j1) d[q] = fma(vt, __ldcg(W + (g + q) * s + k + t), d[q]);
+      }
+      const double tot = warp_reduce8(d);
+      if ((lane & 3) == 0) red[warp * 9 + ((lane >> 2) & 7)] = tot;
+      __syncthreads();
+      if (threadIdx.x < 8) {
+        double q = 0.0;
+        for (int w = 0; w < nw; ++w) q += red[w * 9 + threadIdx.x];
+        wsum[threadIdx.x] = q * tau;
+      }
+      __syncthreads();
+      const bool owner = (g == k + 1) && (k + 1 < n);   // column k+1 leaves its norm
+      double sq = 0.0;
+      for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+        const double vt = vs[t];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (g + q < j1) {
+            double* p = W + (g + q) * s + k + t;
+            const double val = fma(-wsum[q], vt, *p);
+            *p = val;
+            if (q == 0 && owner && t >= 1) sq = fma(val, val, sq);
+          }
+        }
+      }
+      if (owner) {
+        sq = warp_sum(sq);
+        if (lane == 0) nred[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double q = 0.0;
+          for (int w = 0; w < nw; ++w) q += nred[w];
+          norms[k + 1] = q;
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, bar + 1, nb, err)) return;
+  }
+}
+
+// FP64 variant with the columns resident in shared memory (s <= 4096 and at most
+// kQr64sMaxCols columns per CTA), with look-ahead.  CTA b owns columns b, b + nb, ...
+// (cyclic, so every CTA keeps a share of the trailing matrix to the end) and keeps them in
+// shared memory for the whole factorization; each thread holds v_k for its rows in
+// registers.  A CTA touches only its own columns, so steps need no grid barrier: step k
+// waits (bounded) for the flag ready[k] that the owner of column k raises once column k
+// (updated by reflectors 0..k-1) and its norm are in global memory.  The owner of column
+// k+1 updates that column first, publishes it, then updates its other columns; the rest of
+// the trailing update overlaps the next pivot's critical path.  ready[] (n + 1 words) must
+// be zero at launch.  At the end the owner of column n (b) writes it back.
+constexpr int kQr64sMaxCols = 8;
+constexpr int kQr64sRows = 8;          // rows per thread: s <= 512 * 8
+
+__device__ __forceinline__ double block_sum_512(double v, double* nred) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) nred[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q = 0.0;
+    for (int w = 0; w < nw; ++w) q += nred[w];
+    nred[16] = q;
+  }
+  __syncthreads();
+  return nred[16];
+}
+
+__global__ void __launch_bounds__(kQr64Threads, 1)
+    qr64s_kernel(double* __restrict__ W, int64_t s, int64_t n, double* __restrict__ norms,
+                 double* __restrict__ diagR, unsigned* __restrict__ ready, int* err) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  double* cols = reinterpret_cast<double*>(qr_smem);   // [owned][s]
+  __shared__ double red[16 * 9];
+  __shared__ double wsum[8];
+  __shared__ double nred[17];
+  __shared__ int ok_s;
+  const int nb = (int)gridDim.x, b = (int)blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t ncols = n + 1;
+  int owned = 0;
+  for (int64_t j = b; j < ncols; j += nb) ++owned;
+  for (int c = 0; c < owned; ++c) {
+    const int64_t j = b + (int64_t)c * nb;
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) cols[c * s + t] = W[j * s + t];
+  }
+  __syncthreads();
+  if (b == 0) {   // column 0 is ready as it stands: its norm, then the flag
+    double part = 0.0;
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) part = fma(cols[t], cols[t], part);
+    const double nn = block_sum_512(part, nred);
+    if (threadIdx.x == 0) {
+      norms[0] = nn;
+      __threadfence();
+      atomicExch(ready, 1u);
+    }
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    // ---- wait for column k and its norm
+    if (threadIdx.x == 0) {
+      volatile unsigned* vr = ready + k;
+      int ok = 1;
+      if (*vr == 0u) {
+        const uint64_t t0 = globaltimer_ns();
+        while (*vr == 0u) {
+          if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            set_error(err, DEV_TIMEOUT_GRID);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    const double* colk = W + k * s;
+    const double alpha = sqrt(__ldcg(norms + k));
+    const double x0 = __ldcg(colk + k);
+    const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+    const double tau = (alpha > 0.0) ? 1.0 / (alpha * (alpha + fabs(x0))) : 0.0;
+    if (b == 0 && threadIdx.x == 0) diagR[k] = -sgn * alpha;
+    double v[kQr64sRows];
+#pragma unroll
+    for (int r = 0; r < kQr64sRows; ++r) {
+      const int64_t t = threadIdx.x + (int64_t)r * blockDim.x;
+      v[r] = (t < k || t >= s) ? 0.0 : (t == k ? x0 + sgn * alpha : __ldcg(colk + t));
+    }
+    // owned columns with index > k, from c_first on; the next pivot k+1 first if owned
+    int c_first = 0;
+    if (k + 1 > b) c_first = (int)((k + 1 - b + nb - 1) / nb);
+    const int64_t jn = k + 1;
+    if (jn < n && jn % nb == b) {
+      const int cn = (int)(jn / nb);       // == c_first
+      double d = 0.0;
+#pragma unroll
+      for (int r = 0; r < kQr64sRows; ++r) {
+        const int64_t t = threadIdx.x + (int64_t)r * blockDim.x;
+        if (t < s) d = fma(v[r], cols[cn * s + t], d);
+      }
+      const double wn = block_sum_512(d, nred) * tau;
+      double sq = 0.0;
+#pragma unroll
+      for (int r = 0; r < kQr64sRows; ++r) {
+        const int64_t t = threadIdx.x + (int64_t)r * blockDim.x;
+        if (t < s && t >= k) {
+          const double val = fma(-wn, v[r], cols[cn * s + t]);
+          cols[cn * s + t] = val;
+          if (t >= jn) sq = fma(val, val, sq);
+        }
+      }
+      const double nn = block_sum_512(sq, nred);
+      for (int64_t t = threadIdx.x; t < s; t += blockDim.x) W[jn * s + t] = cols[cn * s + t];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        norms[jn] = nn;
+        __threadfence();
+        atomicExch(ready + jn, 1u);
+      }
+      c_first = cn + 1;
+    }
+    // ---- the other owned trailing columns, up to eight at a time
+    if (c_first < owned) {
+      double d[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d[q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c_first + q;
+        if (c < owned) {
+#pragma unroll
+          for (int r = 0; r < kQr64sRows; ++r) {
+            const int64_t t = threadIdx.x + (int64_t)r * blockDim.x;
+            if (t < s) d[q] = fma(v[r], cols[c * s + t], d[q]);
+          }
+        }
+      }
+      const double tot = warp_reduce8(d);
+      if ((lane & 3) == 0) red[warp * 9 + ((lane >> 2) & 7)] = tot;
+      __syncthreads();
+      if (threadIdx.x < 8) {
+        double q = 0.0;
+        for (int w = 0; w < nw; ++w) q += red[w * 9 + threadIdx.x];
+        wsum[threadIdx.x] = q * tau;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c_first + q;
+        if (c < owned) {
+          const double wq = wsum[q];
+#pragma unroll
+          for (int r = 0; r < kQr64sRows; ++r) {
+            const int64_t t = threadIdx.x + (int64_t)r * blockDim.x;
+            if (t < s && t >= k) cols[c * s + t] = fma(-wq, v[r], cols[c * s + t]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // columns 0..n-1 are final in W since they were published; only b's column is left
+  if (n % nb == b) {
+    const int c = (int)(n / nb);
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) W[n * s + t] = cols[c * s + t];
+  }
+}
+
 // R (FP64, col-major, diag >= 0) and c from the factored work matrix.
 template <typename T>
 __global__ void qr_finalize_kernel(const T* __restrict__ W, int64_t s, int64_t n,
@@ -527,6 +791,43 @@ static cudaError_t run_qr(const double* Y, int64_t s, int64_t n, T* W, double* a
   return cudaGetLastError();
 }
 
+static cudaError_t run_qr64(const double* Y, int64_t s, int64_t n, double* W, double* aux, unsigned* bar,
+                           double* R, double* c, int* err, int num_sms, cudaStream_t st) {
+  const int64_t total = s * (n + 1);
+  cudaError_t e = cudaMemcpyAsync(W, Y, (size_t)total * 8, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const int grid = num_sms;                      // one CTA per SM (co-resident: occ >= 1)
+  const int64_t per_cta = (n + 1 + grid - 1) / grid;
+  const bool resident = s <= (int64_t)kQr64Threads * kQr64sRows && per_cta <= kQr64sMaxCols &&
+                        (size_t)per_cta * s * 8 <= 227 * 1024 - 2048;
+  auto kern = resident ? qr64s_kernel : qr64_kernel;
+  const size_t smem = resident ? (size_t)per_cta * s * 8 : (size_t)s * 8;
+  e = allow_dyn_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kQr64Threads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  double* norms = aux;
+  double* diagR = aux + n;
+  // the resident kernel's per-column flags follow diag(R) in aux (n + 1 words, zeroed here)
+  unsigned* ready = reinterpret_cast<unsigned*>(aux + 2 * n + 8);
+  if (resident) {
+    e = cudaMemsetAsync(ready, 0, (size_t)(n + 1) * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  unsigned* sync = resident ? ready : bar;
+  double* Wp = W;
+  int64_t sp = s, np = n;
+  void* args[] = {&Wp, &sp, &np, &norms, &diagR, &sync, &err};
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kQr64Threads), args, smem, st);
+  if (e != cudaSuccess) return e;
+  qr_finalize_kernel<double><<<(unsigned)n, 256, 0, st>>>(W, s, n, diagR, R, c);
+  return cudaGetLastError();
+}
+
 template <typename T, int NB>
 static cudaError_t run_qr_blocked(const double* Y, int64_t s, int64_t n, T* W, double* aux, double* R,
                                   double* c, int num_sms, cudaStream_t st) {
@@ -565,7 +866,7 @@ cudaError_t launch_qr(bool fp64, const double* Y, int64_t s, int64_t n, void* wo
   if (!fp64 && qr_blocked_fits<float>(s, 24))
     return run_qr_blocked<float, 24>(Y, s, n, static_cast<float*>(work), aux, R, c, num_sms, st);
   if (fp64)
-    return run_qr<double>(Y, s, n, static_cast<double*>(work), aux, bar, R, c, err, num_sms, st);
+    return run_qr64(Y, s, n, static_cast<double*>(work), aux, bar, R, c, err, num_sms, st);
   return run_qr<float>(Y, s, n, static_cast<float*>(work), aux, bar, R, c, err, num_sms, st);
 }
 
