@@ -24,6 +24,9 @@ and its application in GMRES-based iterative refinement" (arXiv 2410.06319):
 * ``fgmres``   -- Algorithm 2 (the FGMRES solve): split-preconditioned FGMRES, Eq. (1.2).
 * ``lsir``     -- Algorithm 2 (augmented-system iterative refinement) with
                   the precision-escalation rule of Sec. 5.
+* ``dd``       -- products beyond double (exact splits and sums, rounded to
+                  double-double) for the escalated FGMRES of Sec. 5 with u
+                  double (u_A = u_L = u_R = quad).
 * ``exact``    -- double-double residuals (Dot2) and a refined reference
                   solution x*, r* (the role of the 64-digit solve of Sec. 5).
 * ``theory``   -- closed forms used as pins (Sec. 2 identities, Eq. 4.1,

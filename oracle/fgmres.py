@@ -19,30 +19,49 @@ The products with Atilde, M_L^-1 and M_R^-1 are formed in ``op_dtype``
 basis, the Gram-Schmidt and the rotations): FP64 by default (the GPU path's
 choice); the paper's own setting (Sec. 4: the remaining computations in u) is
 ``work_dtype = u``.
+
+Scaling (Sec. 4.1): with ``alpha`` != 1 the system solved is the scaled one,
+M_L^-1 Atilde_alpha M_R^-1 [dr / alpha; dz] = [f; h / alpha] with
+Atilde_alpha = [[alpha I, A], [A^T, 0]]: the same correction, since alpha (dr / alpha)
++ A dx = f and A^T (dr / alpha) = g / alpha.  Sec. 5 runs alpha = 1.
+
+``op_dtype = "dd"`` takes the three products in double-double or better
+(``oracle.dd``: exact splits and sums), each rounded once to FP64 where FGMRES stores
+it: Sec. 5's escalated setting u_A = u_L = u_R = quad for u = double.
 """
 import numpy as np
 
+from . import dd
 from .qr import solve_upper, solve_upper_t
 
 
-def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64, work_dtype=np.float64):
-    """Solve M_L^-1 Atilde M_R^-1 y = [f; h]; return (dr, dx, info)."""
+def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64, work_dtype=np.float64, alpha=1.0):
+    """Solve M_L^-1 Atilde_alpha M_R^-1 y = [f; h / alpha]; return (dr, dx, info) with
+    dr = alpha y_top (alpha = 1: the unscaled system of Eq. (1.2))."""
     wd = work_dtype
     A64 = np.asarray(A, dtype=np.float64)
     m, n = A64.shape
-    Ao = A64.astype(op_dtype)
-    Ro = np.asarray(R, dtype=op_dtype)
+    quad = isinstance(op_dtype, str) and op_dtype == "dd"
+    Ao = A64 if quad else A64.astype(op_dtype)
+    Ro = np.asarray(R, dtype=np.float64) if quad else np.asarray(R, dtype=op_dtype)
 
     def apply(vtop, vbot):
-        """z = M_R^-1 v (u_R), then w = M_L^-1 Atilde z (u_A, u_L).  The top block of
-        M_R^-1 and of M_L^-1 is I and Atilde's top-left block is I: z_top = v_top enters
-        w_top exactly, and only the products A z_bot and A^T z_top are rounded to u_A."""
+        """z = M_R^-1 v (u_R), then w = M_L^-1 Atilde_alpha z (u_A, u_L).  The top block of
+        M_R^-1 and of M_L^-1 is I and Atilde_alpha's top-left block is alpha I: z_top = v_top
+        enters w_top as alpha v_top, and only the products A z_bot and A^T z_top are
+        rounded to u_A."""
+        if quad:
+            zh, zl = dd.solve_upper(Ro, vbot)
+            wt, _ = dd.matvec(Ao, zh, zl, add=vtop, alpha=alpha)
+            th, tl = dd.matvec_t(Ao, vtop)
+            wb, _ = dd.solve_upper_t(Ro, th, tl)
+            return zh.astype(wd), np.concatenate([wt, wb]).astype(wd)
         zb = solve_upper(Ro, vbot.astype(op_dtype)).astype(op_dtype)
-        wt = vtop + (Ao @ zb).astype(wd)
+        wt = alpha * vtop + (Ao @ zb).astype(wd)
         wb = solve_upper_t(Ro, (Ao.T @ vtop.astype(op_dtype)).astype(op_dtype)).astype(op_dtype)
         return zb.astype(wd), np.concatenate([wt, wb.astype(wd)])
 
-    rhs = np.concatenate([np.asarray(f, np.float64), np.asarray(h, np.float64)]).astype(wd)
+    rhs = np.concatenate([np.asarray(f, np.float64), np.asarray(h, np.float64) / alpha]).astype(wd)
     beta = np.linalg.norm(rhs)
     info = dict(its=0, relres=0.0, converged=True)
     if beta == 0:
@@ -81,7 +100,7 @@ def fgmres(A, R, f, h, tol, maxit, op_dtype=np.float64, work_dtype=np.float64):
         if relres <= tol:
             break
     y = solve_upper(H[:k, :k], g[:k])
-    dr = V[:m, :k] @ y
+    dr = alpha * (V[:m, :k] @ y)
     dx = Zb[:, :k] @ y
     info.update(its=k, relres=float(relres), converged=bool(relres <= tol))
     return dr.astype(np.float64), dx.astype(np.float64), info

@@ -44,8 +44,9 @@ def _residual(A, b, r, x, ur):
 
 
 def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None, rstar=None,
-           gm_work_dtype=np.float64):
-    """The refinement loop of Alg. 2 from (x0, r0).  Returns (x, r, info)."""
+           gm_work_dtype=np.float64, alpha=1.0):
+    """The refinement loop of Alg. 2 from (x0, r0).  Returns (x, r, info).  ``alpha``
+    scales the augmented system (Sec. 4.1; see ``fgmres``)."""
     x = np.array(x0, np.float64, copy=True)
     r = np.array(r0, np.float64, copy=True)
     its, gm_total, converged = 0, 0, False
@@ -54,7 +55,8 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
     for _ in range(ir_maxit):
         f, g = _residual(A, b, r, x, ur)
         h = solve_upper_t(R, g)
-        dr, dx, ginfo = fgmres(A, R, f, h, tol, gm_maxit, op_dtype=op_dtype, work_dtype=gm_work_dtype)
+        dr, dx, ginfo = fgmres(A, R, f, h, tol, gm_maxit, op_dtype=op_dtype, work_dtype=gm_work_dtype,
+                               alpha=alpha)
         x = x + dx
         r = r + dr
         its += 1
@@ -80,13 +82,16 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
 
 def lsir(A, b, R, xs, u, tol, lsqr_maxit=None, ir_maxit=30, gm_maxit=50,
          w_dtype=np.float64, op_dtype=None, ur="exact", us=None, kappa=None,
-         xstar=None, rstar=None, escalate=True, gm_work_dtype=np.float64):
+         xstar=None, rstar=None, escalate=True, gm_work_dtype=np.float64, alpha=1.0):
     """Algorithm 2.  ``u`` is the unit roundoff of ``w_dtype``.
 
     Returns (x, r, info).  ``us`` (unit roundoff of the sketch) and ``kappa``
     drive the escalation rule of Sec. 5.  ``gm_work_dtype`` is the precision of
     FGMRES's basis, Gram-Schmidt and rotations (see ``fgmres``); the escalation
-    raises only the products (u_A = u_L = u_R), as in Sec. 5.
+    raises only the products (u_A = u_L = u_R), as in Sec. 5: to double for u
+    single (Table 3), to quad (double-double, ``oracle.dd``) with at most 80 FGMRES
+    iterations for u double (Table 4).  ``alpha`` scales the augmented system
+    (Sec. 4.1).
     """
     A = np.asarray(A, np.float64)
     b = np.asarray(b, np.float64)
@@ -100,12 +105,13 @@ def lsir(A, b, R, xs, u, tol, lsqr_maxit=None, ir_maxit=30, gm_maxit=50,
     r0 = (b.astype(w_dtype) - Aw @ x0.astype(w_dtype)).astype(np.float64)
     x0 = x0.astype(w_dtype).astype(np.float64)
     x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar, rstar,
-                        gm_work_dtype)
+                        gm_work_dtype, alpha)
     info["escalated"] = False
     if (not info["converged"] and escalate and us is not None and kappa is not None
             and kappa < 1.0 / us):
-        x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, np.float64, ur,
-                            xstar, rstar, gm_work_dtype)
+        double = np.dtype(w_dtype) == np.float64
+        x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, max(gm_maxit, 80) if double else gm_maxit,
+                            "dd" if double else np.float64, ur, xstar, rstar, gm_work_dtype, alpha)
         info["escalated"] = True
     info["lsqr"] = linfo
     return x, r, info

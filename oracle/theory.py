@@ -16,9 +16,14 @@ import numpy as np
 
 
 def kappa_prec_aug(alpha, smax, smin):
-    """Eq. (4.1): kappa(M_L^-1 Atilde_alpha M_R^-1)."""
+    """Sec. 4.1: kappa(M_L^-1 Atilde_alpha M_R^-1) from the extreme singular values of
+    A R^-1.  The eigenvalues of [[alpha I, B], [B^T, 0]] (B = A R^-1, m > n) are alpha
+    (m - n times) and (alpha +- sqrt(alpha^2 + 4 sigma_i^2)) / 2, so the smallest
+    magnitude is min(alpha, (sqrt(alpha^2 + 4 sigma_min^2) - alpha) / 2).  The printed
+    formula has min{2, ...} in the denominator, which is this one at alpha = 1 (the only
+    value Sec. 5 uses); the 2 alpha here is the reading for alpha != 1."""
     num = alpha + np.sqrt(alpha ** 2 + 4 * smax ** 2)
-    den = min(2.0, np.sqrt(alpha ** 2 + 4 * smin ** 2) - alpha)
+    den = min(2.0 * alpha, np.sqrt(alpha ** 2 + 4 * smin ** 2) - alpha)
     return num / den
 
 
