@@ -65,7 +65,11 @@ typedef enum lsq_prec {
   LSQ_F16 = 2,
   LSQ_BF16 = 3,
   LSQ_E4M3 = 4,
-  LSQ_BF16X3 = 5
+  LSQ_BF16X3 = 5,
+  LSQ_F64X2 = 6    /* double-double, hi + lo (about 2^-106; stands for the paper's quad, Sec. 5).
+                      As u_r: the refinement residual [f; g] = [b - r - A x; -A^T r] of Alg. 2
+                      with every product split exactly and summed in double-double, rounded
+                      once to FP64.  Not a sketch, QR or working precision. */
 } lsq_prec;
 
 typedef enum lsq_status {
@@ -85,7 +89,7 @@ typedef enum lsq_status {
 
 /* info.flags bits */
 #define LSQ_WARN_COND 1     /* kappa_est(R) * u_s >= 1: outside Thm 3.1 (Sec. 3.4) */
-#define LSQ_INFO_ESCALATED 2 /* refinement re-run with FP64 FGMRES products (Sec. 5) */
+#define LSQ_INFO_ESCALATED 2 /* refinement re-run with FGMRES products in u^2 (Sec. 5) */
 
 typedef struct lsq_handle lsq_handle;
 
@@ -95,8 +99,10 @@ typedef struct lsq_opts {
   int32_t lsqr_maxit;     /* LSQR cap; 0 -> 2n (Sec. 5) */
   int32_t ir_maxit;       /* refinement cap; 0 -> 30 (Sec. 5) */
   int32_t gmres_maxit;    /* FGMRES cap per refinement step; 0 -> 50 (Sec. 5) */
-  int32_t no_escalate;    /* 1 disables the Sec. 5 re-run with FGMRES products in FP64
-                             (u_A = u_L = u_R = double for u = single) */
+  int32_t no_escalate;    /* 1 disables the Sec. 5 re-run of the refinement from (x_0, r_0) with
+                             FGMRES products in u^2: u_A = u_L = u_R = double for u = single;
+                             double-double (quad) for u = double, with at most
+                             max(gmres_maxit, 80) FGMRES iterations (Table 4) */
   int32_t no_colscale;    /* 1 disables the power-of-two column scaling (Sec. 3.2) */
   int32_t ir_stop;        /* refinement stop rule, with dx_i, dr_i the corrections of step i:
                              0: ||dx_i|| <= u||x|| and ||dr_i|| <= u||r||, or (i >= 1) the
@@ -136,6 +142,17 @@ typedef struct lsq_opts {
                              fixed-point grid 2^-q_c (about 2^-47 of its largest entry) and
                              summed exactly in integers; u_s is then ignored (treated as F64) */
   int32_t sparse_zeta;    /* nonzeros per column of the sparse sign embedding, 1..8; 0 -> 8 */
+  int32_t ops_escalated;  /* 1: FGMRES products in u^2 from the first refinement step (FP64 for
+                             u_w = F32; double-double for u_w = F64), the products of the Sec. 5
+                             re-run */
+  double aug_alpha;       /* Sec. 4.1 scaling of the augmented system: FGMRES solves
+                             M_L^-1 [[alpha I, A], [A^T, 0]] M_R^-1 [dr/alpha; R dx] =
+                             [f; h/alpha], which gives the same correction (dr, dx);
+                             0 -> 1 (unscaled, as Sec. 5 runs it); must be finite, >= 0 */
+  int32_t h_in_ur;        /* with u_r = LSQ_F64X2: 1 solves h = R^-T g in double-double from the
+                             double-double g (Alg. 2 marks this solve with u_r); 0 (default)
+                             solves it in FP64 from g rounded to FP64, the reading under which
+                             Table 4's escalated rows come out as printed */
 } lsq_opts;
 
 /* Diagnostics of one call. */
@@ -168,6 +185,7 @@ typedef struct lsq_info {
   int64_t arnoldi_second_passes; /* FGMRES Arnoldi steps that ran the second Gram-Schmidt pass */
   int32_t us_used;          /* the sketch precision used (the choice of LSQ_AUTO) */
   int32_t sketches;         /* sketches taken (more than one when LSQ_AUTO moved up its ladder) */
+  double aug_alpha;         /* the alpha of the augmented system the refinement solved */
 } lsq_info;
 
 /* sizeof(lsq_opts) for which = 0, sizeof(lsq_info) for which = 1, else 0: lets
@@ -232,15 +250,17 @@ lsq_status lsq_lsqr(lsq_handle* h, const double* A, const double* b, int64_t m, 
 
 /*
  * lsq_lsir -- Algorithm 2: LSQR start, then augmented-system refinement:
- * [f; g] = [b; 0] - [[I, A], [A^T, 0]] [r; x] in u_r (F64), h = R^-T g in u_r,
- * split-preconditioned FGMRES (Eq. 1.2; products with Atilde, M_L^-1, M_R^-1
- * in u_w, Arnoldi and Givens in FP64), update in FP64.  Stops by the rule
+ * [f; g] = [b; 0] - [[I, A], [A^T, 0]] [r; x] in u_r (F64, or double-double
+ * for LSQ_F64X2), h = R^-T g in FP64 (or u_r, opts->h_in_ur), split-preconditioned FGMRES (Eq. 1.2,
+ * scaled by opts->aug_alpha as in Sec. 4.1; products with Atilde, M_L^-1,
+ * M_R^-1 in u_w, Arnoldi and Givens in FP64), update in FP64.  Stops by the rule
  * of opts->ir_stop (by default ||dx|| <= u_w ||x|| and ||dr|| <= u_w ||r||,
  * or the contraction estimate puts the remaining error within 4 u_w), or
  * after opts->ir_maxit steps;
  * then, if not converged and kappa < 1/u_s (kappa_hint, else kappa_est(R)),
  * re-runs the refinement from the LSQR result with the FGMRES products in
- * FP64 (Sec. 5).
+ * u_w^2: FP64 for u_w = F32; double-double with at most max(gmres_maxit, 80)
+ * FGMRES iterations for u_w = F64 (Sec. 5, Tables 3 and 4).
  * Out: x (device FP64, n) and r = b - A x (device FP64, m; may be NULL).
  */
 lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
@@ -249,9 +269,26 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
                     lsq_info* info);
 
 /*
+ * lsq_residual -- the refinement residual of Algorithm 2 (Sec. 4):
+ * [f; g] = [b; 0] - [[I, A], [A^T, 0]] [r; x] = [b - r - A x; -A^T r] in u_r:
+ * LSQ_F64 (FP64 fused multiply-adds) or LSQ_F64X2 (every product split exactly
+ * and summed in double-double, each entry rounded once to FP64).  A (m x n
+ * row-major, row stride opts->lda or n), b and r (m) and x (n) are DEVICE FP64
+ * arrays, read only; f (m) and g (n) are DEVICE FP64 outputs.  Asynchronous on
+ * the handle's stream like the other calls.  LSQ_E_INVAL for a bad argument
+ * (nothing written).
+ */
+lsq_status lsq_residual(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n,
+                        lsq_prec u_r, const lsq_opts* opts, const double* x, const double* r,
+                        double* f, double* g);
+
+/*
  * lsq_ir_step -- one refinement step of Algorithm 2 from the caller's (x, r):
- * [f; g] = [b - r - A x; -A^T r] in u_r (F64), h = R^-T g in u_r, FGMRES on
- * M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (Eq. 1.2; products in u_w, Arnoldi and
+ * [f; g] = [b - r - A x; -A^T r] in u_r (F64 or LSQ_F64X2), h = R^-T g in FP64
+ * (or in u_r with opts->h_in_ur),
+ * FGMRES on M_L^-1 Atilde_alpha M_R^-1 [dr/alpha; dz] = [f; h/alpha] (Eq. 1.2 and
+ * Sec. 4.1, alpha = opts->aug_alpha or 1; products in u_w, or in u_w^2 with
+ * opts->ops_escalated; Arnoldi and
  * Givens in FP64, x0 = 0, at most opts->gmres_maxit iterations, tolerance
  * opts->gmres_tol or tol), then x += R^-1 dz and r += dr.  R is a DEVICE n x n
  * column-major upper-triangular FP64 matrix (e.g. from lsq_qr_r); x (n) and r (m)

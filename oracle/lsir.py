@@ -25,11 +25,17 @@ correction, i.e. the remaining error, is then within the 4u the paper asks
 of the forward errors).
 
 Here u_r is the correctly rounded residual of ``exact.residual_aug`` when
-``ur='exact'`` and plain FP64 otherwise; h_i is solved in FP64.
+``ur='exact'`` and plain FP64 otherwise.  h_i = R^-T g_i: Alg. 2 marks this solve
+with u_r, but Table 4's escalated rows (2*, 138* at kappa = 1e12 and 2*, 137* at
+1e14) are reproduced only when h_i is solved in FP64 from the rounded g_i (2, 140
+and 2, 141 here; a double-double solve from the double-double g_i gives 1, 71 and
+2, 139).  The default reading is therefore the FP64 solve; ``h_ur=True`` (with
+``ur='exact'``) takes the solve in double-double as Alg. 2 prints it
+(``oracle.dd``), rounded to FP64 where FGMRES takes it.
 """
 import numpy as np
 
-from . import exact
+from . import dd, exact
 from .fgmres import fgmres
 from .lsqr import lsqr
 from .qr import solve_upper_t
@@ -44,7 +50,7 @@ def _residual(A, b, r, x, ur):
 
 
 def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None, rstar=None,
-           gm_work_dtype=np.float64, alpha=1.0):
+           gm_work_dtype=np.float64, alpha=1.0, h_ur=False):
     """The refinement loop of Alg. 2 from (x0, r0).  Returns (x, r, info).  ``alpha``
     scales the augmented system (Sec. 4.1; see ``fgmres``)."""
     x = np.array(x0, np.float64, copy=True)
@@ -54,7 +60,11 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
     gm_its = []
     for _ in range(ir_maxit):
         f, g = _residual(A, b, r, x, ur)
-        h = solve_upper_t(R, g)
+        if ur == "exact" and h_ur:
+            gh, gl = dd.matvec_t(A, -np.asarray(r, np.float64))   # g = -A^T r as double-double
+            h = dd.solve_upper_t(np.asarray(R, np.float64), gh, gl)[0]
+        else:
+            h = solve_upper_t(R, g)
         dr, dx, ginfo = fgmres(A, R, f, h, tol, gm_maxit, op_dtype=op_dtype, work_dtype=gm_work_dtype,
                                alpha=alpha)
         x = x + dx
@@ -82,7 +92,7 @@ def refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar=None
 
 def lsir(A, b, R, xs, u, tol, lsqr_maxit=None, ir_maxit=30, gm_maxit=50,
          w_dtype=np.float64, op_dtype=None, ur="exact", us=None, kappa=None,
-         xstar=None, rstar=None, escalate=True, gm_work_dtype=np.float64, alpha=1.0):
+         xstar=None, rstar=None, escalate=True, gm_work_dtype=np.float64, alpha=1.0, h_ur=False):
     """Algorithm 2.  ``u`` is the unit roundoff of ``w_dtype``.
 
     Returns (x, r, info).  ``us`` (unit roundoff of the sketch) and ``kappa``
@@ -91,7 +101,7 @@ def lsir(A, b, R, xs, u, tol, lsqr_maxit=None, ir_maxit=30, gm_maxit=50,
     raises only the products (u_A = u_L = u_R), as in Sec. 5: to double for u
     single (Table 3), to quad (double-double, ``oracle.dd``) with at most 80 FGMRES
     iterations for u double (Table 4).  ``alpha`` scales the augmented system
-    (Sec. 4.1).
+    (Sec. 4.1); ``h_ur`` solves h = R^-T g in u_r (see the module docstring).
     """
     A = np.asarray(A, np.float64)
     b = np.asarray(b, np.float64)
@@ -105,13 +115,13 @@ def lsir(A, b, R, xs, u, tol, lsqr_maxit=None, ir_maxit=30, gm_maxit=50,
     r0 = (b.astype(w_dtype) - Aw @ x0.astype(w_dtype)).astype(np.float64)
     x0 = x0.astype(w_dtype).astype(np.float64)
     x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, gm_maxit, op_dtype, ur, xstar, rstar,
-                        gm_work_dtype, alpha)
+                        gm_work_dtype, alpha, h_ur)
     info["escalated"] = False
     if (not info["converged"] and escalate and us is not None and kappa is not None
             and kappa < 1.0 / us):
         double = np.dtype(w_dtype) == np.float64
         x, r, info = refine(A, b, R, x0, r0, u, tol, ir_maxit, max(gm_maxit, 80) if double else gm_maxit,
-                            "dd" if double else np.float64, ur, xstar, rstar, gm_work_dtype, alpha)
+                            "dd" if double else np.float64, ur, xstar, rstar, gm_work_dtype, alpha, h_ur)
         info["escalated"] = True
     info["lsqr"] = linfo
     return x, r, info

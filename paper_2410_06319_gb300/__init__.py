@@ -14,6 +14,6 @@ library has not been built; there is no fallback.
 from ._lib import (  # noqa: F401
     KERNELS, PREC, STATUS, Handle, Info, LsqError, Opts, Problem, lib, lsq_ir_step, lsq_lsir, lsq_lsir_batched,
     lsq_lsir_host,
-    lsq_lsqr, lsq_omega, lsq_probe_fma_rate, lsq_qr_r, lsq_qr_r_noalloc, lsq_sketch, library_path,
+    lsq_lsqr, lsq_omega, lsq_probe_fma_rate, lsq_qr_r, lsq_qr_r_noalloc, lsq_residual, lsq_sketch, library_path,
     declared_functions,
 )

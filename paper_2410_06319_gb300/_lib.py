@@ -19,7 +19,7 @@ if not os.path.exists(library_path()):
 
 lib = ctypes.CDLL(library_path())
 
-PREC = {"auto": -1, "f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "bf16x3": 5}
+PREC = {"auto": -1, "f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "bf16x3": 5, "f64x2": 6}
 STATUS = {0: "LSQ_OK", 1: "LSQ_NOT_CONVERGED", -1: "LSQ_E_INVAL", -2: "LSQ_E_RANK",
           -3: "LSQ_E_BREAKDOWN", -4: "LSQ_E_NONFINITE", -5: "LSQ_E_CUDA", -6: "LSQ_E_TIMEOUT",
           -7: "LSQ_E_NOMEM", -8: "LSQ_E_UNSUPPORTED", -9: "LSQ_E_SIZE"}
@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
                 ("Y_in", ctypes.c_void_p), ("R_in", ctypes.c_void_p), ("x0_in", ctypes.c_void_p),
                 ("sketch_kchunk", ctypes.c_int64), ("wait_limit_us", ctypes.c_int32),
                 ("expire_sync", ctypes.c_int32), ("sketch_kind", ctypes.c_int32),
-                ("sparse_zeta", ctypes.c_int32)]
+                ("sparse_zeta", ctypes.c_int32), ("ops_escalated", ctypes.c_int32),
+                ("aug_alpha", ctypes.c_double), ("h_in_ur", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +58,7 @@ class Info(ctypes.Structure):
                 ("gmres_relres", ctypes.c_double * 32),
                 ("kern_ms", ctypes.c_double * 8), ("kern_launches", ctypes.c_int64 * 8),
                 ("arnoldi_second_passes", ctypes.c_int64), ("us_used", ctypes.c_int32),
-                ("sketches", ctypes.c_int32)]
+                ("sketches", ctypes.c_int32), ("aug_alpha", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,8 +103,9 @@ lib.lsq_lsir_batched.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Problem), ct
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
 lib.lsq_qr_r_noalloc.argtypes = [_P, _I64, _I64, ctypes.c_int, _P, _P, _P]
 lib.lsq_probe_fma_rate.argtypes = [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
+lib.lsq_residual.argtypes = [_P, _P, _P, _I64, _I64, ctypes.c_int, ctypes.POINTER(Opts), _P, _P, _P, _P]
 for _f in ("lsq_create", "lsq_destroy", "lsq_sketch", "lsq_qr_r", "lsq_lsqr", "lsq_lsir", "lsq_lsir_host", "lsq_ir_step",
-           "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc", "lsq_probe_fma_rate"):
+           "lsq_omega", "lsq_lsir_batched", "lsq_qr_r_noalloc", "lsq_probe_fma_rate", "lsq_residual"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -224,6 +226,13 @@ def lsq_ir_step(h, A, b, m, n, s, u_s, u_p, u_w, u_r, tol, seed, opts, R, x, r, 
     info = info if info is not None else Info()
     st = _check(h, lib.lsq_ir_step(*args, _ptr(R), _ptr(x), _ptr(r), ctypes.byref(info)), "lsq_ir_step")
     return st, info
+
+
+def lsq_residual(h, A, b, m, n, u_r, opts, x, r, f, g):
+    """[f; g] = [b - r - A x; -A^T r] in u_r (Alg. 2 refinement residual), device tensors."""
+    o = _opts(opts)
+    return _check(h, lib.lsq_residual(h.ptr, _ptr(A), _ptr(b), m, n, _prec(u_r), ctypes.byref(o), _ptr(x),
+                                      _ptr(r), _ptr(f), _ptr(g)), "lsq_residual")
 
 
 def _host_ptr(x):

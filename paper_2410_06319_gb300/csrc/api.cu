@@ -201,6 +201,7 @@ struct Ctx {
   cudaStream_t st;
   int nblk;        // pass grid
   int nblk2;       // vector-kernel grid
+  double alpha;    // scaling of the augmented system (Sec. 4.1); 1 unscaled
 };
 
 #define L(expr)         \
@@ -220,7 +221,10 @@ lsq_status validate(const Ctx& c, bool need_b) {
   if (fmt_of(c.us) < 0 && c.us != LSQ_AUTO) return LSQ_E_INVAL;
   if (c.up != LSQ_F32 && c.up != LSQ_F64) return LSQ_E_INVAL;
   if (c.uw != LSQ_F32 && c.uw != LSQ_F64) return LSQ_E_INVAL;
-  if (c.ur != LSQ_F64) return LSQ_E_INVAL;
+  if (c.ur != LSQ_F64 && c.ur != LSQ_F64X2) return LSQ_E_INVAL;
+  if (c.o.ops_escalated < 0 || c.o.ops_escalated > 1) return LSQ_E_INVAL;
+  if (c.o.h_in_ur < 0 || c.o.h_in_ur > 1) return LSQ_E_INVAL;
+  if (!(c.o.aug_alpha >= 0.0) || !std::isfinite(c.o.aug_alpha)) return LSQ_E_INVAL;
   if (c.o.gmres_maxit < 0 || c.o.gmres_maxit > kMaxGmres) return LSQ_E_INVAL;
   if (c.o.ir_maxit < 0 || c.o.ir_maxit > 32) return LSQ_E_INVAL;
   if (c.o.lsqr_maxit < 0) return LSQ_E_INVAL;
@@ -249,6 +253,7 @@ Ctx make_ctx(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t
   c.seed = seed;
   if (opts) c.o = *opts;
   else std::memset(&c.o, 0, sizeof(c.o));
+  c.alpha = c.o.aug_alpha > 0.0 ? c.o.aug_alpha : 1.0;
   c.lda = c.o.lda > 0 ? c.o.lda : n;
   c.lda32 = round_up(n, 4);
   // the sparse sign sketch is exact up to a 2^-47 fixed-point grid: it counts as an FP64
@@ -580,9 +585,14 @@ struct GmOut {
 
 // Alg. 2 (FGMRES): FGMRES on M_L^-1 Atilde M_R^-1 [dr; dz] = [f; h] (operator
 // products in TOP), x0 = 0; r += dr, x += dx.
+// With dd (TOP = double), the three products are taken in double-double (the Sec. 5
+// re-run for u = double): z = R^-1 v_bot, w_top = alpha v_top + A z, w_bot = R^-T A^T v_top,
+// each rounded once to FP64, and the Arnoldi step reads w_top as formed.
 template <typename TOP>
 GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, const double* f,
-                   const double* hv, double tol, int maxit, double* r, double* x) {
+                   const double* hv, double tol, int maxit, double* r, double* x, bool dd = false) {
+  static_assert(sizeof(TOP) == 4 || sizeof(TOP) == 8, "FP32 or FP64 products");
+  if (dd && sizeof(TOP) != 8) throw StatusFail{LSQ_E_INVAL};
   StageTimer tmr(c.h, ST_FGMRES);
   const int64_t m = c.m, n = c.n, ld = m + n;
   const int ldh = maxit + 1;
@@ -598,6 +608,11 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   TOP* P = static_cast<TOP*>(ws(c.h, "gmP", (size_t)c.nblk * n * sizeof(TOP)));
   TOP* sb = static_cast<TOP*>(ws(c.h, "gmS", (round_up(n, 4) + 4) * sizeof(TOP)));
   CK(cudaMemsetAsync(Zb, 0, (size_t)(round_up(n, 4) + 4) * (maxit + 1) * sizeof(TOP), c.st));
+  double* zlo = dd ? static_cast<double*>(ws(c.h, "gmZlo", (n + 4) * 8)) : nullptr;
+  double* Phi = dd ? static_cast<double*>(ws(c.h, "gmPhi", (size_t)c.nblk * n * 8)) : nullptr;
+  double* Plo = dd ? static_cast<double*>(ws(c.h, "gmPlo", (size_t)c.nblk * n * 8)) : nullptr;
+  double* th = dd ? static_cast<double*>(ws(c.h, "gmTh", (n + 4) * 8)) : nullptr;
+  double* tl = dd ? static_cast<double*>(ws(c.h, "gmTl", (n + 4) * 8)) : nullptr;
   CK(cudaMemsetAsync(sb, 0, (round_up(n, 4) + 4) * sizeof(TOP), c.st));
   double* H = static_cast<double*>(ws(c.h, "gmH", (size_t)ldh * maxit * 8, true));
   double* cs = static_cast<double*>(ws(c.h, "gmcs", (maxit + 1) * 8));
@@ -625,14 +640,40 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   hs.maxit = maxit;
   std::memcpy(c.h->h_pinned + 2048, &hs, sizeof(hs));
   CK(cudaMemcpyAsync(gst, c.h->h_pinned + 2048, sizeof(hs), cudaMemcpyHostToDevice, c.st));
-  L(launch_gm_rhs(f, hv, m, n, V, sqp, c.nblk2, c.st));
+  L(launch_gm_rhs(f, hv, m, n, V, sqp, c.nblk2, c.st, c.alpha));
   L(launch_gm_init(sqp, c.nblk2, gst, g, c.st));
   L(launch_gm_scale0(V, ld, gst, v32, m, c.nblk2, c.st));
   const int maxc = maxit + 1;
+  const Tri<double>* tri64 = reinterpret_cast<const Tri<double>*>(&tri);
   auto body = [&]() {
     for (int k = 0; k < kBatch; ++k) {
       const int* dn = &gst->done;
       const int* jp = &gst->j;
+      if (dd) {
+        {
+          KernTimer kt(c.h, K_TRSV, c.o.timing);
+          L(launch_dd_trsv(true, *tri64, V + m, nullptr, ld, reinterpret_cast<double*>(Zb), ldz, zlo, dn, jp,
+                           c.st));
+        }
+        {
+          KernTimer kt(c.h, K_FGM_PASS, c.o.timing);
+          const double* A64 = reinterpret_cast<const double*>(Aop);
+          L(launch_dd_rows(A64, ldop, m, n, reinterpret_cast<const double*>(Zb), zlo, ldz, V, c.alpha, ld, nullptr,
+                           0.0, 1.0, wv, dn, jp, c.h->num_sms, c.st));
+          L(launch_dd_cols(A64, ldop, m, n, V, ld, Phi, Plo, c.nblk, dn, jp, c.st));
+        }
+        L(launch_dd_colsum(Phi, Plo, c.nblk, n, 1.0, th, tl, dn, c.st));
+        {
+          KernTimer kt(c.h, K_TRSV, c.o.timing);
+          L(launch_dd_trsv(false, *tri64, th, tl, 0, wv + m, 0, nullptr, dn, nullptr, c.st));
+        }
+        {
+          KernTimer kt(c.h, K_ARNOLDI, c.o.timing);
+          L(launch_gm_step<double>(V, ld, wv, ld, m, nullptr, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, nullptr,
+                                   gbar, c.h->d_err, c.h->num_sms, c.st, wait_ns, c.alpha));
+        }
+        continue;
+      }
       {
         KernTimer kt(c.h, K_TRSV, c.o.timing);
         L((launch_trsv<TOP, double, TOP>(true, tri, V + m, 1.0, Zb, dn, c.st, jp, ld, ldz)));
@@ -652,16 +693,19 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
       {
         KernTimer kt(c.h, K_ARNOLDI, c.o.timing);
         L(launch_gm_step<TOP>(V, ld, wv, ld, m, az, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, v32, gbar,
-                              c.h->d_err, c.h->num_sms, c.st, wait_ns));
+                              c.h->d_err, c.h->num_sms, c.st, wait_ns, c.alpha));
       }
     }
   };
+  int64_t alpha_bits;
+  std::memcpy(&alpha_bits, &c.alpha, 8);
   CachedGraph* G =
       (c.o.timing || c.o.no_graph)
           ? nullptr
           : get_graph(c,
-                             graph_key(sizeof(TOP) == 4 ? "fgm32" : "fgm64",
-                                       {PV(Aop), ldop, m, n, maxit, (int64_t)wait_ns, PV(V), PV(Zb), PV(wv), PV(P),
+                             graph_key(sizeof(TOP) == 4 ? "fgm32" : (dd ? "fgm64dd" : "fgm64"),
+                                       {PV(Aop), ldop, m, n, maxit, (int64_t)wait_ns, alpha_bits, PV(V), PV(Zb),
+                                        PV(wv), PV(P), PV(zlo), PV(Phi), PV(Plo), PV(th), PV(tl),
                                         PV(az), PV(v32),
                                         PV(sb), PV(H), PV(cs), PV(sn), PV(g), PV(hh), PV(Dp), PV(sqp),
                                         PV(gst), PV(gbar), PV(tri.R), PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk,
@@ -685,7 +729,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   check_dev_error(c.h);   // an expired wait ends the solve here (its iterate is not used)
   StageTimer tu(c.h, ST_UPDATE);
   L(launch_gm_solve(gst, H, ldh, g, y, c.st));
-  L(launch_gm_apply<double>(V, ld, m, gst, y, r, p4, p4 + c.nblk2, c.nblk2, c.st));
+  L(launch_gm_apply<double>(V, ld, m, gst, y, r, p4, p4 + c.nblk2, c.nblk2, c.st, c.alpha));   // dr = alpha V_top y
   L(launch_gm_apply<TOP>(Zb, ldz, n, gst, y, x, p4 + 2 * c.nblk2, p4 + 3 * c.nblk2, c.nblk2, c.st));
   for (int k = 0; k < 4; ++k) L(launch_sum_partials(p4 + k * c.nblk2, c.nblk2, nrm + k, true, c.st));
   double hn[4];
@@ -704,18 +748,40 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
 }
 
 // The refinement loop of Alg. 2 from (x0, r0), FGMRES products in TOP.
+// Alg. 2 (refinement residual): f = b - r - A x and g = -A^T r in u_r (FP64, or double-double
+// rounded once to FP64; with glo, g is left as the double-double gv + glo).
+void stage_residual(Ctx& c, const double* x, const double* r, double* f, double* gv, double* glo = nullptr) {
+  const int64_t m = c.m, n = c.n;
+  double* P = static_cast<double*>(ws(c.h, "respblk", (size_t)c.nblk * n * 8));
+  if (c.ur == LSQ_F64X2) {
+    double* Plo = static_cast<double*>(ws(c.h, "respblk_lo", (size_t)c.nblk * n * 8));
+    KernTimer kt(c.h, K_RES_PASS, c.o.timing);
+    L(launch_dd_rows(c.A, c.lda, m, n, x, nullptr, 0, c.b, 1.0, 0, r, -1.0, -1.0, f, nullptr, nullptr,
+                     c.h->num_sms, c.st));
+    L(launch_dd_cols(c.A, c.lda, m, n, r, 0, P, Plo, c.nblk, nullptr, nullptr, c.st));
+    L(launch_dd_colsum(P, Plo, c.nblk, n, -1.0, gv, glo, nullptr, c.st));
+  } else {
+    {
+      KernTimer kt(c.h, K_RES_PASS, c.o.timing);
+      L(launch_pass_res(c.A, c.lda, m, n, x, r, c.b, f, P, c.nblk, c.st));
+    }
+    L((launch_colsum<double, double>(P, c.nblk, n, nullptr, 1.0, gv, nullptr, c.st)));
+  }
+}
+
+// dd: FGMRES products in double-double (TOP = double); gmax_min raises the FGMRES cap.
 template <typename TOP>
 bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const RCopies& rc, double* x, double* r,
-                  lsq_info* info) {
+                  lsq_info* info, bool dd = false, int gmax_min = 0) {
   const int64_t m = c.m, n = c.n;
   double* f = static_cast<double*>(ws(c.h, "ir_f", m * 8));
   double* gv = static_cast<double*>(ws(c.h, "ir_g", (n + 4) * 8));
   double* hv = static_cast<double*>(ws(c.h, "ir_h", (n + 4) * 8));
-  double* P = static_cast<double*>(ws(c.h, "respblk", (size_t)c.nblk * n * 8));
   const int irmax = c.o.ir_maxit > 0 ? c.o.ir_maxit : 30;
-  const int gmax = c.o.gmres_maxit > 0 ? c.o.gmres_maxit : 50;
+  const int gmax = std::max(c.o.gmres_maxit > 0 ? c.o.gmres_maxit : 50, gmax_min);
   const double gtol = c.o.gmres_tol > 0 ? c.o.gmres_tol : c.tol;
   const double u = unit_roundoff(c.uw);
+  info->aug_alpha = c.alpha;
   bool converged = false;
   double prev_dx = 0.0, prev_dr = 0.0;
   info->ir_its = 0;
@@ -723,14 +789,16 @@ bool stage_refine(Ctx& c, const TOP* Aop, int64_t ldop, const RCopies& rc, doubl
   for (int i = 0; i < irmax; ++i) {
     {
       StageTimer t(c.h, ST_RES);
-      {
-        KernTimer kt(c.h, K_RES_PASS, c.o.timing);
-        L(launch_pass_res(c.A, c.lda, m, n, x, r, c.b, f, P, c.nblk, c.st));
+      if (c.ur == LSQ_F64X2 && c.o.h_in_ur) {   // h = R^-T g in u_r (double-double), rounded
+        double* glo = static_cast<double*>(ws(c.h, "ir_glo", (n + 4) * 8));
+        stage_residual(c, x, r, f, gv, glo);
+        L(launch_dd_trsv(false, rc.f64, gv, glo, 0, hv, 0, nullptr, nullptr, nullptr, c.st));
+      } else {
+        stage_residual(c, x, r, f, gv);
+        L((launch_trsv<double, double, double>(false, rc.f64, gv, 1.0, hv, nullptr, c.st)));
       }
-      L((launch_colsum<double, double>(P, c.nblk, n, nullptr, 1.0, gv, nullptr, c.st)));
-      L((launch_trsv<double, double, double>(false, rc.f64, gv, 1.0, hv, nullptr, c.st)));
     }
-    GmOut go = stage_fgmres<TOP>(c, Aop, ldop, rc.get<TOP>(), f, hv, gtol, gmax, r, x);
+    GmOut go = stage_fgmres<TOP>(c, Aop, ldop, rc.get<TOP>(), f, hv, gtol, gmax, r, x, dd);
     info->gmres_its[i] = go.its;
     info->gmres_its_total += go.its;
     info->arnoldi_second_passes += go.reorth;
@@ -1098,23 +1166,25 @@ lsq_status lsq_lsir(lsq_handle* h, const double* A, const double* b, int64_t m, 
     // gets an even-stride, zero-padded copy first
     auto a64 = [&](int64_t* ld) -> const double* { return a64_rows(c, ld); };
     bool conv;
-    if (c.uw == LSQ_F32) {
+    if (c.uw == LSQ_F32 && !c.o.ops_escalated) {
       conv = stage_refine<float>(c, fr.a32, c.lda32, fr.rc, x, rr, inf);
     } else {
       int64_t ldp;
       const double* Ap = a64(&ldp);
-      conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf);
+      conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf, c.o.ops_escalated && c.uw == LSQ_F64);
     }
     const double kap = c.o.kappa_hint > 0 ? c.o.kappa_hint : inf->kappa_R_est;
-    if (!conv && !c.o.no_escalate && kap < 1.0 / unit_roundoff(c.us) && c.uw == LSQ_F32) {
-      // Sec. 5: re-run the refinement from (x0, r0) with u_A = u_L = u_R = u^2 (FP64 here)
+    if (!conv && !c.o.no_escalate && !c.o.ops_escalated && kap < 1.0 / unit_roundoff(c.us)) {
+      // Sec. 5: re-run the refinement from (x0, r0) with u_A = u_L = u_R = u^2: FP64 for u
+      // single; double-double (the paper's quad) with at most 80 FGMRES iterations for u double
       CK(cudaMemcpyAsync(x, x0, c.n * 8, cudaMemcpyDeviceToDevice, c.st));
       CK(cudaMemcpyAsync(rr, r0, c.m * 8, cudaMemcpyDeviceToDevice, c.st));
       inf->escalated = 1;
       inf->flags |= LSQ_INFO_ESCALATED;
       int64_t ldp;
       const double* Ap = a64(&ldp);
-      conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf);
+      if (c.uw == LSQ_F32) conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf);
+      else conv = stage_refine<double>(c, Ap, ldp, fr.rc, x, rr, inf, true, 80);
     }
     inf->ir_converged = conv ? 1 : 0;
     return conv ? LSQ_OK : LSQ_NOT_CONVERGED;
@@ -1140,15 +1210,27 @@ lsq_status lsq_ir_step(lsq_handle* h, const double* A, const double* b, int64_t 
     check_dev_error(c.h);   // a NaN or an infinity in A or b
     inf->kappa_R_est = kap;
     if (!(kap < INFINITY)) throw StatusFail{LSQ_E_RANK};
-    if (c.uw == LSQ_F32) {
+    if (c.uw == LSQ_F32 && !c.o.ops_escalated) {
       stage_refine<float>(c, a32, c.lda32, rc, x, r, inf);
     } else {
       int64_t ldp;
       const double* Ap = a64_rows(c, &ldp);
-      stage_refine<double>(c, Ap, ldp, rc, x, r, inf);
+      stage_refine<double>(c, Ap, ldp, rc, x, r, inf, c.o.ops_escalated && c.uw == LSQ_F64);
     }
     const double gtol = c.o.gmres_tol > 0 ? c.o.gmres_tol : c.tol;
     return inf->gmres_relres[0] <= gtol ? LSQ_OK : LSQ_NOT_CONVERGED;
+  });
+}
+
+lsq_status lsq_residual(lsq_handle* h, const double* A, const double* b, int64_t m, int64_t n, lsq_prec u_r,
+                        const lsq_opts* opts, const double* x, const double* r, double* f, double* g) {
+  Ctx c = make_ctx(h, A, b, m, n, n, LSQ_F64, LSQ_F64, LSQ_F64, u_r, 1.0, 0, opts);
+  lsq_status v = validate(c, true);
+  if (v != LSQ_OK) return v;
+  if (!x || !r || !f || !g) return LSQ_E_INVAL;
+  return run_guarded(h, nullptr, [&]() {
+    stage_residual(c, x, r, f, g);
+    return LSQ_OK;
   });
 }
 

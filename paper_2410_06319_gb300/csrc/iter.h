@@ -47,8 +47,9 @@ cudaError_t launch_dot(const double* x, const double* y, int64_t len, double* pa
 cudaError_t launch_sum_partials(const double* partial, int nblk, double* out, bool take_sqrt,
                                 cudaStream_t st);
 
+// V0 = [f; h / alpha] (alpha scales the augmented system, Sec. 4.1; 1 for the unscaled one)
 cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n, double* V0,
-                          double* sq_partial, int nblk, cudaStream_t s);
+                          double* sq_partial, int nblk, cudaStream_t s, double alpha = 1.0);
 cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s);
 cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
                              int nblk, cudaStream_t s);
@@ -62,11 +63,34 @@ template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
-                           int num_sms, cudaStream_t s, uint64_t wait_ns = 0);
+                           int num_sms, cudaStream_t s, uint64_t wait_ns = 0, double alpha = 1.0);
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
                             cudaStream_t s);
+// d += scale (B y) over the first st->j columns of B; partial sums of ||scale B y||^2 and ||d||^2
 template <typename TB>
 cudaError_t launch_gm_apply(const TB* B, int64_t ld, int64_t len, const GmState* st, const double* y,
-                            double* d, double* part_dd, double* part_d, int nblk, cudaStream_t s);
+                            double* d, double* part_dd, double* part_d, int nblk, cudaStream_t s,
+                            double scale = 1.0);
+
+// ---- double-double products (u_r = double-double; u_A = u_L = u_R = quad for u double)
+// out[i] = fl(cu u[i] + cw w[i] + sgn sum_k A[i][k] (zh[k] + zl[k])), i < m.  With jp, zh and u
+// are offset by (*jp) * zstr and (*jp) * ustr; u, w and zl may be null.  Skips when *done.
+cudaError_t launch_dd_rows(const double* A, int64_t lda, int64_t m, int64_t n, const double* zh,
+                           const double* zl, int64_t zstr, const double* u, double cu, int64_t ustr,
+                           const double* w, double cw, double sgn, double* out, const int* done, const int* jp,
+                           int num_sms, cudaStream_t st);
+// Phi/Plo[blk][k] = double-double partial of sum_i A[i][k] v[i] over the rows of block blk
+// (nblk blocks); v offset by (*jp) * vstr.
+cudaError_t launch_dd_cols(const double* A, int64_t lda, int64_t m, int64_t n, const double* v, int64_t vstr,
+                           double* Phi, double* Plo, int nblk, const int* done, const int* jp, cudaStream_t st);
+// out = sgn sum_blk P[blk] as double-double (out_lo != null) or rounded to FP64
+cudaError_t launch_dd_colsum(const double* Phi, const double* Plo, int nblk, int64_t n, double sgn,
+                             double* out_hi, double* out_lo, const int* done, cudaStream_t st);
+// x = R^-1 y (upper) or R^-T y in double-double (n <= 1024, one CTA); y = in_hi (+ in_lo),
+// in_hi offset by (*jp) * in_str and out_hi by (*jp) * out_str; out_lo null: out_hi holds
+// x rounded to FP64, else x = out_hi + out_lo.
+cudaError_t launch_dd_trsv(bool upper, const Tri<double>& f, const double* in_hi, const double* in_lo,
+                           int64_t in_str, double* out_hi, int64_t out_str, double* out_lo, const int* done,
+                           const int* jp, cudaStream_t st);
 
 }  // namespace lsq

@@ -939,6 +939,7 @@ struct GmStepArgs {
   int* err;
   int ldd;        // leading dimension of Dp (>= the grid size)
   uint64_t wait_ns;   // limit of each grid-sync wait
+  double alpha;       // w_top = alpha v_top + A z (Sec. 4.1 scaling; 1 unscaled)
 };
 
 // Dp[c][block] = sum over rows [r0, r1) of V[c][i] w[i] for c < ncols; Dp[ncols][block] = sum of w[i]^2.
@@ -1114,9 +1115,10 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs
   const int ldd = a.ldd;
   double* w = a.w;
   const double* V = a.V;
-  if (a.az) {   // w_top = v_top + A z (the pass left A z in az)
+  if (a.az) {   // w_top = alpha v_top + A z (the pass left A z in az); else w_top is formed
     const double* vj = V + (int64_t)j * a.ld;
-    for (int64_t i = r0 + threadIdx.x; i < min(r1, a.m); i += blockDim.x) w[i] = vj[i] + (double)a.az[i];
+    const double al = a.alpha;
+    for (int64_t i = r0 + threadIdx.x; i < min(r1, a.m); i += blockDim.x) w[i] = fma(al, vj[i], (double)a.az[i]);
     __syncthreads();
   }
   // ---- first pass: h and ||w||^2
@@ -1209,7 +1211,7 @@ template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
-                           int num_sms, cudaStream_t s, uint64_t wait_ns) {
+                           int num_sms, cudaStream_t s, uint64_t wait_ns, double alpha) {
   static_assert(sizeof(GmStepArgs<TAZ>) < 4096, "kernel parameter block");
   if (maxc > 128) return cudaErrorInvalidValue;
   auto kern = gm_step_kernel<TAZ>;
@@ -1224,6 +1226,7 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
   a.ldh = ldh;
   a.ldd = 2 * num_sms;   // the caller's Dp holds (maxc + 1) x 2 num_sms values
   a.wait_ns = wait_ns > 0 ? wait_ns : kWaitLimitNs;
+  a.alpha = alpha;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
   cfg.blockDim = dim3(kGmThreads);
@@ -1237,11 +1240,12 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
 }
 template cudaError_t launch_gm_step<float>(double*, int64_t, double*, int64_t, int64_t, const float*, GmState*,
                                            int, double*, double*, double*, double*, int, double*, double*,
-                                           double*, float*, unsigned*, int*, int, cudaStream_t, uint64_t);
+                                           double*, float*, unsigned*, int*, int, cudaStream_t, uint64_t,
+                                           double);
 template cudaError_t launch_gm_step<double>(double*, int64_t, double*, int64_t, int64_t, const double*,
                                             GmState*, int, double*, double*, double*, double*, int, double*,
                                             double*, double*, float*, unsigned*, int*, int, cudaStream_t,
-                                            uint64_t);
+                                            uint64_t, double);
 
 // y = H[:k,:k]^-1 g[:k]  (k = st->j): one warp, column-oriented back substitution
 __global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, const double* g, double* y) {
@@ -1266,7 +1270,7 @@ __global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, con
 template <typename TB>
 __global__ void gm_apply_kernel(const TB* __restrict__ B, int64_t ld, int64_t len, const GmState* st,
                                 const double* __restrict__ y, double* __restrict__ d,
-                                double* part_dd, double* part_d) {
+                                double* part_dd, double* part_d, double scale) {
   __shared__ double ys[128];
   __shared__ double red[33];
   const int k = st->j;
@@ -1277,6 +1281,7 @@ __global__ void gm_apply_kernel(const TB* __restrict__ B, int64_t ld, int64_t le
        i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (int c = 0; c < k; ++c) acc += (double)B[(int64_t)c * ld + i] * ys[c];
+    acc *= scale;
     const double nv = d[i] + acc;
     d[i] = nv;
     s1 += acc * acc;
@@ -1306,14 +1311,15 @@ cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const d
 }
 template <typename TB>
 cudaError_t launch_gm_apply(const TB* B, int64_t ld, int64_t len, const GmState* st, const double* y,
-                            double* d, double* part_dd, double* part_d, int nblk, cudaStream_t s) {
-  gm_apply_kernel<TB><<<nblk, 256, 0, s>>>(B, ld, len, st, y, d, part_dd, part_d);
+                            double* d, double* part_dd, double* part_d, int nblk, cudaStream_t s,
+                            double scale) {
+  gm_apply_kernel<TB><<<nblk, 256, 0, s>>>(B, ld, len, st, y, d, part_dd, part_d, scale);
   return cudaGetLastError();
 }
 template cudaError_t launch_gm_apply<double>(const double*, int64_t, int64_t, const GmState*, const double*,
-                                             double*, double*, double*, int, cudaStream_t);
+                                             double*, double*, double*, int, cudaStream_t, double);
 template cudaError_t launch_gm_apply<float>(const float*, int64_t, int64_t, const GmState*, const double*,
-                                            double*, double*, double*, int, cudaStream_t);
+                                            double*, double*, double*, int, cudaStream_t, double);
 
 cudaError_t launch_sum_partials(const double* partial, int nblk, double* out, bool take_sqrt,
                                 cudaStream_t st) {
@@ -1323,12 +1329,12 @@ cudaError_t launch_sum_partials(const double* partial, int nblk, double* out, bo
 
 // Copies [f; h] into V[:, 0] and leaves partial sums of squares.
 __global__ void gm_rhs_kernel(const double* __restrict__ f, const double* __restrict__ h, int64_t m,
-                              int64_t n, double* __restrict__ V0, double* sq_partial) {
+                              int64_t n, double* __restrict__ V0, double* sq_partial, double alpha) {
   __shared__ double red[33];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m + n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (i < m) ? f[i] : h[i - m];
+    const double v = (i < m) ? f[i] : (alpha == 1.0 ? h[i - m] : h[i - m] / alpha);
     V0[i] = v;
     s += v * v;
   }
@@ -1337,8 +1343,8 @@ __global__ void gm_rhs_kernel(const double* __restrict__ f, const double* __rest
 }
 
 cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n, double* V0,
-                          double* sq_partial, int nblk, cudaStream_t s) {
-  gm_rhs_kernel<<<nblk, 256, 0, s>>>(f, h, m, n, V0, sq_partial);
+                          double* sq_partial, int nblk, cudaStream_t s, double alpha) {
+  gm_rhs_kernel<<<nblk, 256, 0, s>>>(f, h, m, n, V0, sq_partial, alpha);
   return cudaGetLastError();
 }
 

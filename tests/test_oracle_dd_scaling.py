@@ -111,3 +111,19 @@ def test_quad_products_reproduce_table4_starred_rows(golden):
         assert abs(info["gmres_total"] - int(gm_total)) <= 5, (kappa, info)
         ex, er = exact.forward_errors(x, r, xstar, rstar)
         assert ex <= 4 * 2.0 ** -53 and er <= 4 * 2.0 ** -53
+
+
+def test_h_in_quad_reading_converges_at_least_as_fast():
+    """Alg. 2 marks h = R^-T g with u_r; solved that way (double-double from the
+    double-double g) the escalated refinement at kappa = 1e12 needs fewer steps than the
+    printed 2* (the FP64 solve of the default reading reproduces the printed count)."""
+    kappa = 1e12
+    P = paper_problem(kappa, seed=0)
+    xstar, rstar = exact.reference_solution(P.A, P.b)
+    Y = sketch.sketch(P.A, P.b, 400, 0, "f64")
+    R, c = qr.householder_qr(Y, 100)
+    x, r, info = lsir.lsir(P.A, P.b, R, qr.sketch_and_solve(R, c), 2.0 ** -53, 1e-12, w_dtype=np.float64,
+                           us=2.0 ** -53, kappa=kappa, xstar=xstar, rstar=rstar, h_ur=True)
+    assert info["escalated"] and info["converged"] and info["its"] <= 2
+    ex, er = exact.forward_errors(x, r, xstar, rstar)
+    assert ex <= 4 * 2.0 ** -53 and er <= 4 * 2.0 ** -53
