@@ -153,6 +153,8 @@ typedef struct lsq_opts {
                              double-double g (Alg. 2 marks this solve with u_r); 0 (default)
                              solves it in FP64 from g rounded to FP64, the reading under which
                              Table 4's escalated rows come out as printed */
+  int32_t batch_mode;     /* lsq_lsir_batched: 0 grouped launches when the batch allows them,
+                             1 one solve per problem on internal streams */
 } lsq_opts;
 
 /* Diagnostics of one call. */
@@ -329,13 +331,26 @@ lsq_status lsq_lsir_host(lsq_handle* h, const double* A, const double* b, int64_
 
 /*
  * lsq_lsir_batched -- lsq_lsir on nprob independent problems of uneven sizes
- * (probs is a HOST array of descriptors).  The problems run concurrently on
- * up to four internal streams (one worker thread and one workspace per
- * stream, created on first use and owned by the handle); problems with
- * m * n < 2^26 launch their iteration batches directly instead of capturing
- * CUDA graphs.  Each problem's result equals that of lsq_lsir on it alone.  statuses[i] and infos[i] (either
- * may be NULL) receive each problem's outcome.  Returns LSQ_OK if every problem
- * converged, LSQ_NOT_CONVERGED if some did not, or the first error status.
+ * (probs is a HOST array of descriptors).
+ * Grouped mode (the default when the batch is in its range: u_s in F16, BF16,
+ * E4M3, BF16X3; u_p F32 or F64; u_w F32; u_r F64; every n <= 256 and s <= 1024;
+ * the Gaussian sketch; no Y_in, R_in, ops_escalated or timing): every stage runs
+ * as one grouped launch over all problems -- the cast, one tensor-core sketch
+ * grid over every problem's (tile, column group, split) items with per-problem
+ * tensor maps and Philox keys, one QR CTA per problem, and one pass launch per
+ * LSQR or FGMRES iteration covering every problem's rows, with per-problem done
+ * flags -- and the iteration batches replay as CUDA graphs.  A problem's result
+ * does not depend on the rest of the batch; it matches lsq_lsir's on the same
+ * problem to rounding (the passes and the QR block the work differently).
+ * Per-problem mode (opts->batch_mode = 1, or a batch outside that range): the
+ * problems run concurrently on up to four internal streams (one worker thread
+ * and one workspace per stream, created on first use and owned by the handle),
+ * each exactly as lsq_lsir runs it alone.
+ * statuses[i] and infos[i] (either may be NULL) receive each problem's outcome;
+ * in grouped mode infos[i].stage_ms is not filled.  Returns LSQ_OK if every
+ * problem converged, LSQ_NOT_CONVERGED if some did not, or the first error
+ * status (a NaN or infinity in any problem's A or b: LSQ_E_NONFINITE for the
+ * whole grouped call).
  */
 lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* probs, lsq_prec u_s,
                             lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol,

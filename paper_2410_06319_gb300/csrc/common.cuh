@@ -93,6 +93,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t smem_dst, const void* tmap,
       : "memory");
 }
 
+// Grouped launches: problem p owns blocks [start[p], start[p + 1]) of the grid
+// (start: nprob + 1 prefix sums).  Returns the p that owns block b.
+__device__ __forceinline__ int group_of(const int* __restrict__ start, int nprob, int64_t b) {
+  int lo = 0, hi = nprob;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t smem_dst, const void* tmap, int32_t x,
                                             int32_t y, int32_t z, uint32_t bar) {
   asm volatile(

@@ -8,6 +8,34 @@
 
 namespace lsq {
 
+// Arguments of the register-blocked pass over A (one problem):
+//   PM_LSQR: q = A x + cu u_in ; u_out = q ; Pblk = A^T q per CTA ; sq = sum q^2 per CTA
+//   PM_FGM : az = A x ; Pblk = A^T v
+//   PM_RES : f = b - r - A x ; Pblk = A^T (-r)
+enum PassMode { PM_LSQR = 0, PM_FGM = 1, PM_RES = 2 };
+
+template <typename T>
+struct PassArgs {
+  const T* A;
+  int64_t lda, m;
+  int n, nv;             // nv = vectors per row (ceil(n / VW), padded rows for A32)
+  const T* x;            // multiplied vector, nv * VW entries (zero padded)
+  const T* uin;          // LSQR
+  T* uout;
+  const double* cu_ptr;
+  double cu_mul;
+  const T* v;            // FGMRES coefficient vector
+  T* az;                 // FGMRES: A x
+  const double* r;       // residual
+  const double* b;
+  double* f;
+  T* Pblk;
+  double* sq;
+  const int* done;
+  const int* jp;         // FGMRES: x and v are column (*jp) of their bases
+  int64_t xstr, vstr;
+};
+
 // LSQR (Paige & Saunders 1982) scalars, kept on the device so that iterations
 // run without host round trips; kernels of an iteration exit early once done.
 struct LsqrState {

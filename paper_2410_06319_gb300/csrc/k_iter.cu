@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "batch.h"
 #include "iter.h"
 #include "kernels.h"
 #include "trsv.cuh"
@@ -57,32 +58,8 @@ __device__ __forceinline__ void load_vec(const T* p, T (&o)[VW], bool streaming)
   for (int k = 0; k < VW; ++k) o[k] = e[k];
 }
 
-enum PassMode { PM_LSQR = 0, PM_FGM = 1, PM_RES = 2 };
-
-template <typename T>
-struct PassArgs {
-  const T* A;
-  int64_t lda, m;
-  int n, nv;             // nv = vectors per row (ceil(n / VW), padded rows for A32)
-  const T* x;            // multiplied vector, nv * VW entries (zero padded)
-  const T* uin;          // LSQR
-  T* uout;
-  const double* cu_ptr;
-  double cu_mul;
-  const T* v;            // FGMRES coefficient vector
-  T* az;                 // FGMRES: A x
-  const double* r;       // residual
-  const double* b;
-  double* f;
-  T* Pblk;
-  double* sq;
-  const int* done;
-  const int* jp;         // FGMRES: x and v are column (*jp) of their bases
-  int64_t xstr, vstr;
-};
-
 template <typename T, int VW, int VPL, int MODE>
-__global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
+__device__ __forceinline__ void pass_body(PassArgs<T> p, int64_t blk, int64_t nblk) {
   if (p.done && *p.done) return;
   if (p.jp) {
     const int64_t j = *p.jp;
@@ -93,7 +70,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
   T* red = reinterpret_cast<T*>(pass_smem);          // [8 warps][nv * VW]
   __shared__ double sqred[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * 8 + warp, tw = (int64_t)gridDim.x * 8;
+  const int64_t gw = blk * 8 + warp, tw = nblk * 8;
   T xv[VPL][VW], acc[VPL][VW];
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
@@ -192,13 +169,18 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
     T s = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s += red[w * width + c];
-    p.Pblk[(int64_t)blockIdx.x * p.n + c] = s;
+    p.Pblk[blk * p.n + c] = s;
   }
   if (MODE == PM_LSQR && threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += sqred[w];
-    p.sq[blockIdx.x] = s;
+    p.sq[blk] = s;
   }
+}
+
+template <typename T, int VW, int VPL, int MODE>
+__global__ void __launch_bounds__(256) pass_kernel(PassArgs<T> p) {
+  pass_body<T, VW, VPL, MODE>(p, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------ bulk-streamed passes
@@ -593,12 +575,12 @@ cudaError_t launch_pass_res(const double* A, int64_t lda, int64_t m, int64_t n, 
 
 // ------------------------------------------------------------ column sums
 template <typename TP, typename TO>
-__global__ void colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, const double* scale_ptr,
-                              double scale_mul, TO* __restrict__ out, const int* done) {
+__device__ __forceinline__ void colsum_body(const TP* __restrict__ P, int nblk, int64_t n, const double* scale_ptr,
+                                            double scale_mul, TO* __restrict__ out, const int* done, int64_t bx) {
   if (done && *done) return;
   __shared__ double part[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+  const int64_t c = bx * 32 + tx;
   double s = 0.0;
   if (c < n)
     for (int b = ty; b < nblk; b += 32) s += (double)P[(int64_t)b * n + c];
@@ -610,6 +592,12 @@ __global__ void colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, con
     const double sc = (scale_ptr ? *scale_ptr : 1.0) * scale_mul;
     out[c] = (TO)(t * sc);
   }
+}
+
+template <typename TP, typename TO>
+__global__ void colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, const double* scale_ptr,
+                              double scale_mul, TO* __restrict__ out, const int* done) {
+  colsum_body<TP, TO>(P, nblk, n, scale_ptr, scale_mul, out, done, blockIdx.x);
 }
 
 template <typename TP, typename TO>
@@ -646,8 +634,8 @@ template cudaError_t launch_pass_lsqr_any<double>(const double*, int64_t, int64_
 // beta = ||q|| from the per-CTA sums of squares (every CTA recomputes it);
 // out[c] = (A^T q)_c / beta.  Block 0 publishes beta and 1/beta.
 template <typename TP>
-__global__ void lsqr_colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, const double* sq,
-                                   LsqrState* st, bool init, TP* __restrict__ out) {
+__device__ __forceinline__ void lsqr_colsum_body(const TP* __restrict__ P, int nblk, int64_t n, const double* sq,
+                                                 LsqrState* st, bool init, TP* __restrict__ out, int64_t bx) {
   if (!init && st->done) return;
   __shared__ double part[32][33];
   __shared__ double beta_s;
@@ -666,12 +654,12 @@ __global__ void lsqr_colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n
   __syncthreads();
   const double beta = beta_s;
   const double us = beta > 0.0 ? 1.0 / beta : 0.0;
-  if (blockIdx.x == 0 && tid == 0) {
+  if (bx == 0 && tid == 0) {
     st->beta = beta;
     st->us = us;
     if (init) st->phibar = beta;
   }
-  const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+  const int64_t c = bx * 32 + tx;
   double sacc = 0.0;
   if (c < n)
     for (int b = ty; b < nblk; b += 32) sacc += (double)P[(int64_t)b * n + c];
@@ -684,13 +672,19 @@ __global__ void lsqr_colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n
   }
 }
 
+template <typename TP>
+__global__ void lsqr_colsum_kernel(const TP* __restrict__ P, int nblk, int64_t n, const double* sq,
+                                   LsqrState* st, bool init, TP* __restrict__ out) {
+  lsqr_colsum_body<TP>(P, nblk, n, sq, st, init, out, blockIdx.x);
+}
+
 // One CTA: vt = R^-T s ; (init) alpha v = vt, w = v, z = 0 ; (iteration)
 // alpha v = vt - beta v, plane rotation, z += (phi/rho) w, w = v - (theta/rho) w,
 // stopping tests ; then t = R^-1 v for the next pass.
 template <typename T>
-__global__ void __launch_bounds__(kTrsvThreads)
-    lsqr_step_kernel(Tri<T> f, const T* __restrict__ s, T* __restrict__ v, T* __restrict__ w,
-                     T* __restrict__ z, T* __restrict__ t, LsqrState* st, bool init) {
+__device__ __forceinline__ void lsqr_step_body(const Tri<T>& f, const T* __restrict__ s, T* __restrict__ v,
+                                               T* __restrict__ w, T* __restrict__ z, T* __restrict__ t,
+                                               LsqrState* st, bool init) {
   if (!init && st->done) return;
   __shared__ T xs[1024];
   __shared__ double red[33];
@@ -768,6 +762,13 @@ __global__ void __launch_bounds__(kTrsvThreads)
   __syncthreads();
   if (!block_trsv<T, true>(f.R, f.ld, f.DU, n, xs, step_buf, f.err)) return;    // t = R^-1 v
   for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = xs[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTrsvThreads)
+    lsqr_step_kernel(Tri<T> f, const T* __restrict__ s, T* __restrict__ v, T* __restrict__ w,
+                     T* __restrict__ z, T* __restrict__ t, LsqrState* st, bool init) {
+  lsqr_step_body<T>(f, s, v, w, z, t, st, init);
 }
 
 template <typename T>
@@ -951,7 +952,8 @@ struct GmStepArgs {
 constexpr int kGmRed = 160;   // doubles of the slice-sum buffer (>= max(16, G) x 8 with G <= 17)
 __device__ __forceinline__ void gm_partials(const double* __restrict__ V, int64_t ld,
                                             const double* __restrict__ w, int64_t r0, int64_t r1,
-                                            int ncols, double* Dp, int ldd, double* red /* [kGmRed] */) {
+                                            int ncols, double* Dp, int ldd, double* red /* [kGmRed] */,
+                                            int64_t blk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = (ncols + kGmGroup) / kGmGroup;   // groups covering ncols + 1 sums
   const int S = G >= nw ? 1 : nw / G;
@@ -994,7 +996,7 @@ __device__ __forceinline__ void gm_partials(const double* __restrict__ V, int64_
     const int g = c / kGmGroup, k = c % kGmGroup;
     double s = 0.0;
     for (int sl = 0; sl < S; ++sl) s += red[(sl * G + g) * kGmGroup + k];
-    Dp[(int64_t)c * ldd + blockIdx.x] = s;   // column-major: [column][block]
+    Dp[(int64_t)c * ldd + blk] = s;   // column-major: [column][block]
   }
   __syncthreads();
 }
@@ -1122,7 +1124,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs
     __syncthreads();
   }
   // ---- first pass: h and ||w||^2
-  gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red);
+  gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red, blockIdx.x);
   if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, a.wait_ns, hs, s_flag)) {
     if (threadIdx.x == 0) a.st->done = 1;   // later launches of the batch skip; the host reads err
     return;
@@ -1158,7 +1160,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs
     }
     for (; i < r1; i += step) w[i] = gm_row_update(V, a.ld, w[i], i, ncols, hs);
     __syncthreads();   // this CTA's rows of w1 are final for the second pass
-    gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red);
+    gm_partials(V, a.ld, w, r0, r1, ncols, a.Dp, ldd, red, blockIdx.x);
     if (!gm_sync_sums(a.Dp, ldd, a.hsum, ncols + 1, a.bar, a.bar + 1, a.err, a.wait_ns, hs, s_flag)) {
     if (threadIdx.x == 0) a.st->done = 1;   // later launches of the batch skip; the host reads err
     return;
@@ -1361,6 +1363,449 @@ __global__ void gm_scale0_kernel(double* V0, int64_t len, const GmState* st, flo
 cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
                              int nblk, cudaStream_t s) {
   gm_scale0_kernel<<<nblk, 256, 0, s>>>(V0, len, st, v32, m);
+  return cudaGetLastError();
+}
+
+
+// ============================================================ grouped (batched) forms
+// Problem p owns CTAs [start[p], start[p + 1]) of each launch; its block index and
+// block count within the launch stand in for blockIdx.x and gridDim.x of the
+// single-problem kernels above, whose bodies these call.
+
+template <typename T, int VW, int VPL, int MODE>
+__global__ void __launch_bounds__(256)
+    grouped_pass_kernel(const PassArgs<T>* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  const int pr = group_of(start, nprob, blockIdx.x);
+  pass_body<T, VW, VPL, MODE>(tab[pr], (int64_t)blockIdx.x - start[pr], (int64_t)start[pr + 1] - start[pr]);
+}
+
+template <typename T>
+cudaError_t launch_grouped_pass(int mode, int vw, int vpl, const PassArgs<T>* tab, const int* start,
+                                int64_t ctas, int nprob, size_t smem, cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  if (ctas > 2147483647LL) return cudaErrorInvalidValue;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = allow_dyn_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctas, 256, smem, st>>>(tab, start, nprob);
+    return cudaGetLastError();
+  };
+  if constexpr (sizeof(T) == 4) {
+    if (vw != 4 || vpl != 2) return cudaErrorInvalidValue;
+    if (mode == PM_LSQR) return go(grouped_pass_kernel<float, 4, 2, PM_LSQR>);
+    if (mode == PM_FGM) return go(grouped_pass_kernel<float, 4, 2, PM_FGM>);
+  } else {
+    if (vw != 1 || vpl != 8) return cudaErrorInvalidValue;
+    if (mode == PM_LSQR) return go(grouped_pass_kernel<double, 1, 8, PM_LSQR>);
+    if (mode == PM_FGM) return go(grouped_pass_kernel<double, 1, 8, PM_FGM>);
+    if (mode == PM_RES) return go(grouped_pass_kernel<double, 1, 8, PM_RES>);
+  }
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_grouped_pass<float>(int, int, int, const PassArgs<float>*, const int*, int64_t, int,
+                                                size_t, cudaStream_t);
+template cudaError_t launch_grouped_pass<double>(int, int, int, const PassArgs<double>*, const int*, int64_t, int,
+                                                 size_t, cudaStream_t);
+
+template <typename TP, typename TO>
+__global__ void grouped_colsum_kernel(const GColsum<TP, TO>* __restrict__ tab, const int* __restrict__ start,
+                                      int nprob) {
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GColsum<TP, TO>& g = tab[pr];
+  colsum_body<TP, TO>(g.P, g.nblk, g.n, g.scale_ptr, g.scale_mul, g.out, g.done, (int64_t)blockIdx.x - start[pr]);
+}
+
+template <typename TP, typename TO>
+cudaError_t launch_grouped_colsum(const GColsum<TP, TO>* tab, const int* start, int64_t ctas, int nprob,
+                                  cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  grouped_colsum_kernel<TP, TO><<<(unsigned)ctas, dim3(32, 32), 0, st>>>(tab, start, nprob);
+  return cudaGetLastError();
+}
+template cudaError_t launch_grouped_colsum<float, float>(const GColsum<float, float>*, const int*, int64_t, int,
+                                                         cudaStream_t);
+template cudaError_t launch_grouped_colsum<double, double>(const GColsum<double, double>*, const int*, int64_t,
+                                                           int, cudaStream_t);
+
+template <typename TP>
+__global__ void grouped_lsqr_colsum_kernel(const GLsqrColsum<TP>* __restrict__ tab, const int* __restrict__ start,
+                                           int nprob, bool init) {
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GLsqrColsum<TP>& g = tab[pr];
+  lsqr_colsum_body<TP>(g.P, g.nblk, g.n, g.sq, g.st, init, g.out, (int64_t)blockIdx.x - start[pr]);
+}
+
+template <typename TP>
+cudaError_t launch_grouped_lsqr_colsum(const GLsqrColsum<TP>* tab, const int* start, int64_t ctas, int nprob,
+                                       bool init, cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  grouped_lsqr_colsum_kernel<TP><<<(unsigned)ctas, dim3(32, 32), 0, st>>>(tab, start, nprob, init);
+  return cudaGetLastError();
+}
+template cudaError_t launch_grouped_lsqr_colsum<float>(const GLsqrColsum<float>*, const int*, int64_t, int, bool,
+                                                       cudaStream_t);
+
+template <typename T>
+__global__ void __launch_bounds__(kTrsvThreads)
+    grouped_lsqr_step_kernel(const GLsqrStep<T>* __restrict__ tab, bool init) {
+  const GLsqrStep<T>& g = tab[blockIdx.x];
+  lsqr_step_body<T>(g.f, g.s, g.v, g.w, g.z, g.t, g.st, init);
+}
+
+template <typename T>
+cudaError_t launch_grouped_lsqr_step(const GLsqrStep<T>* tab, int nprob, bool init, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  const size_t smem = TrsvSmem<T>::bytes;
+  cudaError_t e = allow_dyn_smem(grouped_lsqr_step_kernel<T>, smem);
+  if (e != cudaSuccess) return e;
+  grouped_lsqr_step_kernel<T><<<(unsigned)nprob, kTrsvThreads, smem, st>>>(tab, init);
+  return cudaGetLastError();
+}
+template cudaError_t launch_grouped_lsqr_step<float>(const GLsqrStep<float>*, int, bool, cudaStream_t);
+
+template <typename TX, typename TY, typename TO>
+__global__ void grouped_axpby_kernel(const GAxpby<TX, TY, TO>* __restrict__ tab, const int* __restrict__ start,
+                                     int nprob) {
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GAxpby<TX, TY, TO>& g = tab[pr];
+  if (g.done && *g.done) return;
+  const int64_t i = ((int64_t)blockIdx.x - start[pr]) * blockDim.x + threadIdx.x;
+  if (i >= g.len) return;
+  double v = (double)g.x[i] * g.a;
+  if (g.y) v += (double)g.y[i] * g.b;
+  g.out[i] = (TO)v;
+}
+
+template <typename TX, typename TY, typename TO>
+cudaError_t launch_grouped_axpby(const GAxpby<TX, TY, TO>* tab, const int* start, int64_t ctas, int nprob,
+                                 cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  grouped_axpby_kernel<TX, TY, TO><<<(unsigned)ctas, 256, 0, st>>>(tab, start, nprob);
+  return cudaGetLastError();
+}
+template cudaError_t launch_grouped_axpby<double, double, float>(const GAxpby<double, double, float>*, const int*,
+                                                                 int64_t, int, cudaStream_t);
+template cudaError_t launch_grouped_axpby<float, double, double>(const GAxpby<float, double, double>*, const int*,
+                                                                 int64_t, int, cudaStream_t);
+template cudaError_t launch_grouped_axpby<double, double, double>(const GAxpby<double, double, double>*,
+                                                                  const int*, int64_t, int, cudaStream_t);
+
+// ||x|| by one CTA per problem
+__global__ void grouped_norm_kernel(const GNorm* __restrict__ tab) {
+  __shared__ double red[33];
+  const GNorm& g = tab[blockIdx.x];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < g.len; i += blockDim.x) s += g.x[i] * g.x[i];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) *g.out = sqrt(s);
+}
+
+cudaError_t launch_grouped_norm(const GNorm* tab, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  grouped_norm_kernel<<<(unsigned)nprob, 1024, 0, st>>>(tab);
+  return cudaGetLastError();
+}
+
+// ---- FGMRES
+// rhs: V[:, 0] = [f; h / alpha] over the problem's CTAs, partial sums of squares
+__global__ void grouped_gm_rhs_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  __shared__ double red[33];
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GGm& g = tab[pr];
+  const int64_t blk = (int64_t)blockIdx.x - start[pr], nb = (int64_t)start[pr + 1] - start[pr];
+  double s = 0.0;
+  if (!*g.skip) {
+    for (int64_t i = blk * blockDim.x + threadIdx.x; i < g.m + g.n; i += nb * blockDim.x) {
+      const double v = (i < g.m) ? g.f[i] : (g.alpha == 1.0 ? g.h[i - g.m] : g.h[i - g.m] / g.alpha);
+      g.V[i] = v;
+      s += v * v;
+    }
+  }
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) g.sqp[blk] = s;
+}
+
+// beta = ||[f; h / alpha]|| (partials in CTA order), state reset, g = beta e_1
+__global__ void grouped_gm_init_kernel(const GGm* __restrict__ tab, const int* __restrict__ start) {
+  __shared__ double red[33];
+  const GGm& g = tab[blockIdx.x];
+  const int nb = start[blockIdx.x + 1] - start[blockIdx.x];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += g.sqp[b];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) {
+    GmState* st = g.st;
+    const double beta = sqrt(s);
+    st->beta0 = beta;
+    st->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->j = 0;
+    st->relres = beta > 0.0 ? 1.0 : 0.0;
+    st->reorth = 0;
+    st->nreorth = 0;
+    st->done = (*g.skip || beta == 0.0 || st->maxit <= 0) ? 1 : 0;
+    g.g[0] = beta;
+  }
+}
+
+__global__ void grouped_gm_scale0_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GGm& g = tab[pr];
+  if (g.st->done) return;
+  const int64_t blk = (int64_t)blockIdx.x - start[pr], nb = (int64_t)start[pr + 1] - start[pr];
+  const double sc = g.st->inv_h;
+  for (int64_t i = blk * blockDim.x + threadIdx.x; i < g.m + g.n; i += nb * blockDim.x) {
+    const double v = g.V[i] * sc;
+    g.V[i] = v;
+    if (g.v32 && i < g.m) g.v32[i] = (float)v;
+  }
+}
+
+cudaError_t launch_grouped_gm_init(const GGm* tab, const int* start, int64_t ctas, int nprob, cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  grouped_gm_rhs_kernel<<<(unsigned)ctas, 256, 0, st>>>(tab, start, nprob);
+  grouped_gm_init_kernel<<<(unsigned)nprob, 256, 0, st>>>(tab, start);
+  grouped_gm_scale0_kernel<<<(unsigned)ctas, 256, 0, st>>>(tab, start, nprob);
+  return cudaGetLastError();
+}
+
+// Arnoldi, phase A (second = 0): w_top = alpha v_top + A z (unless the pass formed it), then
+// the partials of V^T w and ||w||^2 over the CTA's rows; phase A' (second = 1, problems
+// whose first pass lost more than half of ||w||^2): the same partials of w1.
+__global__ void __launch_bounds__(kGmThreads)
+    garn_partials_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int nprob, int second) {
+  __shared__ double red[kGmRed];
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GGm& g = tab[pr];
+  const GmState* st = g.st;
+  if (st->done || (second && !st->reorth)) return;
+  const int j = st->j, ncols = j + 1;
+  const int64_t blk = (int64_t)blockIdx.x - start[pr], nb = (int64_t)start[pr + 1] - start[pr];
+  const int64_t len = g.m + g.n, chunk = (len + nb - 1) / nb;
+  const int64_t r0 = blk * chunk, r1 = min(len, r0 + chunk);
+  if (!second && g.az) {
+    const double* vj = g.V + (int64_t)j * g.ld;
+    const double al = g.alpha;
+    for (int64_t i = r0 + threadIdx.x; i < min(r1, g.m); i += blockDim.x) {
+      const double azi = g.az_f32 ? (double)static_cast<const float*>(g.az)[i] : static_cast<const double*>(g.az)[i];
+      g.w[i] = fma(al, vj[i], azi);
+    }
+    __syncthreads();
+  }
+  gm_partials(g.V, g.ld, g.w, r0, r1, ncols, g.Dp, (int)nb, red, blk);
+}
+
+// phase B / B' (one CTA per problem): column sums of the partials in block order, then the
+// twice-is-enough test (first pass) and the squared norm of the new column
+__global__ void __launch_bounds__(kGmThreads)
+    garn_reduce_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int second) {
+  const GGm& g = tab[blockIdx.x];
+  GmState* st = g.st;
+  if (st->done || (second && !st->reorth)) return;
+  const int j = st->j, ncols = j + 1;
+  const int nb = start[blockIdx.x + 1] - start[blockIdx.x];
+  double* hs = second ? g.hs2 : g.hs1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c <= ncols; c += nw) {
+    const double* col = g.Dp + (int64_t)c * nb;
+    double t0 = 0.0, t1 = 0.0;
+    int q = lane;
+    for (; q + 32 < nb; q += 64) {
+      t0 += col[q];
+      t1 += col[q + 32];
+    }
+    if (q < nb) t0 += col[q];
+    const double tt = warp_sum(t0 + t1);
+    if (lane == 0) hs[c] = tt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q = 0.0;
+    for (int c = 0; c < ncols; ++c) q = fma(hs[c], hs[c], q);
+    const double wn2 = hs[ncols];
+    if (!second) {
+      const int re = q > 0.5 * wn2 ? 1 : 0;
+      st->reorth = re;
+      st->nreorth += re;
+      const double hn2 = wn2 - q;
+      g.hs1[ncols + 1] = hn2 > 0.0 ? hn2 : 0.0;   // used when there is no second pass
+    } else {
+      const double hn2 = wn2 - q;
+      g.hs2[ncols + 1] = hn2 > 0.0 ? hn2 : 0.0;
+    }
+  }
+}
+
+// phase C1 (second pass problems): w1 = w - V h over the CTA's rows
+__global__ void __launch_bounds__(kGmThreads)
+    garn_sub_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  __shared__ double hs[130];
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GGm& g = tab[pr];
+  const GmState* st = g.st;
+  if (st->done || !st->reorth) return;
+  const int j = st->j, ncols = j + 1;
+  const int64_t blk = (int64_t)blockIdx.x - start[pr], nb = (int64_t)start[pr + 1] - start[pr];
+  const int64_t len = g.m + g.n, chunk = (len + nb - 1) / nb;
+  const int64_t r0 = blk * chunk, r1 = min(len, r0 + chunk);
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = g.hs1[c];
+  __syncthreads();
+  const int64_t step = blockDim.x;
+  int64_t i = r0 + threadIdx.x;
+  for (; i + step < r1; i += 2 * step) {
+    double wa = g.w[i], wb = g.w[i + step];
+    gm_row_update2(g.V, g.ld, i, i + step, ncols, hs, wa, wb);
+    g.w[i] = wa;
+    g.w[i + step] = wb;
+  }
+  for (; i < r1; i += step) g.w[i] = gm_row_update(g.V, g.ld, g.w[i], i, ncols, hs);
+}
+
+// phase C: v_{j+1} = (w - V h) / ||w - V h|| over the CTA's rows (h of the last pass)
+__global__ void __launch_bounds__(kGmThreads)
+    garn_newcol_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  __shared__ double hs[130];
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GGm& g = tab[pr];
+  const GmState* st = g.st;
+  if (st->done) return;
+  const int j = st->j, ncols = j + 1;
+  const double* hsrc = st->reorth ? g.hs2 : g.hs1;
+  const int64_t blk = (int64_t)blockIdx.x - start[pr], nb = (int64_t)start[pr + 1] - start[pr];
+  const int64_t len = g.m + g.n, chunk = (len + nb - 1) / nb;
+  const int64_t r0 = blk * chunk, r1 = min(len, r0 + chunk);
+  for (int c = threadIdx.x; c <= ncols; c += blockDim.x) hs[c] = hsrc[c == ncols ? ncols + 1 : c];
+  __syncthreads();
+  const double hn2 = hs[ncols];
+  const double inv = hn2 > 0.0 ? 1.0 / sqrt(hn2) : 0.0;
+  double* vn = g.V + (int64_t)(j + 1) * g.ld;
+  const int64_t step = blockDim.x;
+  int64_t i = r0 + threadIdx.x;
+  for (; i + step < r1; i += 2 * step) {
+    double wa = g.w[i], wb = g.w[i + step];
+    gm_row_update2(g.V, g.ld, i, i + step, ncols, hs, wa, wb);
+    wa *= inv;
+    wb *= inv;
+    vn[i] = wa;
+    vn[i + step] = wb;
+    if (g.v32) {
+      if (i < g.m) g.v32[i] = (float)wa;
+      if (i + step < g.m) g.v32[i + step] = (float)wb;
+    }
+  }
+  for (; i < r1; i += step) {
+    const double v = gm_row_update(g.V, g.ld, g.w[i], i, ncols, hs) * inv;
+    vn[i] = v;
+    if (g.v32 && i < g.m) g.v32[i] = (float)v;
+  }
+}
+
+// phase D (one warp per problem): Hessenberg column h (+ h2), Givens step, j + 1
+__global__ void garn_finish_kernel(const GGm* __restrict__ tab) {
+  __shared__ double hcol[130];
+  const GGm& g = tab[blockIdx.x];
+  GmState* st = g.st;
+  if (st->done) return;
+  const int j = st->j, ncols = j + 1;
+  const int re = st->reorth;
+  for (int c = threadIdx.x; c < ncols; c += 32) hcol[c] = re ? g.hs1[c] + g.hs2[c] : g.hs1[c];
+  __syncwarp();
+  const double hn2 = re ? g.hs2[ncols + 1] : g.hs1[ncols + 1];
+  gm_finish_warp(hn2, st, hcol, g.H, g.ldh, g.cs, g.sn, g.g);
+}
+
+cudaError_t launch_grouped_arnoldi(const GGm* tab, const int* start, int64_t ctas, int nprob, cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  const unsigned nc = (unsigned)ctas, np = (unsigned)nprob;
+  garn_partials_kernel<<<nc, kGmThreads, 0, st>>>(tab, start, nprob, 0);
+  garn_reduce_kernel<<<np, kGmThreads, 0, st>>>(tab, start, 0);
+  garn_sub_kernel<<<nc, kGmThreads, 0, st>>>(tab, start, nprob);
+  garn_partials_kernel<<<nc, kGmThreads, 0, st>>>(tab, start, nprob, 1);
+  garn_reduce_kernel<<<np, kGmThreads, 0, st>>>(tab, start, 1);
+  garn_newcol_kernel<<<nc, kGmThreads, 0, st>>>(tab, start, nprob);
+  garn_finish_kernel<<<np, 32, 0, st>>>(tab);
+  return cudaGetLastError();
+}
+
+// update: y = H^-1 g (one warp per problem), then r += alpha V_top y, x += Z y over the
+// problem's CTAs with the partial sums of ||alpha V_top y||^2, ||r||^2, ||Z y||^2, ||x||^2
+__global__ void grouped_gm_solve_kernel(const GGm* __restrict__ tab) {
+  extern __shared__ double hsm[];   // k x k, column-major
+  __shared__ double rhs[130];
+  const GGm& g = tab[blockIdx.x];
+  if (*g.skip) return;
+  const int k = g.st->j, lane = threadIdx.x;
+  for (int c = 0; c < k; ++c)
+    for (int i = lane; i <= c; i += 32) hsm[c * k + i] = g.H[(int64_t)c * g.ldh + i];
+  for (int i = lane; i < k; i += 32) rhs[i] = g.g[i];
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    const double yi = rhs[i] / hsm[i * k + i];
+    __syncwarp();
+    for (int l = lane; l < i; l += 32) rhs[l] -= hsm[i * k + l] * yi;
+    if (lane == 0) g.y[i] = yi;
+    __syncwarp();
+  }
+}
+
+__global__ void grouped_gm_apply_kernel(const GGm* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  __shared__ double ys[128];
+  __shared__ double red[33];
+  const int pr = group_of(start, nprob, blockIdx.x);
+  const GGm& g = tab[pr];
+  const int64_t blk = (int64_t)blockIdx.x - start[pr], nb = (int64_t)start[pr + 1] - start[pr];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  if (!*g.skip) {
+    const int k = g.st->j;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = g.y[c];
+    __syncthreads();
+    for (int64_t i = blk * blockDim.x + threadIdx.x; i < g.m; i += nb * blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < k; ++c) acc += g.V[(int64_t)c * g.ld + i] * ys[c];
+      acc *= g.alpha;
+      const double nv = g.r[i] + acc;
+      g.r[i] = nv;
+      s[0] += acc * acc;
+      s[1] += nv * nv;
+    }
+    for (int64_t i = blk * blockDim.x + threadIdx.x; i < g.n; i += nb * blockDim.x) {
+      double acc = 0.0;
+      if (g.zb_f32)
+        for (int c = 0; c < k; ++c) acc += (double)static_cast<const float*>(g.Zb)[(int64_t)c * g.ldz + i] * ys[c];
+      else
+        for (int c = 0; c < k; ++c) acc += static_cast<const double*>(g.Zb)[(int64_t)c * g.ldz + i] * ys[c];
+      const double nv = g.x[i] + acc;
+      g.x[i] = nv;
+      s[2] += acc * acc;
+      s[3] += nv * nv;
+    }
+  }
+  for (int q = 0; q < 4; ++q) {
+    const double v = block_sum_d(s[q], red);
+    if (threadIdx.x == 0) g.p4[q * nb + blk] = v;
+  }
+}
+
+__global__ void grouped_gm_norms_kernel(const GGm* __restrict__ tab, const int* __restrict__ start) {
+  __shared__ double red[33];
+  const GGm& g = tab[blockIdx.x];
+  const int nb = start[blockIdx.x + 1] - start[blockIdx.x];
+  for (int q = 0; q < 4; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += g.p4[q * nb + b];
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) g.nrm[q] = s;
+  }
+}
+
+cudaError_t launch_grouped_gm_update(const GGm* tab, const int* start, int64_t ctas, int nprob,
+                                     cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  const size_t smem = (size_t)kMaxGmresBatch * kMaxGmresBatch * 8;
+  cudaError_t e = allow_dyn_smem(grouped_gm_solve_kernel, smem);
+  if (e != cudaSuccess) return e;
+  grouped_gm_solve_kernel<<<(unsigned)nprob, 32, smem, st>>>(tab);
+  grouped_gm_apply_kernel<<<(unsigned)ctas, 256, 0, st>>>(tab, start, nprob);
+  grouped_gm_norms_kernel<<<(unsigned)nprob, 256, 0, st>>>(tab, start);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "batch.h"
 #include "kernels.h"
 
 namespace lsq {
@@ -349,10 +350,9 @@ __global__ void __launch_bounds__(kQr64Threads, 1)
 
 // R (FP64, col-major, diag >= 0) and c from the factored work matrix.
 template <typename T>
-__global__ void qr_finalize_kernel(const T* __restrict__ W, int64_t s, int64_t n,
-                                   const double* __restrict__ diagR, double* __restrict__ R,
-                                   double* __restrict__ c) {
-  const int64_t j = blockIdx.x;          // column of R
+__device__ __forceinline__ void qr_finalize_body(const T* __restrict__ W, int64_t s, int64_t n,
+                                                 const double* __restrict__ diagR, double* __restrict__ R,
+                                                 double* __restrict__ c, int64_t j /* column of R */) {
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     const double sg = (diagR[i] < 0.0) ? -1.0 : 1.0;
     double v = 0.0;
@@ -361,6 +361,13 @@ __global__ void qr_finalize_kernel(const T* __restrict__ W, int64_t s, int64_t n
     if (R) R[j * n + i] = v * sg;
     if (c && j == 0) c[i] = (double)W[n * s + i] * sg;
   }
+}
+
+template <typename T>
+__global__ void qr_finalize_kernel(const T* __restrict__ W, int64_t s, int64_t n,
+                                   const double* __restrict__ diagR, double* __restrict__ R,
+                                   double* __restrict__ c) {
+  qr_finalize_body<T>(W, s, n, diagR, R, c, blockIdx.x);
 }
 
 // ------------------------------------------------------------ blocked variant
@@ -869,5 +876,77 @@ cudaError_t launch_qr(bool fp64, const double* Y, int64_t s, int64_t n, void* wo
     return run_qr64(Y, s, n, static_cast<double*>(work), aux, bar, R, c, err, num_sms, st);
   return run_qr<float>(Y, s, n, static_cast<float*>(work), aux, bar, R, c, err, num_sms, st);
 }
+
+
+// ============================================================ grouped (batched) QR
+// One 1024-thread CTA per problem (s <= 1024): the reflectors of qr_kernel, v in shared
+// memory, whole trailing columns per warp (lanes over rows, one warp sum per dot
+// product); the warp that updates column k+1 also sums its squares below the diagonal
+// for the next step's norm.  W (s x (n + 1), ld = s) stays in global memory.
+template <typename T>
+__global__ void __launch_bounds__(1024) grouped_qr_kernel(const GQr<T>* __restrict__ tab) {
+  const GQr<T>& g = tab[blockIdx.x];
+  const int64_t s = g.s, n = g.n;
+  T* W = g.W;
+  __shared__ T vs[1024];
+  __shared__ T red[33];
+  __shared__ T nrm_next;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t e = threadIdx.x; e < s * (n + 1); e += blockDim.x) W[e] = (T)g.Y[e];
+  __syncthreads();
+  T part = 0;
+  for (int64_t t = threadIdx.x; t < s; t += blockDim.x) part += W[t] * W[t];
+  T nn = block_sum_1024(part, red);
+  for (int64_t k = 0; k < n; ++k) {
+    const T* colk = W + k * s;
+    const T alpha = sqrt(nn);
+    const T x0 = colk[k];
+    const T sgn = (x0 >= T(0)) ? T(1) : T(-1);
+    const T scale = (alpha > T(0)) ? T(1) / (alpha * (alpha + fabs(x0))) : T(0);
+    if (threadIdx.x == 0) g.diagR[k] = (double)(-sgn * alpha);
+    const int64_t len = s - k;
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) vs[t] = (t == 0) ? x0 + sgn * alpha : colk[k + t];
+    __syncthreads();
+    for (int64_t j = k + 1 + warp; j <= n; j += nw) {
+      T* colj = W + j * s + k;
+      T d = 0;
+      for (int64_t t = lane; t < len; t += 32) d += vs[t] * colj[t];
+      const T wj = warp_sum(d) * scale;
+      T sq = 0;
+      for (int64_t t = lane; t < len; t += 32) {
+        const T val = colj[t] - wj * vs[t];
+        colj[t] = val;
+        if (t >= 1) sq += val * val;
+      }
+      if (j == k + 1) {
+        sq = warp_sum(sq);
+        if (lane == 0) nrm_next = sq;
+      }
+    }
+    __syncthreads();
+    nn = nrm_next;
+  }
+}
+
+template <typename T>
+__global__ void grouped_qr_finalize_kernel(const GQr<T>* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GQr<T>& g = tab[p];
+  qr_finalize_body<T>(g.W, g.s, g.n, g.diagR, g.R, g.c, (int64_t)blockIdx.x - start[p]);
+}
+
+template <typename T>
+cudaError_t launch_grouped_qr(const GQr<T>* tab, const int* col_start, int64_t col_ctas, int nprob, int64_t max_n,
+                              cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  (void)max_n;
+  grouped_qr_kernel<T><<<(unsigned)nprob, 1024, 0, st>>>(tab);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  grouped_qr_finalize_kernel<T><<<(unsigned)col_ctas, 256, 0, st>>>(tab, col_start, nprob);
+  return cudaGetLastError();
+}
+template cudaError_t launch_grouped_qr<float>(const GQr<float>*, const int*, int64_t, int, int64_t, cudaStream_t);
+template cudaError_t launch_grouped_qr<double>(const GQr<double>*, const int*, int64_t, int, int64_t, cudaStream_t);
 
 }  // namespace lsq

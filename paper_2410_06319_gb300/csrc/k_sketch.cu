@@ -14,6 +14,8 @@
 //  * reduce: FP64 sum of the split partials, times s^-1/2 and 2^-k_j.
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "cast.cuh"
 #include "common.cuh"
 #include "gauss.cuh"
@@ -87,11 +89,11 @@ __device__ __forceinline__ float f64bits_to_f32(uint64_t u) {
   return __double2float_rn(__longlong_as_double((long long)u));
 }
 
-__global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
-                                  const double* __restrict__ b, int64_t m, int64_t n,
-                                  unsigned long long* cmax, float* __restrict__ a32, int64_t lda32,
-                                  int64_t rows_per_block, int* err) {
-  const int64_t r0 = blockIdx.x * rows_per_block;
+__device__ __forceinline__ void colmax_a32_body(const double* __restrict__ A, int64_t lda,
+                                                const double* __restrict__ b, int64_t m, int64_t n,
+                                                unsigned long long* cmax, float* __restrict__ a32,
+                                                int64_t lda32, int64_t rows_per_block, int* err, int64_t blk) {
+  const int64_t r0 = blk * rows_per_block;
   const int64_t r1 = min(m, r0 + rows_per_block);
   const int64_t cend = a32 ? max(n + 1, lda32) : n + 1;
   const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
@@ -119,6 +121,13 @@ __global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
     // |v| bits at or above those of +infinity: an infinity or a NaN in the column
     if (c <= n && mx >= 0x7FF0000000000000ull) set_error(err, DEV_NONFINITE);
   }
+}
+
+__global__ void colmax_a32_kernel(const double* __restrict__ A, int64_t lda,
+                                  const double* __restrict__ b, int64_t m, int64_t n,
+                                  unsigned long long* cmax, float* __restrict__ a32, int64_t lda32,
+                                  int64_t rows_per_block, int* err) {
+  colmax_a32_body(A, lda, b, m, n, cmax, a32, lda32, rows_per_block, err, blockIdx.x);
 }
 
 cudaError_t launch_colmax_a32(const double* A, int64_t lda, const double* b, int64_t m, int64_t n,
@@ -190,12 +199,12 @@ __device__ __forceinline__ void cast_bits(uint64_t u, int k, uint32_t (&t)[3]) {
 // few MB (a K-major layout with m-long rows puts every row of a stage on its
 // own page once m is in the millions).
 template <int FMT>
-__global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
-                                      const double* __restrict__ b, int64_t m, int64_t n,
-                                      const int* __restrict__ kexp, void* __restrict__ Bt,
-                                      int64_t plane_rows, int planes) {
+__device__ __forceinline__ void cast_transpose_body(const double* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ b, int64_t m, int64_t n,
+                                                    const int* __restrict__ kexp, void* __restrict__ Bt,
+                                                    int64_t plane_rows, int planes, int64_t bx, int64_t by) {
   __shared__ uint64_t tile[32][33];
-  const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int64_t j0 = bx * 32, c0 = by * 32;
   const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
   const uint64_t* bu = reinterpret_cast<const uint64_t*>(b);
   for (int r = threadIdx.y; r < 32; r += 8) {
@@ -239,6 +248,14 @@ __global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
   }
 }
 
+template <int FMT>
+__global__ void cast_transpose_kernel(const double* __restrict__ A, int64_t lda,
+                                      const double* __restrict__ b, int64_t m, int64_t n,
+                                      const int* __restrict__ kexp, void* __restrict__ Bt,
+                                      int64_t plane_rows, int planes) {
+  cast_transpose_body<FMT>(A, lda, b, m, n, kexp, Bt, plane_rows, planes, blockIdx.x, blockIdx.y);
+}
+
 int64_t bt_blocks(int64_t m) { return (m + kBtBlock - 1) / kBtBlock; }
 
 size_t bt_bytes(int fmt, int64_t m, int64_t plane_rows) {
@@ -279,19 +296,6 @@ __host__ __device__ constexpr int sk_threads(bool defer) {
   return (2 + kSkGenWarps + (defer ? 0 : kSkFixWarps)) * 32;
 }
 
-struct SketchTcArgs {
-  int64_t s, m, ncols, kchunk, s_pad;
-  int bn, nsub, tmem_cols, rows_per_plane;
-  uint32_t k0, k1;
-  float* partial;
-  int* err;
-  // deferred mode: per generator warp a list of the (a, b) pairs whose FP32
-  // estimate was too close to a rounding midpoint, packed (data row << 16 | sketch row)
-  uint64_t* rec;
-  uint32_t* rec_cnt;
-  uint32_t rec_cap;
-};
-
 __device__ __forceinline__ void fix_barrier() {
   asm volatile("bar.sync 1, %0;" ::"n"(kSkFixThreads) : "memory");
 }
@@ -323,9 +327,14 @@ __device__ __forceinline__ uint32_t swz_chunk(int row, int kc) {
 // multiplied with the FP32 estimates at once and those pairs are recorded;
 // sketch_fix_kernel then evaluates them in FP64 and adds (fl_s(G) - estimate) times
 // the matching rows of A_s to the partials, which gives the same product.
-template <int FMT, int STAGES, int ROWB, int NT, bool DEFER>
+//
+// GROUPED: one launch for a batch of problems.  CTA b belongs to the problem p with
+// grp.start[p] <= b < grp.start[p + 1]; its local index gives (tile, column group, split)
+// in that problem's grid; the problem's arguments come from grp.tab[p] and its tensor map
+// from grp.maps[p] (global memory, written by the host before the launch).
+template <int FMT, int STAGES, int ROWB, int NT, bool DEFER, bool GROUPED>
 __global__ void __launch_bounds__(sk_threads(DEFER), 1)
-    sketch_tc_kernel(const __grid_constant__ CUtensorMap tmB, const SketchTcArgs a) {
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap tmB, const SketchTcArgs a_in, const SketchGroup grp) {
   constexpr int GF = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;   // format of the sketch operand
   constexpr int EB = (GF == FMT_E4M3) ? 1 : 2;                // bytes per element
   constexpr int BK = ROWB / EB;                               // K elements per stage
@@ -338,6 +347,20 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t mt = blockIdx.x, ng = blockIdx.y, split = blockIdx.z;
+  const CUtensorMap* tmp = &tmB;
+  int gp = 0;
+  if constexpr (GROUPED) {
+    gp = group_of(grp.start, grp.nprob, blockIdx.x);
+    const int64_t local = (int64_t)blockIdx.x - grp.start[gp];
+    const int mtl = grp.tab[gp].mtiles, ngl = grp.tab[gp].ngroups;
+    mt = local % mtl;
+    ng = (local / mtl) % ngl;
+    split = local / ((int64_t)mtl * ngl);
+    tmp = grp.maps + gp;
+  }
+  const SketchTcArgs a = GROUPED ? grp.tab[gp] : a_in;
   const uint32_t b_bytes = (uint32_t)a.bn * ROWB;              // one plane of Bt per stage
   const uint32_t stage_bytes = S_BYTES + NT * b_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
@@ -350,8 +373,6 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
   const uint32_t genned0 = smem_u32(bars + 2 * STAGES), fixed0 = smem_u32(bars + 3 * STAGES);
   const uint32_t done_bar = smem_u32(bars + 4 * STAGES);
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t mt = blockIdx.x, ng = blockIdx.y, split = blockIdx.z;
   const int64_t k_begin = split * a.kchunk;
   const int64_t k_end = min(a.m, k_begin + a.kchunk);
   const int nk = (int)((k_end - k_begin + BK - 1) / BK);
@@ -380,7 +401,12 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
   if (warp == 0) {
     // ---------------- TMA producer: NT planes x nsub boxes of [chunk rows x ROWB bytes]
     if (lane == 0) {
-      prefetch_tmap(&tmB);
+      if constexpr (GROUPED) {   // the map was written through the generic proxy
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(tmp))
+                     : "memory");
+      }
+      prefetch_tmap(tmp);
       for (int ks = 0; ks < nk; ++ks) {
         const int st = ks % STAGES;
         const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
@@ -391,7 +417,7 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
         const int32_t kin = (int32_t)(kx % kBtBlock), kblk = (int32_t)(kx / kBtBlock);
         for (int t = 0; t < NT; ++t)
           for (int c = 0; c < a.nsub; ++c)
-            tma_load_3d(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB), &tmB, kin,
+            tma_load_3d(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB), tmp, kin,
                         (int32_t)(t * a.rows_per_plane + ng * a.bn + c * chunk), kblk, full0 + 8 * st);
       }
     }
@@ -665,17 +691,29 @@ template <int FMT, int STAGES, int ROWB, int NT>
 static cudaError_t launch_tc_inst(const SketchPlan& p, const CUtensorMap& tm, const SketchTcArgs& a,
                                   cudaStream_t st) {
   dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
+  const SketchGroup none{};
   if (a.rec) {
-    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, true>;
+    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, true, false>;
     cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, sk_threads(true), p.smem, st>>>(tm, a);
+    kern<<<grid, sk_threads(true), p.smem, st>>>(tm, a, none);
   } else {
-    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, false>;
+    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, false, false>;
     cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, sk_threads(false), p.smem, st>>>(tm, a);
+    kern<<<grid, sk_threads(false), p.smem, st>>>(tm, a, none);
   }
+  return cudaGetLastError();
+}
+
+template <int FMT, int STAGES, int ROWB, int NT>
+static cudaError_t launch_tc_grouped_inst(const SketchGroup& g, int64_t ctas, size_t smem, cudaStream_t st) {
+  auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, false, true>;
+  cudaError_t e = allow_dyn_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  kern<<<(unsigned)ctas, sk_threads(false), smem, st>>>(unused, SketchTcArgs{}, g);
   return cudaGetLastError();
 }
 
@@ -691,6 +729,8 @@ cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_
   a.bn = p.bn;
   a.nsub = p.nsub;
   a.rows_per_plane = p.ngroups * p.bn;
+  a.mtiles = p.mtiles;
+  a.ngroups = p.ngroups;
   int tc = 32;
   while (tc < p.bn) tc <<= 1;
   a.tmem_cols = tc;
@@ -711,6 +751,46 @@ cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_
                                : launch_tc_inst<FMT_E4M3, 2, 128, 1>(p, tm, a, st);
     case FMT_BF16X3: return four ? launch_tc_inst<FMT_BF16X3, 4, 64, 3>(p, tm, a, st)
                                  : launch_tc_inst<FMT_BF16X3, 2, 64, 3>(p, tm, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+SketchTcArgs sketch_tc_args(const SketchPlan& p, uint64_t seed, float* partial, int* err) {
+  SketchTcArgs a{};
+  a.s = p.s;
+  a.m = p.m;
+  a.ncols = p.ncols;
+  a.kchunk = p.kchunk;
+  a.s_pad = p.s_pad;
+  a.bn = p.bn;
+  a.nsub = p.nsub;
+  a.rows_per_plane = p.ngroups * p.bn;
+  a.mtiles = p.mtiles;
+  a.ngroups = p.ngroups;
+  int tc = 32;
+  while (tc < p.bn) tc <<= 1;
+  a.tmem_cols = tc;
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.partial = partial;
+  a.err = err;
+  return a;
+}
+
+cudaError_t launch_sketch_tc_grouped(int fmt, int stages, const SketchGroup& g, int64_t ctas, size_t smem,
+                                     cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  if (ctas > 2147483647LL) return cudaErrorInvalidValue;
+  const bool four = stages == 4;
+  switch (fmt) {
+    case FMT_F16: return four ? launch_tc_grouped_inst<FMT_F16, 4, 128, 1>(g, ctas, smem, st)
+                              : launch_tc_grouped_inst<FMT_F16, 2, 128, 1>(g, ctas, smem, st);
+    case FMT_BF16: return four ? launch_tc_grouped_inst<FMT_BF16, 4, 128, 1>(g, ctas, smem, st)
+                               : launch_tc_grouped_inst<FMT_BF16, 2, 128, 1>(g, ctas, smem, st);
+    case FMT_E4M3: return four ? launch_tc_grouped_inst<FMT_E4M3, 4, 128, 1>(g, ctas, smem, st)
+                               : launch_tc_grouped_inst<FMT_E4M3, 2, 128, 1>(g, ctas, smem, st);
+    case FMT_BF16X3: return four ? launch_tc_grouped_inst<FMT_BF16X3, 4, 64, 3>(g, ctas, smem, st)
+                                 : launch_tc_grouped_inst<FMT_BF16X3, 2, 64, 3>(g, ctas, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -973,11 +1053,11 @@ cudaError_t launch_sketch_cc(int fmt, const double* A, int64_t lda, const double
 // 2^-48 relative (double-float), on the FP32 pipe instead of GB300's narrow FP64 pipe
 // (the sum over thousands of 2048-row splits at m = 4e6 is 8e9 additions).
 template <typename TP>
-__global__ void sketch_reduce_kernel(const TP* __restrict__ partial, int splits, int64_t ncols,
-                                     int64_t s, int64_t s_pad, const int* __restrict__ kexp,
-                                     double inv_sqrt_s, double* __restrict__ Y) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t c = blockIdx.y;
+__device__ __forceinline__ void sketch_reduce_body(const TP* __restrict__ partial, int splits, int64_t ncols,
+                                                   int64_t s, int64_t s_pad, const int* __restrict__ kexp,
+                                                   double inv_sqrt_s, double* __restrict__ Y, int64_t bx,
+                                                   int64_t c) {
+  const int64_t i = bx * (int64_t)blockDim.x + threadIdx.x;
   if (i >= s) return;
   double acc;
   if constexpr (sizeof(TP) == 8) {
@@ -999,6 +1079,87 @@ __global__ void sketch_reduce_kernel(const TP* __restrict__ partial, int splits,
   }
   const int k = kexp ? kexp[c] : 0;
   Y[c * s + i] = ldexp(acc * inv_sqrt_s, -k);
+}
+
+template <typename TP>
+__global__ void sketch_reduce_kernel(const TP* __restrict__ partial, int splits, int64_t ncols,
+                                     int64_t s, int64_t s_pad, const int* __restrict__ kexp,
+                                     double inv_sqrt_s, double* __restrict__ Y) {
+  sketch_reduce_body<TP>(partial, splits, ncols, s, s_pad, kexp, inv_sqrt_s, Y, blockIdx.x, blockIdx.y);
+}
+
+// ============================================================ grouped (batched) forms
+// One launch per stage for a batch of problems: CTA b works for the problem p with
+// start[p] <= b < start[p + 1] (start: prefix sums of the per-problem CTA counts), on
+// the block of that problem's own grid given by b - start[p].  Per-problem arguments
+// come from a device table.
+__global__ void grouped_colmax_kernel(const GCast* __restrict__ tab, const int* __restrict__ start, int nprob,
+                                      int* err) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GCast& g = tab[p];
+  colmax_a32_body(g.A, g.lda, g.b, g.m, g.n, g.cmax, g.a32, g.lda32, kGroupedColmaxRows, err,
+                  (int64_t)blockIdx.x - start[p]);
+}
+
+__global__ void grouped_scale_exps_kernel(const GCast* __restrict__ tab, const int* __restrict__ start,
+                                          int nprob, int t) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GCast& g = tab[p];
+  const int64_t c = ((int64_t)blockIdx.x - start[p]) * blockDim.x + threadIdx.x;
+  if (c > g.n) return;
+  const double mx = __longlong_as_double((long long)g.cmax[c]);
+  int k = 0;
+  if (t >= 0 && mx > 0.0 && isfinite(mx)) {
+    int ex;
+    frexp(mx, &ex);
+    k = t - (ex - 1);
+  }
+  g.kexp[c] = k;
+}
+
+template <int FMT>
+__global__ void grouped_cast_kernel(const GCast* __restrict__ tab, const int* __restrict__ start, int nprob,
+                                    int planes) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GCast& g = tab[p];
+  const int64_t local = (int64_t)blockIdx.x - start[p];
+  cast_transpose_body<FMT>(g.A, g.lda, g.b, g.m, g.n, g.kexp, g.Bt, g.plane_rows, planes, local % g.cast_gx,
+                           local / g.cast_gx);
+}
+
+__global__ void grouped_sketch_reduce_kernel(const GReduce* __restrict__ tab, const int* __restrict__ start,
+                                             int nprob) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GReduce& g = tab[p];
+  const int64_t local = (int64_t)blockIdx.x - start[p];
+  const int64_t gx = (g.s + 255) / 256;
+  sketch_reduce_body<float>(g.partial, g.splits, g.ncols, g.s, g.s_pad, g.kexp, 1.0 / sqrt((double)g.s), g.Y,
+                            local % gx, local / gx);
+}
+
+cudaError_t launch_grouped_cast(int fmt, const GCast* tab, const int* colmax_start, int64_t colmax_ctas,
+                                const int* exps_start, int64_t exps_ctas, const int* cast_start,
+                                int64_t cast_ctas, int nprob, int t, int* err, cudaStream_t st) {
+  if (colmax_ctas > 2147483647LL || cast_ctas > 2147483647LL) return cudaErrorInvalidValue;
+  grouped_colmax_kernel<<<(unsigned)colmax_ctas, 256, 0, st>>>(tab, colmax_start, nprob, err);
+  grouped_scale_exps_kernel<<<(unsigned)exps_ctas, 256, 0, st>>>(tab, exps_start, nprob, t);
+  const int planes = (fmt == FMT_BF16X3) ? 3 : 1;
+  const dim3 block(32, 8);
+  switch (fmt) {
+    case FMT_F16: grouped_cast_kernel<FMT_F16><<<(unsigned)cast_ctas, block, 0, st>>>(tab, cast_start, nprob, planes); break;
+    case FMT_BF16: grouped_cast_kernel<FMT_BF16><<<(unsigned)cast_ctas, block, 0, st>>>(tab, cast_start, nprob, planes); break;
+    case FMT_E4M3: grouped_cast_kernel<FMT_E4M3><<<(unsigned)cast_ctas, block, 0, st>>>(tab, cast_start, nprob, planes); break;
+    case FMT_BF16X3: grouped_cast_kernel<FMT_BF16X3><<<(unsigned)cast_ctas, block, 0, st>>>(tab, cast_start, nprob, planes); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_sketch_reduce(const GReduce* tab, const int* start, int64_t ctas, int nprob,
+                                         cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  grouped_sketch_reduce_kernel<<<(unsigned)ctas, 256, 0, st>>>(tab, start, nprob);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sketch_reduce(const void* partial, bool partial_f64, int splits, int64_t ncols,

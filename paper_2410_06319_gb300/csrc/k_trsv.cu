@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "batch.h"
 #include "kernels.h"
 #include "trsv.cuh"
 
@@ -367,9 +368,8 @@ LSQ_TRSV_INST(double, double, float)
 LSQ_TRSV_INST(double, float, float)
 
 // ------------------------------------------------------------ preparation
-__global__ void prepare_r_kernel(const double* __restrict__ R, int64_t n, float* R32, float* L32,
-                                 int64_t ld32, double* R64, double* L64, int64_t ld64) {
-  const int64_t j = blockIdx.x;
+__device__ __forceinline__ void prepare_r_body(const double* __restrict__ R, int64_t n, float* R32, float* L32,
+                                               int64_t ld32, double* R64, double* L64, int64_t ld64, int64_t j) {
   for (int64_t i = threadIdx.x; i < ld32; i += blockDim.x) {
     const double v = (i <= j && i < n) ? R[j * n + i] : 0.0;   // R(i, j), upper
     R32[j * ld32 + i] = (float)v;
@@ -384,15 +384,20 @@ __global__ void prepare_r_kernel(const double* __restrict__ R, int64_t n, float*
   }
 }
 
+__global__ void prepare_r_kernel(const double* __restrict__ R, int64_t n, float* R32, float* L32,
+                                 int64_t ld32, double* R64, double* L64, int64_t ld64) {
+  prepare_r_body(R, n, R32, L32, ld32, R64, L64, ld64, blockIdx.x);
+}
+
 // Inverse of the diagonal block k of the upper-triangular R (one warp per
 // block): lane j forms column j of T^-1 by back substitution.  DU(i, j) at
 // k*1024 + j*32 + i; DL = DU^T (the inverse of the diagonal block of R^T) at
 // k*1024 + i*32 + j.
 template <typename T>
-__global__ void dinv_kernel(const T* __restrict__ R, int64_t ld, int n, T* __restrict__ DU,
-                            T* __restrict__ DL) {
+__device__ __forceinline__ void dinv_body(const T* __restrict__ R, int64_t ld, int n, T* __restrict__ DU,
+                                          T* __restrict__ DL, int k) {
   __shared__ T tb[32][33];
-  const int k = blockIdx.x, lane = threadIdx.x;
+  const int lane = threadIdx.x;
   const int i0 = k * 32, w = min(32, n - i0);
   for (int c = 0; c < 32; ++c) tb[lane][c] = (lane < w && c < w) ? R[(size_t)(i0 + c) * ld + i0 + lane] : T(0);
   __syncwarp();
@@ -411,7 +416,13 @@ __global__ void dinv_kernel(const T* __restrict__ R, int64_t ld, int n, T* __res
   }
 }
 
-__global__ void kappa_diag_kernel(const double* __restrict__ R, int64_t n, double* out) {
+template <typename T>
+__global__ void dinv_kernel(const T* __restrict__ R, int64_t ld, int n, T* __restrict__ DU,
+                            T* __restrict__ DL) {
+  dinv_body<T>(R, ld, n, DU, DL, blockIdx.x);
+}
+
+__device__ __forceinline__ void kappa_diag_body(const double* __restrict__ R, int64_t n, double* out) {
   __shared__ double mx[32], mn[32];
   double a = 0.0, b = INFINITY;
   bool bad = false;
@@ -442,6 +453,10 @@ __global__ void kappa_diag_kernel(const double* __restrict__ R, int64_t n, doubl
   }
 }
 
+__global__ void kappa_diag_kernel(const double* __restrict__ R, int64_t n, double* out) {
+  kappa_diag_body(R, n, out);
+}
+
 cudaError_t launch_prepare_r(const double* R, int64_t n, Tri<float>* f32, Tri<double>* f64,
                              double* kappa_est, cudaStream_t st) {
   prepare_r_kernel<<<(unsigned)n, 256, 0, st>>>(R, n, const_cast<float*>(f32->R), const_cast<float*>(f32->L),
@@ -461,6 +476,84 @@ cudaError_t launch_prepare_r(const double* R, int64_t n, Tri<float>* f32, Tri<do
     e = cudaGetLastError();
   }
   return e;
+}
+
+
+// ============================================================ grouped (batched) forms
+template <typename T, typename TIN, typename TOUT, bool UPPER>
+__global__ void __launch_bounds__(kTrsvThreads)
+    grouped_trsv_kernel(const GTrsv<T, TIN, TOUT>* __restrict__ tab) {
+  const GTrsv<T, TIN, TOUT>& g = tab[blockIdx.x];
+  if (g.done && *g.done) return;
+  const TIN* y = g.y;
+  TOUT* x = g.x;
+  if (g.jp) {
+    const int64_t j = *g.jp;
+    y += j * g.ys;
+    x += j * g.xstr;
+  }
+  __shared__ T xs[1024];
+  extern __shared__ __align__(16) unsigned char trsv_buf[];
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) xs[i] = (T)((double)y[i] * g.yscale);
+  __syncthreads();
+  if (!block_trsv<T, UPPER>(g.M, g.ld, g.D, g.n, xs, trsv_buf, nullptr)) return;
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) x[i] = (TOUT)xs[i];
+}
+
+template <typename T, typename TIN, typename TOUT>
+cudaError_t launch_grouped_trsv(bool upper, const GTrsv<T, TIN, TOUT>* tab, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  const size_t smem = TrsvSmem<T>::bytes;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = allow_dyn_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nprob, kTrsvThreads, smem, st>>>(tab);
+    return cudaGetLastError();
+  };
+  return upper ? go(grouped_trsv_kernel<T, TIN, TOUT, true>) : go(grouped_trsv_kernel<T, TIN, TOUT, false>);
+}
+template cudaError_t launch_grouped_trsv<float, double, double>(bool, const GTrsv<float, double, double>*, int,
+                                                                cudaStream_t);
+template cudaError_t launch_grouped_trsv<float, float, float>(bool, const GTrsv<float, float, float>*, int,
+                                                              cudaStream_t);
+template cudaError_t launch_grouped_trsv<float, double, float>(bool, const GTrsv<float, double, float>*, int,
+                                                               cudaStream_t);
+template cudaError_t launch_grouped_trsv<float, float, double>(bool, const GTrsv<float, float, double>*, int,
+                                                               cudaStream_t);
+template cudaError_t launch_grouped_trsv<double, double, double>(bool, const GTrsv<double, double, double>*,
+                                                                 int, cudaStream_t);
+
+__global__ void grouped_prepare_r_kernel(const GPrepR* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GPrepR& g = tab[p];
+  prepare_r_body(g.R, g.n, const_cast<float*>(g.f32.R), const_cast<float*>(g.f32.L), g.f32.ld,
+                 const_cast<double*>(g.f64.R), const_cast<double*>(g.f64.L), g.f64.ld, (int64_t)blockIdx.x - start[p]);
+}
+
+template <typename T>
+__global__ void grouped_dinv_kernel(const GPrepR* __restrict__ tab, const int* __restrict__ start, int nprob) {
+  const int p = group_of(start, nprob, blockIdx.x);
+  const GPrepR& g = tab[p];
+  const int k = blockIdx.x - start[p];
+  if constexpr (sizeof(T) == 4)
+    dinv_body<float>(g.f32.R, g.f32.ld, (int)g.n, const_cast<float*>(g.f32.DU), const_cast<float*>(g.f32.DL), k);
+  else
+    dinv_body<double>(g.f64.R, g.f64.ld, (int)g.n, const_cast<double*>(g.f64.DU), const_cast<double*>(g.f64.DL), k);
+}
+
+__global__ void grouped_kappa_kernel(const GPrepR* __restrict__ tab) {
+  const GPrepR& g = tab[blockIdx.x];
+  kappa_diag_body(g.R, g.n, g.kappa);
+}
+
+cudaError_t launch_grouped_prepare_r(const GPrepR* tab, const int* col_start, int64_t col_ctas,
+                                     const int* blk_start, int64_t blk_ctas, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  grouped_prepare_r_kernel<<<(unsigned)col_ctas, 256, 0, st>>>(tab, col_start, nprob);
+  grouped_dinv_kernel<float><<<(unsigned)blk_ctas, 32, 0, st>>>(tab, blk_start, nprob);
+  grouped_dinv_kernel<double><<<(unsigned)blk_ctas, 32, 0, st>>>(tab, blk_start, nprob);
+  grouped_kappa_kernel<<<(unsigned)nprob, 256, 0, st>>>(tab);
+  return cudaGetLastError();
 }
 
 }  // namespace lsq

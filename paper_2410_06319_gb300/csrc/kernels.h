@@ -32,6 +32,55 @@ cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const d
                                   int64_t n, const int* kexp, void* Bt, int64_t plane_rows,
                                   cudaStream_t st);
 
+// Arguments of one tensor-core sketch launch (one problem).
+struct SketchTcArgs {
+  int64_t s, m, ncols, kchunk, s_pad;
+  int bn, nsub, tmem_cols, rows_per_plane;
+  int mtiles, ngroups;        // CTA grid of one problem: mtiles x ngroups x splits
+  uint32_t k0, k1;
+  float* partial;
+  int* err;
+  // deferred mode: per generator warp a list of the (a, b) pairs whose FP32
+  // estimate was too close to a rounding midpoint, packed (data row << 16 | sketch row)
+  uint64_t* rec;
+  uint32_t* rec_cnt;
+  uint32_t rec_cap;
+};
+
+// A grouped sketch launch: problem p owns CTAs [start[p], start[p + 1]); tab[p] and
+// maps[p] (64-byte aligned, device memory) are its arguments and tensor map.
+struct SketchGroup {
+  const SketchTcArgs* tab;
+  const CUtensorMap* maps;
+  const int* start;
+  int nprob;
+};
+
+// Per-problem arguments of the grouped cast (column maxima and FP32 copy, power-of-two
+// column exponents, cast into the blocked Bt layout).
+constexpr int64_t kGroupedColmaxRows = 64;
+struct GCast {
+  const double* A;
+  int64_t lda;
+  const double* b;
+  int64_t m, n;
+  unsigned long long* cmax;   // n + 1, zeroed before the launch
+  float* a32;                 // FP32 copy (may be null)
+  int64_t lda32;
+  int* kexp;
+  void* Bt;
+  int64_t plane_rows;
+  int64_t cast_gx;            // row tiles of 32 in this problem's cast grid
+};
+// Per-problem arguments of the grouped split reduction of the FP32 sketch partials.
+struct GReduce {
+  const float* partial;
+  int splits;
+  int64_t ncols, s, s_pad;
+  const int* kexp;
+  double* Y;
+};
+
 struct SketchPlan {
   int fmt;             // FMT_F16, FMT_BF16, FMT_E4M3 (tensor cores) or FMT_F32/F64
   int64_t s, m, ncols; // ncols = n + 1
@@ -60,6 +109,20 @@ bool encode_bt_tmap(CUtensorMap* tm, const void* Bt, int fmt, int64_t rows, int6
 // deferred mode: the uncertain pairs go to sketch_rec_lists(p) lists of
 // sketch_rec_cap(p) entries (counts in rec_cnt) and launch_sketch_fix corrects the
 // partials; if it reports *overflow != 0 the exact mode must be rerun.
+// The arguments launch_sketch_tc builds for plan p (exact mode), for a grouped table.
+SketchTcArgs sketch_tc_args(const SketchPlan& p, uint64_t seed, float* partial, int* err);
+// One launch for a batch: ctas = start[nprob]; smem = the largest plan's; every plan must
+// have the same format and stage count.
+cudaError_t launch_sketch_tc_grouped(int fmt, int stages, const SketchGroup& g, int64_t ctas, size_t smem,
+                                     cudaStream_t st);
+// Grouped cast: colmax CTAs (ceil(m / kGroupedColmaxRows) per problem), exponent CTAs
+// (ceil((n + 1) / 256)), cast CTAs (cast_gx x ceil(plane_rows / 32)); t as in launch_scale_exps.
+cudaError_t launch_grouped_cast(int fmt, const GCast* tab, const int* colmax_start, int64_t colmax_ctas,
+                                const int* exps_start, int64_t exps_ctas, const int* cast_start,
+                                int64_t cast_ctas, int nprob, int t, int* err, cudaStream_t st);
+// Grouped sketch_reduce: ceil(s / 256) x (n + 1) CTAs per problem.
+cudaError_t launch_grouped_sketch_reduce(const GReduce* tab, const int* start, int64_t ctas, int nprob,
+                                         cudaStream_t st);
 cudaError_t launch_sketch_tc(const SketchPlan& p, const CUtensorMap& tm, uint64_t seed,
                              float* partial, int* err, cudaStream_t st, uint64_t* rec = nullptr,
                              uint32_t* rec_cnt = nullptr, uint32_t rec_cap = 0);

@@ -1,0 +1,117 @@
+"""Grouped batched mode (one launch per stage for all problems) through the C ABI.
+
+* Uneven problems in the good regime (kappa u_s < 1): every problem reaches the oracle's
+  reference solution within 4u (Sec. 5's target), as the single solve does.
+* A problem's result does not depend on the rest of the batch: the same problem alone
+  and inside a batch gives the same bits.
+* The grouped and per-problem modes agree to the accuracy both reach.
+* Problems shaped like the 512-problem batch (m ~ U[5e3, m_max], n ~ U[32, 256],
+  kappa log-U[1e2, 1e8], rho log-U[1e-8, 1e-1], BF16 sketch s = 4n), m capped so the
+  oracle's reference solution stays quick: every problem that reports convergence is
+  within 4u of it, and those with kappa u_s < 1 (Sec. 3's condition) converge.
+* A NaN in one problem's A gives LSQ_E_NONFINITE for the call.
+"""
+import numpy as np
+import pytest
+import torch
+
+from conftest import dev
+from lsq_synth import batch_specs, randsvd_problem
+from oracle import exact
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def zeros(k):
+    return torch.zeros(k, dtype=torch.float64, device="cuda")
+
+
+def _batch(shapes, seed0):
+    Ps, probs = [], []
+    for k, (m, n, kappa, rho) in enumerate(shapes):
+        P = randsvd_problem(m, n, kappa, rho=rho, seed=seed0 + k)
+        Ps.append(P)
+        probs.append(dict(A=dev(P.A), b=dev(P.b), m=m, n=n, s=4 * n, seed=k, x=zeros(n), r=zeros(m)))
+    return Ps, probs
+
+
+GOOD = [(3000, 32, 1e2, 1e-1), (7000, 64, 1e4, 1e-4), (5000, 100, 1e3, 1e-6), (4100, 45, 10.0, 1e-2),
+        (9000, 77, 1e5, 1e-3), (6500, 128, 1e6, 1e-5), (12000, 200, 1e3, 1e-2), (2500, 256, 1e2, 1e-3)]
+
+
+def test_grouped_batch_reaches_the_oracle_solution(lsq, handle):
+    Ps, probs = _batch(GOOD, 70)
+    st, sts, infos = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    assert st == 0 and all(v == 0 for v in sts), sts
+    for P, pr, inf in zip(Ps, probs, infos):
+        xstar, rstar = exact.reference_solution(P.A, P.b)
+        ex, er = exact.forward_errors(pr["x"].cpu().numpy(), pr["r"].cpu().numpy(), xstar, rstar)
+        assert inf.ir_converged == 1 and ex <= 4 * U32 and er <= 4 * U32, (P.meta, ex, er)
+        assert inf.lsqr_its > 0 and inf.gmres_its_total > 0
+
+
+def test_grouped_result_does_not_depend_on_the_batch(lsq, handle):
+    Ps, probs = _batch(GOOD[:5], 90)
+    lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    # problem 2 alone (a batch of one) and inside another batch
+    for others in ([], [0, 4], [1, 3, 4]):
+        sel = [2] + others
+        sub = []
+        for k in sel:
+            P = Ps[k]
+            m, n = P.A.shape
+            sub.append(dict(A=probs[k]["A"], b=probs[k]["b"], m=m, n=n, s=4 * n, seed=k, x=zeros(n), r=zeros(m)))
+        lsq.lsq_lsir_batched(handle, sub, "bf16x3", "f32", "f32", "f64", 1e-6)
+        assert torch.equal(sub[0]["x"], probs[2]["x"]) and torch.equal(sub[0]["r"], probs[2]["r"]), others
+
+
+def test_grouped_and_per_problem_modes_agree(lsq, handle):
+    Ps, probs = _batch(GOOD[:6], 110)
+    _, probs2 = _batch(GOOD[:6], 110)
+    st1, s1, i1 = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    st2, s2, i2 = lsq.lsq_lsir_batched(handle, probs2, "bf16x3", "f32", "f32", "f64", 1e-6, {"batch_mode": 1})
+    assert s1 == s2 == [0] * 6
+    for P, a, bb in zip(Ps, probs, probs2):
+        x1, x2 = a["x"].cpu().numpy(), bb["x"].cpu().numpy()
+        assert np.linalg.norm(x1 - x2) <= 8 * U32 * np.linalg.norm(x2)
+
+
+def test_batch_shaped_sample_against_the_oracle(lsq, handle):
+    specs = batch_specs(32, seed=3, m_range=(5000, 30000))
+    Ps, probs = [], []
+    for k, sp in enumerate(specs):
+        P = randsvd_problem(sp["m"], sp["n"], sp["kappa"], rho=sp["rho"], seed=200 + k)
+        Ps.append(P)
+        probs.append(dict(A=dev(P.A), b=dev(P.b), m=sp["m"], n=sp["n"], s=4 * sp["n"], seed=k,
+                          x=zeros(sp["n"]), r=zeros(sp["m"])))
+    st, sts, infos = lsq.lsq_lsir_batched(handle, probs, "bf16", "f32", "f32", "f64", 1e-6,
+                                          {"ir_maxit": 6, "lsqr_maxit": 200})
+    assert st in (0, 1) and all(v in (0, 1) for v in sts)
+    good = 0
+    for P, pr, inf, sp in zip(Ps, probs, infos, specs):
+        if not inf.ir_converged and sp["kappa"] * 2.0 ** -8 >= 1.0:
+            continue   # outside the guarantee and not converged: nothing to compare
+        xstar, rstar = exact.reference_solution(P.A, P.b)
+        ex, er = exact.forward_errors(pr["x"].cpu().numpy(), pr["r"].cpu().numpy(), xstar, rstar)
+        if inf.ir_converged:
+            assert ex <= 4 * U32 and er <= 4 * U32, (sp, ex, er)
+        if sp["kappa"] * 2.0 ** -8 < 1.0:
+            good += 1
+            assert inf.ir_converged == 1, (sp, ex, er)
+    print("converged", sum(i.ir_converged for i in infos), "of", len(infos), "good regime", good)
+
+
+def test_nonfinite_input_in_one_problem(lsq, handle):
+    Ps, probs = _batch(GOOD[:3], 130)
+    A = probs[1]["A"].clone()
+    A[17] = float("nan")
+    probs[1]["A"] = A
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    assert e.value.status == -4   # LSQ_E_NONFINITE
+    # the handle stays usable
+    Ps, probs = _batch(GOOD[:2], 140)
+    st, sts, _ = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    assert st == 0

@@ -281,7 +281,7 @@ def test_lsir_split_sketch_converges_where_bf16_fails(lsq, handle):
 
 
 def test_batched_uneven_problems_match_single_solves(lsq, handle):
-    """lsq_lsir_batched over uneven problems equals lsq_lsir on each problem."""
+    """lsq_lsir_batched in per-problem mode over uneven problems equals lsq_lsir on each problem."""
     shapes = [(3000, 32, 1e2), (7000, 64, 1e4), (5000, 100, 1e3), (4100, 45, 10.0), (9000, 77, 1e5)]
     probs, singles, P_all = [], [], []
     for k, (m, n, kappa) in enumerate(shapes):
@@ -293,7 +293,7 @@ def test_batched_uneven_problems_match_single_solves(lsq, handle):
         xs, rs = zeros(n), zeros(m)
         lsq.lsq_lsir(handle, A, b, m, n, 4 * n, "bf16x3", "f32", "f32", "f64", 1e-6, k, None, xs, rs)
         singles.append((xs.cpu().numpy(), rs.cpu().numpy()))
-    st, sts, infos = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6)
+    st, sts, infos = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6, {"batch_mode": 1})
     assert st == 0 and all(v == 0 for v in sts)
     for k, pr in enumerate(probs):
         assert np.array_equal(pr["x"].cpu().numpy(), singles[k][0])
