@@ -298,37 +298,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# ---------------------------------------------------------------- batched sample
-BATCH = dict(count=24, m_range=(5000, 40000), n_range=(32, 256), kappa_range=(1e2, 1e8),
+# ---------------------------------------------------------------- batched configuration
+BATCH = dict(count=512, m_range=(5000, 200000), n_range=(32, 256), kappa_range=(1e2, 1e8),
              rho_range=(1e-8, 1e-1), seed=4)
+BATCH_US = "bf16"
 
 
-def run_batched_sample(lsq, h, torch):
-    """lsq_lsir_batched over BATCH["count"] problems drawn like the batched configuration
-    (n, kappa and rho ranges as configured; m capped at 40000 so that the host-side
-    generation stays within seconds).  One warm-up call, then one timed call."""
-    from lsq_synth.problems import batch_specs, randsvd_problem
+def run_batched(lsq, torch, pk, fp64_fma, opts=None):
+    """The batched configuration: BATCH["count"] problems (m, n, kappa, rho drawn as
+    configured) drawn on the device, BF16 sketch s = 4n, FP32 QR/LSQR/FGMRES products,
+    FP64 residuals, through one grouped lsq_lsir_batched call on its own handle.  One
+    warm-up call (workspace allocation, graph captures), then one timed call (CUDA events
+    on the handle's stream, and the host clock).  The roofline fraction sums each problem's
+    stage floors times its own iteration counts over the measured time."""
+    from lsq_synth.device import DeviceRandsvd
+    from lsq_synth.problems import batch_specs
     specs = batch_specs(**BATCH)
+    t0 = time.perf_counter()
     probs = []
     for k, sp in enumerate(specs):
-        P = randsvd_problem(sp["m"], sp["n"], sp["kappa"], rho=sp["rho"], seed=sp["seed"])
-        probs.append(dict(A=torch.from_numpy(P.A).cuda(), b=torch.from_numpy(P.b).cuda(), m=sp["m"],
-                          n=sp["n"], s=4 * sp["n"], seed=k,
-                          x=torch.zeros(sp["n"], dtype=torch.float64, device="cuda"),
-                          r=torch.zeros(sp["m"], dtype=torch.float64, device="cuda")))
-    us = "bf16x3"
-    lsq.lsq_lsir_batched(h, probs, us, "f32", "f32", "f64", 1e-6)
+        gen = DeviceRandsvd(sp["m"], sp["n"], seed=sp["seed"])
+        A, b, _ = gen.problem(sp["kappa"], sp["rho"])
+        gen.release()
+        del gen
+        probs.append(dict(A=A.contiguous(), b=b.contiguous(), m=sp["m"], n=sp["n"], s=4 * sp["n"], seed=k,
+                          x=torch.zeros(sp["n"], dtype=torch.float64, device=A.device),
+                          r=torch.zeros(sp["m"], dtype=torch.float64, device=A.device)))
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, sts, infos = lsq.lsq_lsir_batched(h, probs, us, "f32", "f32", "f64", 1e-6)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t_draw = time.perf_counter() - t0
+    hb = lsq.Handle()
+    try:
+        lsq.lsq_lsir_batched(hb, probs, BATCH_US, "f32", "f32", "f64", 1e-6, opts)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        st, sts, infos = lsq.lsq_lsir_batched(hb, probs, BATCH_US, "f32", "f32", "f64", 1e-6, opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        dev_s = e0.elapsed_time(e1) / 1e3
+    finally:
+        hb.close()
+    floor_ms = 0.0
+    bytes_passes = 0.0
+    its = {"lsqr": 0, "fgmres": 0, "ir": 0, "escalated": 0}
+    for sp, inf in zip(specs, infos):
+        d = inf.as_dict()
+        wl = {"m": sp["m"], "n": sp["n"], "s": 4 * sp["n"], "u_s": BATCH_US, "u_p": "f32"}
+        floor_ms += sum(tts_floor(wl, d, pk, fp64_fma).values())
+        lda32 = (sp["n"] + 3) // 4 * 4
+        bytes_passes += (d["lsqr_its"] + d["gmres_its_total"] + 2) * (4.0 * sp["m"] * lda32 + 8.0 * sp["m"])
+        its["lsqr"] += d["lsqr_its"]
+        its["fgmres"] += d["gmres_its_total"]
+        its["ir"] += d["ir_its"]
+        its["escalated"] += d["escalated"]
+    t_s = max(wall, dev_s)
     conv = sum(1 for i in infos if i.ir_converged == 1)
-    ok_cond = sum(1 for sp in specs if sp["kappa"] * 2.0 ** -24 < 1.0)
-    return {"problems": len(specs), "u_s": us, "seconds": dt, "solves_per_s": len(specs) / dt,
-            "converged": conv, "kappa_u_s_below_1": ok_cond,
-            "sample": "m ~ U[5000, 40000], n ~ U[32, 256], kappa log-U[1e2, 1e8], rho log-U[1e-8, 1e-1], "
-                      "s = 4n; host wall clock around one lsq_lsir_batched call"}
+    return {"problems": len(specs), "u_s": BATCH_US, "seconds": t_s, "device_seconds": dev_s,
+            "solves_per_s": len(specs) / t_s, "converged": conv,
+            "not_converged": sum(1 for v in sts if v == 1), "errors": sum(1 for v in sts if v < 0),
+            "kappa_u_s_below_1": sum(1 for sp in specs if sp["kappa"] * 2.0 ** -8 < 1.0),
+            "iterations_total": its,
+            "roofline": {"floor_ms": floor_ms, "frac": floor_ms / (t_s * 1e3),
+                         "pass_bytes_gbs": bytes_passes / t_s / 1e9,
+                         "how": "sum over the problems of their stage floors (HBM bytes, tensor flops at the "
+                                "sustained BF16 peak, FP64 FMAs at the measured FP64 rate) times their own "
+                                "iteration counts, over the measured time of the call"},
+            "mode": ("per problem (four streams, lsq_lsir on each)" if opts and opts.get("batch_mode")
+                     else "grouped (one launch per stage for all problems, iteration batches as CUDA graphs)"),
+            "draw_s": t_draw,
+            "sample": "m ~ U[5000, 200000], n ~ U[32, 256], kappa log-U[1e2, 1e8], rho log-U[1e-8, 1e-1], "
+                      "s = 4n, drawn on the device (U from CholeskyQR2 of a Gaussian); inputs resident; "
+                      "timed: one lsq_lsir_batched call after a warm-up call"}
 
 
 # ---------------------------------------------------------------- rooflines
@@ -643,13 +686,14 @@ def run_ours(args):
     except Exception as exc:
         secondary = {"error": f"{type(exc).__name__}: {exc}"}
 
-    # ---- batched mode: a seeded sample shaped like the 512-problem configuration
+    # ---- batched configuration: 512 uneven problems in one grouped call
     batched = None
-    if rank == 0:
+    if rank == 0 and not args.no_batched:
         try:
-            batched = run_batched_sample(lsq, h, torch)
+            batched = run_batched(lsq, torch, pk, fp64_fma)
         except Exception as e:   # reported, never fatal for the headline line
             batched = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
 
     u = 2.0 ** -24
     line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -689,7 +733,8 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- single cases for profilers
-CASES = ("lsir_m4e6", "fgmres_pass_m2e5_n1000", "arnoldi_m1e6_n1000", "sketch_m2e5_n1000")
+CASES = ("lsir_m4e6", "fgmres_pass_m2e5_n1000", "arnoldi_m1e6_n1000", "sketch_m2e5_n1000", "batched_512",
+         "batched_64")
 
 
 def run_case(name):
@@ -699,12 +744,25 @@ def run_case(name):
     refinement step (six FGMRES iterations, CUDA graphs off) on a 200000 x 1000
     Gaussian A.  arnoldi_m1e6_n1000: one refinement step of up to 40 FGMRES
     iterations on a 1e6 x 1000, kappa = 1e7 problem.  sketch_m2e5_n1000: one
-    lsq_sketch (s = 4000, BF16X3) of a 200000 x 1000 Gaussian A.
+    lsq_sketch (s = 4000, BF16X3) of a 200000 x 1000 Gaussian A.  batched_512: the batched
+    configuration (512 problems, one warm-up and one timed grouped call); batched_64: its
+    first 64 problems.
     """
     import torch
     import paper_2410_06319_gb300 as lsq
     from lsq_synth.device import DeviceRandsvd
     torch.manual_seed(0)
+    if name.startswith("batched_"):
+        # the batched configuration (batched_512), or its first 64 problems (batched_64,
+        # also timed in the per-problem mode for comparison)
+        if name == "batched_64":
+            BATCH["count"] = 64
+        res = run_batched(lsq, torch, peaks(), lsq.lsq_probe_fma_rate("f64"))
+        if name == "batched_64":
+            res["per_problem_mode"] = run_batched(lsq, torch, peaks(), lsq.lsq_probe_fma_rate("f64"),
+                                                  opts={"batch_mode": 1})
+        print(json.dumps({"case": name, **res}), flush=True)
+        return
     h = lsq.Handle()
 
     def randn(m, n):
@@ -746,6 +804,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave out the batched configuration (512 problems) from the bench line")
     ap.add_argument("--case", default=None, choices=CASES,
                     help="run one small named workload once (no timing; for profilers)")
     args = ap.parse_args()
