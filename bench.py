@@ -304,7 +304,7 @@ BATCH = dict(count=512, m_range=(5000, 200000), n_range=(32, 256), kappa_range=(
 BATCH_US = "bf16"
 
 
-def run_batched(lsq, torch, pk, fp64_fma, opts=None):
+def run_batched(lsq, torch, pk, fp64_fma, opts=None, warm=True):
     """The batched configuration: BATCH["count"] problems (m, n, kappa, rho drawn as
     configured) drawn on the device, BF16 sketch s = 4n, FP32 QR/LSQR/FGMRES products,
     FP64 residuals, through one grouped lsq_lsir_batched call on its own handle.  One
@@ -328,7 +328,8 @@ def run_batched(lsq, torch, pk, fp64_fma, opts=None):
     t_draw = time.perf_counter() - t0
     hb = lsq.Handle()
     try:
-        lsq.lsq_lsir_batched(hb, probs, BATCH_US, "f32", "f32", "f64", 1e-6, opts)
+        if warm:
+            lsq.lsq_lsir_batched(hb, probs, BATCH_US, "f32", "f32", "f64", 1e-6, opts)
         torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -734,7 +735,7 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- single cases for profilers
 CASES = ("lsir_m4e6", "fgmres_pass_m2e5_n1000", "arnoldi_m1e6_n1000", "sketch_m2e5_n1000", "batched_512",
-         "batched_64")
+         "batched_64", "batched_16")
 
 
 def run_case(name):
@@ -746,7 +747,8 @@ def run_case(name):
     iterations on a 1e6 x 1000, kappa = 1e7 problem.  sketch_m2e5_n1000: one
     lsq_sketch (s = 4000, BF16X3) of a 200000 x 1000 Gaussian A.  batched_512: the batched
     configuration (512 problems, one warm-up and one timed grouped call); batched_64: its
-    first 64 problems.
+    first 64 problems (and the per-problem mode on them); batched_16: its first 16 problems,
+    one grouped call (for launch lists).
     """
     import torch
     import paper_2410_06319_gb300 as lsq
@@ -755,9 +757,9 @@ def run_case(name):
     if name.startswith("batched_"):
         # the batched configuration (batched_512), or its first 64 problems (batched_64,
         # also timed in the per-problem mode for comparison)
-        if name == "batched_64":
-            BATCH["count"] = 64
-        res = run_batched(lsq, torch, peaks(), lsq.lsq_probe_fma_rate("f64"))
+        if name in ("batched_64", "batched_16"):
+            BATCH["count"] = int(name.split("_")[1])
+        res = run_batched(lsq, torch, peaks(), lsq.lsq_probe_fma_rate("f64"), warm=(name != "batched_16"))
         if name == "batched_64":
             res["per_problem_mode"] = run_batched(lsq, torch, peaks(), lsq.lsq_probe_fma_rate("f64"),
                                                   opts={"batch_mode": 1})

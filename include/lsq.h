@@ -155,6 +155,9 @@ typedef struct lsq_opts {
                              Table 4's escalated rows come out as printed */
   int32_t batch_mode;     /* lsq_lsir_batched: 0 grouped launches when the batch allows them,
                              1 one solve per problem on internal streams */
+  int32_t batch_grid;     /* grouped mode: CTAs of the persistent pass launches; 0 -> chosen by
+                             timing the candidates on the first call for a batch shape (cached in
+                             the handle); every choice gives the same result */
 } lsq_opts;
 
 /* Diagnostics of one call. */

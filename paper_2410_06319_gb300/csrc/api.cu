@@ -832,7 +832,7 @@ lsq_status lsq_residual(lsq_handle* h, const double* A, const double* b, int64_t
 lsq_status lsq_lsir_batched(lsq_handle* h, int32_t nprob, const lsq_problem* probs, lsq_prec u_s,
                             lsq_prec u_p, lsq_prec u_w, lsq_prec u_r, double tol,
                             const lsq_opts* opts, int32_t* statuses, lsq_info* infos) {
-  if (opts && (opts->batch_mode < 0 || opts->batch_mode > 1)) return LSQ_E_INVAL;
+  if (opts && (opts->batch_mode < 0 || opts->batch_mode > 1 || opts->batch_grid < 0)) return LSQ_E_INVAL;
   if (!h || nprob < 0 || (nprob > 0 && !probs)) return LSQ_E_INVAL;
   for (int32_t i = 0; i < nprob; ++i) {   // validate everything before any launch
     lsq_opts o;

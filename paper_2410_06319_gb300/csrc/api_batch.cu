@@ -98,6 +98,7 @@ struct BatchCtx {
   lsq_opts o;
   double alpha;
   std::vector<int64_t> m, n, s, lda, lda32;
+  int64_t pass_grid = 0;   // CTAs of the persistent grouped passes (0: one per item)
 };
 
 // A graph of `body` cached under `key` (the pointers it captured are part of the key).
@@ -118,6 +119,54 @@ void run_graph(BatchCtx& b, CachedGraph* G) {
     CK((__VA_ARGS__));      \
     ++b.h->launches;        \
   } while (0)
+
+// The tile autotuner: the grid of the persistent grouped passes.  Candidates are one CTA
+// per item and 32, 16, 8 or 4 CTAs per SM; each runs the given pass (whose outputs the
+// solve overwrites) once to warm up and three times under CUDA events, and the fastest is
+// kept for this batch shape in the handle.  Every candidate computes every item the same
+// way, so the choice changes the speed only.
+int64_t tune_pass_grid(BatchCtx& b, const PassArgs<float>* tab, const Groups& g, size_t smem) {
+  if (b.o.batch_grid > 0) return b.o.batch_grid;
+  std::string key = "pass";
+  {
+    uint64_t hsh = 1469598103934665603ull;
+    for (int p = 0; p < b.np; ++p) {
+      hsh = (hsh ^ (uint64_t)b.m[p]) * 1099511628211ull;
+      hsh = (hsh ^ (uint64_t)b.lda32[p]) * 1099511628211ull;
+    }
+    key += ":" + std::to_string(b.np) + ":" + std::to_string(hsh);
+  }
+  auto it = b.h->tuned.find(key);
+  if (it != b.h->tuned.end()) return it->second;
+  std::vector<int64_t> cands = {0};
+  for (int per : {32, 16, 8, 4}) {
+    const int64_t gsz = (int64_t)per * b.h->num_sms;
+    if (gsz < g.total) cands.push_back(gsz);
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int64_t best = 0;
+  float best_ms = 0.f;
+  for (const int64_t c : cands) {
+    CK(launch_grouped_pass<float>(PM_LSQR, 4, 2, tab, g.dev, g.total, b.np, smem, b.st, c));
+    CK(cudaEventRecord(e0, b.st));
+    for (int r = 0; r < 3; ++r) CK(launch_grouped_pass<float>(PM_LSQR, 4, 2, tab, g.dev, g.total, b.np, smem, b.st, c));
+    CK(cudaEventRecord(e1, b.st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    b.h->launches += 4;
+    if (c == cands.front() || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b.h->tuned[key] = best;
+  return best;
+}
 
 // The FGMRES solves of one refinement step for every active problem (Alg. 2, FGMRES
 // solve), products in TOP; fills per-problem iteration counts, relative residuals,
@@ -266,7 +315,7 @@ void batch_fgmres(BatchCtx& b, const std::vector<const TOP*>& Aop, const std::ve
   auto body = [&]() {
     for (int k = 0; k < kBatch; ++k) {
       LB(launch_grouped_trsv<TOP, double, TOP>(true, dz, np, b.st));
-      LB(launch_grouped_pass<TOP>(PM_FGM, vw, vpl, dp, gPass.dev, gPass.total, np, pass_smem, b.st));
+      LB(launch_grouped_pass<TOP>(PM_FGM, vw, vpl, dp, gPass.dev, gPass.total, np, pass_smem, b.st, b.pass_grid));
       LB(launch_grouped_colsum<TOP, TOP>(dc, gCol.dev, gCol.total, np, b.st));
       LB(launch_grouped_trsv<TOP, TOP, double>(false, dw, np, b.st));
       LB(launch_grouped_arnoldi(dg, gArn.dev, gArn.total, np, b.st));
@@ -277,7 +326,7 @@ void batch_fgmres(BatchCtx& b, const std::vector<const TOP*>& Aop, const std::ve
                                 : batch_graph(b, graph_key(f32 ? "bfgm32" : "bfgm64",
                                                            {PV(dz), PV(dp), PV(dc), PV(dw), PV(dg), PV(gPass.dev),
                                                             gPass.total, PV(gArn.dev), gArn.total, np,
-                                                            (int64_t)pass_smem}),
+                                                            (int64_t)pass_smem, b.pass_grid}),
                                               body);
   states.assign(np, GmState{});
   for (int it = 0; it <= gmax + kBatch; it += kBatch) {
@@ -592,19 +641,23 @@ lsq_status lsq_batch_grouped(lsq_handle* h, int32_t nprob, const lsq_problem* pr
       LB(launch_grouped_axpby(db32, gm.dev, gm.total, np, b.st));
       LB(launch_grouped_norm(dnb, np, b.st));
       LB(launch_grouped_axpby(dneg, gn.dev, gn.total, np, b.st));
-      LB(launch_grouped_pass<float>(PM_LSQR, 4, 2, dp0, gp.dev, gp.total, np, pass_smem, b.st));
+      // the persistent passes' grid: forced, cached for this batch shape, or chosen now by
+      // timing this (repeatable) first pass with each candidate
+      b.pass_grid = tune_pass_grid(b, dp0, gp, pass_smem);
+      LB(launch_grouped_pass<float>(PM_LSQR, 4, 2, dp0, gp.dev, gp.total, np, pass_smem, b.st, b.pass_grid));
       LB(launch_grouped_lsqr_colsum<float>(dcs, gn.dev, gn.total, np, true, b.st));
       LB(launch_grouped_lsqr_step<float>(dstep, np, true, b.st));
       auto body = [&]() {
         for (int k = 0; k < kBatch; ++k) {
-          LB(launch_grouped_pass<float>(PM_LSQR, 4, 2, dp1, gp.dev, gp.total, np, pass_smem, b.st));
+          LB(launch_grouped_pass<float>(PM_LSQR, 4, 2, dp1, gp.dev, gp.total, np, pass_smem, b.st, b.pass_grid));
           LB(launch_grouped_lsqr_colsum<float>(dcs, gn.dev, gn.total, np, false, b.st));
           LB(launch_grouped_lsqr_step<float>(dstep, np, false, b.st));
         }
       };
       CachedGraph* G = b.o.no_graph ? nullptr
                                     : batch_graph(b, graph_key("blsqr", {PV(dp1), PV(dcs), PV(dstep), PV(gp.dev),
-                                                                         gp.total, np, (int64_t)pass_smem}),
+                                                                         gp.total, np, (int64_t)pass_smem,
+                                                                         b.pass_grid}),
                                                   body);
       int maxit_all = 0;
       for (int p = 0; p < np; ++p) maxit_all = std::max(maxit_all, init[p].maxit);
@@ -664,7 +717,7 @@ lsq_status lsq_batch_grouped(lsq_handle* h, int32_t nprob, const lsq_problem* pr
       for (int p = 0; p < np; ++p) maxw = std::max(maxw, b.lda32[p]);
       LB(launch_grouped_axpby(upload(h, "b_tn2", tneg), gn.dev, gn.total, np, b.st));
       LB(launch_grouped_pass<float>(PM_LSQR, 4, 2, upload(h, "b_tq2", tq), gp.dev, gp.total, np, (size_t)8 * maxw * 4,
-                                    b.st));
+                                    b.st, b.pass_grid));
       LB(launch_grouped_axpby(upload(h, "b_tr2", tr), gm.dev, gm.total, np, b.st));
       CK(cudaStreamSynchronize(b.st));
     }
@@ -760,7 +813,8 @@ lsq_status lsq_batch_grouped(lsq_handle* h, int32_t nprob, const lsq_problem* pr
         CK(cudaMemcpyAsync(skip_dev, skip.data(), (size_t)np * 4, cudaMemcpyHostToDevice, b.st));
         {
           StageTimer t(h, ST_RES);
-          LB(launch_grouped_pass<double>(PM_RES, 1, 8, dres, gp.dev, gp.total, np, (size_t)8 * maxn * 8, b.st));
+          LB(launch_grouped_pass<double>(PM_RES, 1, 8, dres, gp.dev, gp.total, np, (size_t)8 * maxn * 8, b.st,
+                                         b.pass_grid));
           LB(launch_grouped_colsum<double, double>(dcg, gn.dev, gn.total, np, b.st));
           LB(launch_grouped_trsv<double, double, double>(false, dth, np, b.st));
         }

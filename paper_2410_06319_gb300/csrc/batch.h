@@ -114,10 +114,12 @@ struct GGm {
 
 // ---- k_iter.cu
 // the register-blocked pass over A for every problem (vw: vector width, vpl: vectors per
-// lane, covering every problem's row; smem: 8 x (the widest row) x sizeof(T))
+// lane, covering every problem's row; smem: 8 x (the widest row) x sizeof(T)).  ctas items
+// (start[nprob]); grid: CTAs of the persistent launch (0 or >= ctas: one per item); the
+// result is the same for every grid.
 template <typename T>
 cudaError_t launch_grouped_pass(int mode, int vw, int vpl, const PassArgs<T>* tab, const int* start,
-                                int64_t ctas, int nprob, size_t smem, cudaStream_t st);
+                                int64_t ctas, int nprob, size_t smem, cudaStream_t st, int64_t grid = 0);
 template <typename TP, typename TO>
 cudaError_t launch_grouped_colsum(const GColsum<TP, TO>* tab, const int* start, int64_t ctas, int nprob,
                                   cudaStream_t st);

@@ -86,6 +86,7 @@ struct lsq_handle {
   };
   std::vector<Mark> marks;
   std::vector<lsq_handle*> workers;    // sub-handles of lsq_lsir_batched (own streams)
+  std::unordered_map<std::string, int64_t> tuned;   // grouped-launch grid sizes chosen by timing
 };
 
 namespace {

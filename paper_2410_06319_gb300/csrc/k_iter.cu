@@ -1372,22 +1372,30 @@ cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* 
 // block count within the launch stand in for blockIdx.x and gridDim.x of the
 // single-problem kernels above, whose bodies these call.
 
+// Persistent over the items (problem, block of the problem's pass): CTA b takes items b,
+// b + gridDim.x, ...; every item is computed exactly as a CTA of that problem's own pass
+// would compute it, so the result does not depend on the grid size.
 template <typename T, int VW, int VPL, int MODE>
 __global__ void __launch_bounds__(256)
-    grouped_pass_kernel(const PassArgs<T>* __restrict__ tab, const int* __restrict__ start, int nprob) {
-  const int pr = group_of(start, nprob, blockIdx.x);
-  pass_body<T, VW, VPL, MODE>(tab[pr], (int64_t)blockIdx.x - start[pr], (int64_t)start[pr + 1] - start[pr]);
+    grouped_pass_kernel(const PassArgs<T>* __restrict__ tab, const int* __restrict__ start, int nprob,
+                        int64_t items) {
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int pr = group_of(start, nprob, it);
+    pass_body<T, VW, VPL, MODE>(tab[pr], it - start[pr], (int64_t)start[pr + 1] - start[pr]);
+    __syncthreads();   // the item's shared-memory reduction is read before the next item writes it
+  }
 }
 
 template <typename T>
 cudaError_t launch_grouped_pass(int mode, int vw, int vpl, const PassArgs<T>* tab, const int* start,
-                                int64_t ctas, int nprob, size_t smem, cudaStream_t st) {
+                                int64_t ctas, int nprob, size_t smem, cudaStream_t st, int64_t grid) {
   if (ctas <= 0) return cudaSuccess;
   if (ctas > 2147483647LL) return cudaErrorInvalidValue;
+  const int64_t g = (grid > 0 && grid < ctas) ? grid : ctas;
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = allow_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)ctas, 256, smem, st>>>(tab, start, nprob);
+    kern<<<(unsigned)g, 256, smem, st>>>(tab, start, nprob, ctas);
     return cudaGetLastError();
   };
   if constexpr (sizeof(T) == 4) {
@@ -1403,9 +1411,9 @@ cudaError_t launch_grouped_pass(int mode, int vw, int vpl, const PassArgs<T>* ta
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_grouped_pass<float>(int, int, int, const PassArgs<float>*, const int*, int64_t, int,
-                                                size_t, cudaStream_t);
+                                                size_t, cudaStream_t, int64_t);
 template cudaError_t launch_grouped_pass<double>(int, int, int, const PassArgs<double>*, const int*, int64_t, int,
-                                                 size_t, cudaStream_t);
+                                                 size_t, cudaStream_t, int64_t);
 
 template <typename TP, typename TO>
 __global__ void grouped_colsum_kernel(const GColsum<TP, TO>* __restrict__ tab, const int* __restrict__ start,

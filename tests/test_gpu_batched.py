@@ -5,6 +5,8 @@
 * A problem's result does not depend on the rest of the batch: the same problem alone
   and inside a batch gives the same bits.
 * The grouped and per-problem modes agree to the accuracy both reach.
+* The autotuned grid of the persistent passes changes nothing in the result: forced grids
+  of one CTA per SM, eight per SM and one per item give the same bits as the tuned one.
 * Problems shaped like the 512-problem batch (m ~ U[5e3, m_max], n ~ U[32, 256],
   kappa log-U[1e2, 1e8], rho log-U[1e-8, 1e-1], BF16 sketch s = 4n), m capped so the
   oracle's reference solution stays quick: every problem that reports convergence is
@@ -65,6 +67,18 @@ def test_grouped_result_does_not_depend_on_the_batch(lsq, handle):
             sub.append(dict(A=probs[k]["A"], b=probs[k]["b"], m=m, n=n, s=4 * n, seed=k, x=zeros(n), r=zeros(m)))
         lsq.lsq_lsir_batched(handle, sub, "bf16x3", "f32", "f32", "f64", 1e-6)
         assert torch.equal(sub[0]["x"], probs[2]["x"]) and torch.equal(sub[0]["r"], probs[2]["r"]), others
+
+
+def test_pass_grid_choice_is_bit_identical(lsq, handle):
+    outs = []
+    for grid in (0, 152, 8 * 152, 1 << 30):
+        Ps, probs = _batch(GOOD[:6], 150)
+        st, sts, _ = lsq.lsq_lsir_batched(handle, probs, "bf16x3", "f32", "f32", "f64", 1e-6, {"batch_grid": grid})
+        assert st == 0
+        outs.append([(p["x"].cpu(), p["r"].cpu()) for p in probs])
+    for o in outs[1:]:
+        for (x0, r0), (x1, r1) in zip(outs[0], o):
+            assert torch.equal(x0, x1) and torch.equal(r0, r1)
 
 
 def test_grouped_and_per_problem_modes_agree(lsq, handle):
