@@ -31,7 +31,7 @@ void stage_sketch(Ctx& c, double* Y) {
     void* work = ws(c.h, "sparse", sparse_workspace(c.m, ncols, (int)c.s, sp.splits));
     KernTimer kt(c.h, K_SKETCH, c.o.timing);
     L(launch_sparse_sketch(sp, c.A, c.lda, c.b, c.m, c.n, (int)c.s, zeta, c.seed, cmax, work, Y, c.st));
-    c.h->launches += 3;
+    c.h->launches += 5;
     return;
   }
   int* kexp = static_cast<int*>(ws(c.h, "kexp", ncols * 4));

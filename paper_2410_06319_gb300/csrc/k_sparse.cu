@@ -9,15 +9,17 @@
 //  * grid kernel: per column c of [A | b] the exponent q_c of a fixed-point grid 2^-q_c
 //    with max|a_c| 2^q_c <= 2^(61 - h), h the bit length of the largest count, so no
 //    sum of a sketch row's entries leaves 62 bits.
-//  * sketch kernel: each CTA owns a block of CB columns (and a slice of the data rows)
-//    and adds the rounded entries (round half even on the grid, integer arithmetic on
-//    the FP64 bits) into int64 accumulators in shared memory with integer atomics: exact,
-//    so the result does not depend on the order.  A warp takes one data row per step,
-//    lane = (k, c): the zeta rows of a data row are distinct, so its lanes never collide.
-//  * finalize: the exact sum of the row slices, converted once to FP64, times 2^-q_c and
-//    zeta^-1/2 (the same operations in the same order as the definition, so Y is exact).
-// HBM: [A | b] is read once; the row table (16 bytes per data row) is re-read per column
-// block and stays in L2.
+//  * quantize kernel: [A | b] rounded once onto the column grids (round half even on the
+//    grid, integer arithmetic on the FP64 bits) into an int64 copy.
+//  * lists: an exclusive scan of the counts and a fill give, for every sketch row, the
+//    list of its (data row, sign) entries (a counting sort; the order within a list is
+//    whatever the atomics give, which the exact integer sums make irrelevant).
+//  * gather kernel: one CTA per sketch row adds (or subtracts) the int64 rows of its list,
+//    threads over the columns (coalesced rows), and writes the row of Y: the exact sum
+//    converted once to FP64, times 2^-q_c and zeta^-1/2 (the same operations as the
+//    definition, so Y is exact).
+// HBM: [A | b] read once and its int64 copy written once, then every data row of the copy
+// read zeta times (once per sketch row it lands in); no atomics on the data.
 #include <cstdint>
 
 #include "common.cuh"
@@ -117,114 +119,165 @@ __device__ __forceinline__ long long to_grid(uint64_t u, int q) {
   return (u >> 63) ? -v : v;
 }
 
-constexpr int kSpThreads = 512;
-
-template <int CB>
-__global__ void __launch_bounds__(kSpThreads)
-    sparse_sketch_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ b, int64_t m,
-                         int64_t n, int s, int zeta, const uint16_t* __restrict__ table,
-                         const int* __restrict__ qexp, long long* __restrict__ part, int64_t rows_per_split) {
-  extern __shared__ __align__(16) long long acc[];   // [s][CB]
-  const int64_t c0 = (int64_t)blockIdx.x * CB;
-  const int64_t split = blockIdx.y;
-  const int64_t ncols = n + 1;
-  for (int i = threadIdx.x; i < s * CB; i += blockDim.x) acc[i] = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  constexpr int KPW = 32 / CB;                  // table entries a lane group covers per step
-  const int k = lane / CB, cc = lane % CB;      // lane -> (target slot, column)
-  const int64_t c = c0 + cc;
-  const bool col_ok = c < ncols;
-  const int q = col_ok ? qexp[c] : 0;
+// Aq[j][c] = round(a_jc 2^q_c) for c < n, Aq[j][n] = round(b_j 2^q_n); rows of ncols int64.
+__global__ void __launch_bounds__(256)
+    sparse_quant_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ b, int64_t m,
+                        int64_t n, const int* __restrict__ qexp, long long* __restrict__ Aq, int rows_per_cta) {
   const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
   const uint64_t* bu = reinterpret_cast<const uint64_t*>(b);
-  const int64_t r0 = split * rows_per_split, r1 = min(m, r0 + rows_per_split);
-  for (int64_t j = r0 + warp; j < r1; j += nw) {
-    const uint64_t u = col_ok ? (c < n ? __ldcs(Au + j * lda + c) : __ldcs(bu + j)) : 0ull;
-    const long long v = to_grid(u, q);
-    // 32 / CB >= 8 lane groups: every slot of the row in one step
-    for (int kk = k; kk < zeta; kk += KPW) {
-      if (!col_ok) break;
-      const uint16_t t = table[j * kSpMaxZeta + kk];
-      const int row = t & 0x7FFF;
-      const long long sv = (t >> 15) ? -v : v;
-      atomicAdd(reinterpret_cast<unsigned long long*>(acc + row * CB + cc), (unsigned long long)sv);
+  const int64_t ncols = n + 1;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+  for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) {
+    const int q = qexp[c];
+    for (int64_t j = r0; j < r1; ++j) {
+      const uint64_t u = c < n ? __ldcs(Au + j * lda + c) : bu[j];
+      Aq[j * ncols + c] = to_grid(u, q);
     }
   }
+}
+
+// offsets = exclusive prefix sums of counts (s + 1 entries; one CTA of 1024 threads, s <= 16384)
+__global__ void __launch_bounds__(1024) sparse_scan_kernel(const unsigned* __restrict__ counts, int s,
+                                                           unsigned long long* __restrict__ offsets) {
+  __shared__ unsigned long long part[1024];
+  const int per = (s + 1023) / 1024;
+  const int i0 = threadIdx.x * per, i1 = min(s, i0 + per);
+  unsigned long long v = 0;
+  for (int i = i0; i < i1; ++i) v += counts[i];
+  part[threadIdx.x] = v;
   __syncthreads();
-  for (int i = threadIdx.x; i < s * CB; i += blockDim.x) {
-    const int cl = i / s, row = i % s;
-    const int64_t col = c0 + cl;
-    if (col < ncols) part[(split * ncols + col) * s + row] = acc[row * CB + cl];
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan of the chunk sums (Hillis-Steele)
+    const unsigned long long add = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  unsigned long long run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0ull;
+  for (int i = i0; i < i1; ++i) {
+    offsets[i] = run;
+    run += counts[i];
+  }
+  if (threadIdx.x == 1023) offsets[s] = part[1023];
+}
+
+// list[offsets[r] + slot] = j | sign << 63 for every entry (j, k) of the row table
+__global__ void sparse_fill_kernel(const uint16_t* __restrict__ table, int64_t m, int zeta,
+                                   const unsigned long long* __restrict__ offsets, unsigned* __restrict__ cursor,
+                                   unsigned long long* __restrict__ list) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  for (int k = 0; k < zeta; ++k) {
+    const uint16_t tv = table[j * kSpMaxZeta + k];
+    const int r = tv & 0x7FFF;
+    const unsigned slot = atomicAdd(cursor + r, 1u);
+    list[offsets[r] + slot] = (unsigned long long)j | ((unsigned long long)(tv >> 15) << 63);
   }
 }
 
-__global__ void sparse_finalize_kernel(const long long* __restrict__ part, int splits, int64_t ncols, int s,
-                                       const int* __restrict__ qexp, double scale, double* __restrict__ Y) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= ncols * s) return;
-  const int64_t c = idx / s;
-  long long t = 0;
-  for (int sp = 0; sp < splits; ++sp) t += part[(int64_t)sp * ncols * s + idx];
-  Y[idx] = ldexp((double)t, -qexp[c]) * scale;
+// Y[c][r] = 2^-q_c zeta^-1/2 sum over the list of r of +-Aq[j][c]; one CTA per sketch row r
+constexpr int kSpGatherThreads = 256;
+constexpr int kSpGatherPer = 5;        // columns per thread: ncols <= 1280
+__global__ void __launch_bounds__(kSpGatherThreads)
+    sparse_gather_kernel(const long long* __restrict__ Aq, int64_t ncols, int s,
+                         const unsigned long long* __restrict__ offsets, const unsigned long long* __restrict__ list,
+                         const int* __restrict__ qexp, double scale, double* __restrict__ Y) {
+  const int r = blockIdx.x;
+  const unsigned long long e0 = offsets[r], e1 = offsets[r + 1];
+  long long acc[kSpGatherPer];
+#pragma unroll
+  for (int i = 0; i < kSpGatherPer; ++i) acc[i] = 0;
+  unsigned long long e = e0;
+  for (; e + 4 <= e1; e += 4) {      // four rows in flight per thread
+    unsigned long long w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = __ldg(list + e + u);
+    long long v[4][kSpGatherPer];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long* row = Aq + (int64_t)(w[u] & 0x7FFFFFFFFFFFFFFFull) * ncols;
+#pragma unroll
+      for (int i = 0; i < kSpGatherPer; ++i) {
+        const int64_t c = threadIdx.x + (int64_t)i * kSpGatherThreads;
+        v[u][i] = c < ncols ? __ldcs(row + c) : 0ll;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < kSpGatherPer; ++i) acc[i] += (w[u] >> 63) ? -v[u][i] : v[u][i];
+  }
+  for (; e < e1; ++e) {
+    const unsigned long long w = __ldg(list + e);
+    const long long* row = Aq + (int64_t)(w & 0x7FFFFFFFFFFFFFFFull) * ncols;
+#pragma unroll
+    for (int i = 0; i < kSpGatherPer; ++i) {
+      const int64_t c = threadIdx.x + (int64_t)i * kSpGatherThreads;
+      const long long v = c < ncols ? __ldcs(row + c) : 0ll;
+      acc[i] += (w >> 63) ? -v : v;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kSpGatherPer; ++i) {
+    const int64_t c = threadIdx.x + (int64_t)i * kSpGatherThreads;
+    if (c < ncols) Y[c * s + r] = ldexp((double)acc[i], -qexp[c]) * scale;
+  }
 }
 
-size_t sparse_workspace(int64_t m, int64_t ncols, int s, int splits) {
-  return (size_t)m * kSpMaxZeta * 2 + (size_t)s * 4 + (size_t)ncols * 4 +
-         (size_t)splits * (size_t)ncols * (size_t)s * 8 + 1024;
+namespace {
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+}  // namespace
+
+size_t sparse_workspace(int64_t m, int64_t ncols, int s, int /*splits*/) {
+  return al256((size_t)m * kSpMaxZeta * 2) + al256((size_t)s * 4) + al256((size_t)ncols * 4) +
+         al256((size_t)(s + 1) * 8) + al256((size_t)s * 4) + al256((size_t)m * kSpMaxZeta * 8) +
+         al256((size_t)m * (size_t)ncols * 8) + 1024;
 }
 
-SparsePlan plan_sparse(int64_t m, int64_t ncols, int s, int num_sms) {
+SparsePlan plan_sparse(int64_t m, int64_t ncols, int s, int /*num_sms*/) {
   SparsePlan p{};
-  p.cb = (int64_t)s * 4 * 8 <= 200 * 1024 ? 4 : ((int64_t)s * 2 * 8 <= 200 * 1024 ? 2 : 1);
-  p.colblocks = (int)((ncols + p.cb - 1) / p.cb);
-  const int per_sm = (int)((227 * 1024) / ((size_t)s * p.cb * 8));
-  const int64_t want = 2ll * num_sms * (per_sm > 0 ? per_sm : 1);
-  int64_t splits = (want + p.colblocks - 1) / p.colblocks;
-  const int64_t max_by_rows = (m + 4095) / 4096;          // at least 4096 data rows a split
-  if (splits > max_by_rows) splits = max_by_rows;
-  const double budget = 2147483648.0;                      // int64 partials, at most 2 GiB
-  const int64_t max_by_mem = (int64_t)(budget / (8.0 * (double)ncols * s));
-  if (splits > max_by_mem) splits = max_by_mem;
-  if (splits < 1) splits = 1;
-  p.rows_per_split = (m + splits - 1) / splits;
-  p.splits = (int)((m + p.rows_per_split - 1) / p.rows_per_split);
-  p.smem = (size_t)s * p.cb * 8;
+  p.cb = (int)ncols;          // one gather CTA covers every column of a sketch row
+  p.colblocks = 1;
+  p.splits = 1;
+  p.rows_per_split = m;
+  p.smem = 0;
+  (void)s;
   return p;
 }
 
 cudaError_t launch_sparse_sketch(const SparsePlan& p, const double* A, int64_t lda, const double* b, int64_t m,
                                  int64_t n, int s, int zeta, uint64_t seed,
                                  const unsigned long long* cmax_bits, void* work, double* Y, cudaStream_t st) {
+  (void)p;
   if (zeta < 1 || zeta > kSpMaxZeta || zeta > s || s > 16384) return cudaErrorInvalidValue;
   const int64_t ncols = n + 1;
+  if (ncols > (int64_t)kSpGatherThreads * kSpGatherPer) return cudaErrorInvalidValue;
   auto* base = static_cast<unsigned char*>(work);
-  auto* table = reinterpret_cast<uint16_t*>(base);
-  size_t off = ((size_t)m * kSpMaxZeta * 2 + 255) & ~(size_t)255;
-  auto* counts = reinterpret_cast<unsigned*>(base + off);
-  off = (off + (size_t)s * 4 + 255) & ~(size_t)255;
-  auto* qexp = reinterpret_cast<int*>(base + off);
-  off = (off + (size_t)ncols * 4 + 255) & ~(size_t)255;
-  auto* part = reinterpret_cast<long long*>(base + off);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* q = base + off;
+    off += al256(bytes);
+    return q;
+  };
+  auto* table = reinterpret_cast<uint16_t*>(take((size_t)m * kSpMaxZeta * 2));
+  auto* counts = reinterpret_cast<unsigned*>(take((size_t)s * 4));
+  auto* qexp = reinterpret_cast<int*>(take((size_t)ncols * 4));
+  auto* offsets = reinterpret_cast<unsigned long long*>(take((size_t)(s + 1) * 8));
+  auto* cursor = reinterpret_cast<unsigned*>(take((size_t)s * 4));
+  auto* list = reinterpret_cast<unsigned long long*>(take((size_t)m * kSpMaxZeta * 8));
+  auto* Aq = reinterpret_cast<long long*>(take((size_t)m * (size_t)ncols * 8));
   cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)s * 4, st);
   if (e != cudaSuccess) return e;
-  sparse_rows_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, s, zeta, (uint32_t)seed,
-                                                                  (uint32_t)(seed >> 32), table, counts);
-  sparse_grid_kernel<<<1, 1024, 0, st>>>(cmax_bits, ncols, counts, s, qexp);
-  dim3 grid((unsigned)p.colblocks, (unsigned)p.splits);
-  auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t ee = allow_dyn_smem(kern, p.smem);
-    if (ee != cudaSuccess) return ee;
-    kern<<<grid, kSpThreads, p.smem, st>>>(A, lda, b, m, n, s, zeta, table, qexp, part, p.rows_per_split);
-    return cudaGetLastError();
-  };
-  if (p.cb == 4) e = go(sparse_sketch_kernel<4>);
-  else if (p.cb == 2) e = go(sparse_sketch_kernel<2>);
-  else e = go(sparse_sketch_kernel<1>);
+  e = cudaMemsetAsync(cursor, 0, (size_t)s * 4, st);
   if (e != cudaSuccess) return e;
-  const int64_t total = ncols * s;
-  sparse_finalize_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, p.splits, ncols, s, qexp,
-                                                                          1.0 / sqrt((double)zeta), Y);
+  const unsigned row_ctas = (unsigned)((m + 255) / 256);
+  sparse_rows_kernel<<<row_ctas, 256, 0, st>>>(m, s, zeta, (uint32_t)seed, (uint32_t)(seed >> 32), table, counts);
+  sparse_grid_kernel<<<1, 1024, 0, st>>>(cmax_bits, ncols, counts, s, qexp);
+  constexpr int kRows = 16;
+  sparse_quant_kernel<<<(unsigned)((m + kRows - 1) / kRows), 256, 0, st>>>(A, lda, b, m, n, qexp, Aq, kRows);
+  sparse_scan_kernel<<<1, 1024, 0, st>>>(counts, s, offsets);
+  sparse_fill_kernel<<<row_ctas, 256, 0, st>>>(table, m, zeta, offsets, cursor, list);
+  sparse_gather_kernel<<<(unsigned)s, kSpGatherThreads, 0, st>>>(Aq, ncols, s, offsets, list, qexp,
+                                                                 1.0 / sqrt((double)zeta), Y);
   return cudaGetLastError();
 }
 

@@ -146,9 +146,9 @@ cudaError_t launch_sketch_reduce(const void* partial, bool partial_f64, int spli
 // sums): Y = Omega [A | b], FP64, column-major with ld = s.  cmax_bits: the column maxima
 // of the cast pass.  work: sparse_workspace() bytes.
 struct SparsePlan {
-  int cb;                 // columns per CTA (shared-memory accumulators s x cb int64)
-  int colblocks;
-  int splits;             // slices of the data rows (partials summed exactly)
+  int cb;                 // columns per gather CTA (all n + 1: one CTA per sketch row)
+  int colblocks;          // 1
+  int splits;             // 1 (each sketch row is summed whole)
   int64_t rows_per_split;
   size_t smem;
 };
