@@ -332,9 +332,19 @@ __device__ __forceinline__ uint32_t swz_chunk(int row, int kc) {
 // grp.start[p] <= b < grp.start[p + 1]; its local index gives (tile, column group, split)
 // in that problem's grid; the problem's arguments come from grp.tab[p] and its tensor map
 // from grp.maps[p] (global memory, written by the host before the launch).
-template <int FMT, int STAGES, int ROWB, int NT, bool DEFER, bool GROUPED>
+//
+// SHARE (deferred mode, two column groups): the CTAs of the two column groups of a
+// (tile, split) form a cluster and share the sketch operand: each generates half of the
+// 128-row tile (rows 64 r .. 64 r + 63 for cluster rank r) into its own shared memory and
+// copies it into its partner's stage with one bulk copy per generator warp, completing the
+// partner's full barrier; each MMA commit releases the stage in both CTAs (the empty
+// barriers count two arrivals), so neither CTA overwrites a stage its partner still reads.
+// Before exiting, the producer waits for the last release of every stage, so no arrival
+// from the partner can land in a CTA that has exited.
+template <int FMT, int STAGES, int ROWB, int NT, bool DEFER, bool GROUPED, bool SHARE = false>
 __global__ void __launch_bounds__(sk_threads(DEFER), 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap tmB, const SketchTcArgs a_in, const SketchGroup grp) {
+  static_assert(!SHARE || (DEFER && !GROUPED), "operand sharing runs in deferred mode, one problem");
   constexpr int GF = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;   // format of the sketch operand
   constexpr int EB = (GF == FMT_E4M3) ? 1 : 2;                // bytes per element
   constexpr int BK = ROWB / EB;                               // K elements per stage
@@ -377,11 +387,14 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
   const int64_t k_end = min(a.m, k_begin + a.kchunk);
   const int nk = (int)((k_end - k_begin + BK - 1) / BK);
   const int chunk = a.bn / a.nsub;
+  constexpr uint32_t HALF = S_BYTES / 2;                      // the half tile a CTA generates (SHARE)
+  constexpr int GCH = SHARE ? NCHUNK / 2 : NCHUNK;            // chunks this CTA generates per stage
+  const uint32_t rank = SHARE ? cl_rank() : 0u;
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) {
       mbar_init(full0 + 8 * st, DEFER ? 1 + kSkGenWarps : kSkFixWarps + 1);
-      mbar_init(empty0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, SHARE ? 2 : 1);
       mbar_init(genned0 + 8 * st, kSkGenWarps);
       mbar_init(fixed0 + 8 * st, kSkFixWarps);
       qcnt[st] = 0;
@@ -397,6 +410,7 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tslot;
+  if constexpr (SHARE) cl_sync();   // the partner's barriers are initialised before any copy or commit
 
   if (warp == 0) {
     // ---------------- TMA producer: NT planes x nsub boxes of [chunk rows x ROWB bytes]
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
         const int st = ks % STAGES;
         const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
         if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
-        mbar_arrive_expect_tx(full0 + 8 * st, (uint32_t)NT * b_bytes);
+        mbar_arrive_expect_tx(full0 + 8 * st, (uint32_t)NT * b_bytes + (SHARE ? HALF : 0u));
         const uint32_t sb = smem_u32(smem + st * stage_bytes + S_BYTES);
         const int64_t kx = k_begin + (int64_t)ks * BK;
         const int32_t kin = (int32_t)(kx % kBtBlock), kblk = (int32_t)(kx / kBtBlock);
@@ -419,6 +433,13 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
           for (int c = 0; c < a.nsub; ++c)
             tma_load_3d(sb + t * b_bytes + (uint32_t)(c * chunk * ROWB), tmp, kin,
                         (int32_t)(t * a.rows_per_plane + ng * a.bn + c * chunk), kblk, full0 + 8 * st);
+      }
+      if constexpr (SHARE) {
+        // tail: the last release of every stage (both MMAs) has arrived here
+        for (int st = 0; st < STAGES && st < nk; ++st) {
+          const int last = st + ((nk - 1 - st) / STAGES) * STAGES;
+          if (!mbar_wait(empty0 + 8 * st, (uint32_t)(last / STAGES) & 1u, a.err, DEV_TIMEOUT_EMPTY)) break;
+        }
       }
     }
   } else if (warp == 1) {
@@ -448,7 +469,8 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
             }
           }
         }
-        tc_commit(empty0 + 8 * st);
+        if constexpr (SHARE) tc_commit_mc(empty0 + 8 * st, (uint16_t)0x3);
+        else tc_commit(empty0 + 8 * st);
       }
       tc_commit(done_bar);
     }
@@ -466,13 +488,19 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
       uint8_t* S = smem + st * stage_bytes;
       uint32_t* qb = qbuf + st * (kSkQMax * 3);
       const int64_t kbase = k_begin + (int64_t)ks * BK;
-      for (int c = g; c < NCHUNK; c += kSkGenThreads) {
-        const int row = c / CPR, kc = c % CPR;
+      // SPL threads per 16-byte chunk (two when a half tile has fewer chunks than there are
+      // generator threads: each then takes one Philox call and writes 8 bytes)
+      constexpr int SPL = (SHARE && EB == 2 && GCH * 2 <= kSkGenThreads) ? 2 : 1;
+      constexpr int HPI = (EPC / 4) / SPL;   // Philox calls per thread and chunk
+      for (int itm = g; itm < GCH * SPL; itm += kSkGenThreads) {
+        const int c = itm / SPL, hp = itm % SPL;
+        const int row = c / CPR + (int)rank * 64, kc = c % CPR;
         const uint32_t i = (uint32_t)(mt * 128 + row);
         const uint64_t q0 = (uint64_t)(kbase + kc * EPC) >> 2;
-        uint32_t w[4];
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int h = 0; h < EPC / 4; ++h) {
+        for (int hh = 0; hh < HPI; ++hh) {
+          const int h = hp * HPI + hh;
           const uint4 x = philox4x32_10(gauss_counter(q0 + h, i), a.k0, a.k1);
           uint32_t e0, o0, e1, o1;
           const bool ok0 = gauss_pair_fast<GF>(x.x, x.y, e0, o0);
@@ -512,16 +540,31 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
             }
           }
           if constexpr (EB == 2) {
-            w[2 * h] = e0 | (o0 << 16);
-            w[2 * h + 1] = e1 | (o1 << 16);
+            w[2 * hh] = e0 | (o0 << 16);
+            w[2 * hh + 1] = e1 | (o1 << 16);
           } else {
-            w[h] = e0 | (o0 << 8) | (e1 << 16) | (o1 << 24);
+            w[hh] = e0 | (o0 << 8) | (e1 << 16) | (o1 << 24);
           }
         }
-        *reinterpret_cast<uint4*>(S + swz_chunk<ROWB>(row, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+        if constexpr (SPL == 1)
+          *reinterpret_cast<uint4*>(S + swz_chunk<ROWB>(row, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+        else
+          *reinterpret_cast<uint2*>(S + swz_chunk<ROWB>(row, kc) + 8 * hp) = make_uint2(w[0], w[1]);
       }
       fence_proxy_async_smem();
       __syncwarp();
+      if constexpr (SHARE) {
+        // this warp's 32 items cover 32 / SPL chunks, whole rows of the tile: one contiguous run
+        constexpr int SPLc = (EB == 2 && GCH * 2 <= kSkGenThreads) ? 2 : 1;
+        static_assert(GCH * SPLc <= kSkGenThreads && (GCH * SPLc) % 32 == 0 && (32 / SPLc) % CPR == 0,
+                      "one item per generator thread, whole rows per warp");
+        const int i0 = (warp - 2) * 32;
+        if (lane == 0 && i0 < GCH * SPLc) {
+          const uint32_t off = (uint32_t)((i0 / SPLc / CPR + (int)rank * 64) * ROWB);
+          const uint32_t src = smem_u32(S) + off;
+          bulk_s2s(cl_map(src, rank ^ 1u), src, (uint32_t)(32 / SPLc) * 16u, cl_map(full0 + 8 * st, rank ^ 1u));
+        }
+      }
       if (lane == 0) mbar_arrive(DEFER ? full0 + 8 * st : genned0 + 8 * st);
     }
     if (DEFER && lane == 0) a.rec_cnt[cta * kSkGenWarps + (warp - 2)] = wcnt;
@@ -580,6 +623,7 @@ __global__ void __launch_bounds__(sk_threads(DEFER), 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (SHARE) cl_sync();   // neither CTA leaves while its partner may still copy or commit into it
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, (uint32_t)a.tmem_cols);
@@ -692,6 +736,25 @@ static cudaError_t launch_tc_inst(const SketchPlan& p, const CUtensorMap& tm, co
                                   cudaStream_t st) {
   dim3 grid((unsigned)p.mtiles, (unsigned)p.ngroups, (unsigned)p.splits);
   const SketchGroup none{};
+  if (a.rec && p.ngroups == 2) {
+    // the two column groups of a (tile, split) share the generated operand (a cluster of two)
+    auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, true, false, true>;
+    cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(sk_threads(true));
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 2;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tm, a, none);
+  }
   if (a.rec) {
     auto kern = sketch_tc_kernel<FMT, STAGES, ROWB, NT, true, false>;
     cudaError_t e = allow_dyn_smem(kern, (size_t)p.smem);
@@ -808,6 +871,7 @@ constexpr int kFixThreads = 512;
 struct SketchFixArgs {
   int64_t s, m, n, ncols, s_pad, lda;
   int bn;
+  int share;   // the two column groups shared the operand: read both CTAs' lists
   uint32_t k0, k1, cap;
   const uint64_t* rec;
   const uint32_t* rec_cnt;
@@ -828,22 +892,26 @@ template <int FMT>
 __global__ void __launch_bounds__(kFixThreads)
     sketch_fix_kernel(const SketchFixArgs f) {
   constexpr int GF = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;
-  __shared__ uint32_t off[kSkGenWarps + 1];
+  __shared__ uint32_t off[2 * kSkGenWarps + 1];
   __shared__ int ovf;
   __shared__ int wsum[kFixThreads / 32];
   __shared__ FixRec kept[kFixThreads];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t cta = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+  // with a shared operand, the partner CTA (other column group) generated half of the rows
+  const int64_t peer = blockIdx.x + (int64_t)gridDim.x * ((blockIdx.y ^ 1u) + (int64_t)gridDim.y * blockIdx.z);
+  const int nl = f.share ? 2 * kSkGenWarps : kSkGenWarps;
+  auto list_of = [&](int w) { return (w < kSkGenWarps ? cta : peer) * kSkGenWarps + (w % kSkGenWarps); };
   if (tid == 0) {
     uint32_t o = 0;
     int bad = 0;
-    for (int w = 0; w < kSkGenWarps; ++w) {
-      const uint32_t c = f.rec_cnt[cta * kSkGenWarps + w];
+    for (int w = 0; w < nl; ++w) {
+      const uint32_t c = f.rec_cnt[list_of(w)];
       if (c > f.cap) bad = 1;
       off[w] = o;
       o += min(c, f.cap);
     }
-    off[kSkGenWarps] = o;
+    off[nl] = o;
     ovf = bad;
   }
   __syncthreads();
@@ -851,7 +919,7 @@ __global__ void __launch_bounds__(kFixThreads)
     if (tid == 0) atomicExch(f.overflow, 1);
     return;
   }
-  const uint32_t total = off[kSkGenWarps];
+  const uint32_t total = off[nl];
   const int64_t split = blockIdx.z;
   const int64_t col = (int64_t)blockIdx.y * f.bn + tid;
   const bool has_col = tid < f.bn && col < f.ncols;
@@ -866,7 +934,7 @@ __global__ void __launch_bounds__(kFixThreads)
     if (idx < total) {
       int w = 0;
       while (idx >= off[w + 1]) ++w;
-      const uint64_t pk = f.rec[(cta * kSkGenWarps + w) * (int64_t)f.cap + (idx - off[w])];
+      const uint64_t pk = f.rec[list_of(w) * (int64_t)f.cap + (idx - off[w])];
       r.i = (uint32_t)(pk & 0xFFFFu);
       r.j0 = pk >> 16;
       const uint4 x = philox4x32_10(gauss_counter(r.j0 >> 2, r.i), f.k0, f.k1);
@@ -927,6 +995,7 @@ cudaError_t launch_sketch_fix(const SketchPlan& p, uint64_t seed, const uint64_t
   f.s_pad = p.s_pad;
   f.lda = lda;
   f.bn = p.bn;
+  f.share = p.ngroups == 2 ? 1 : 0;   // launch_sketch_tc shares the operand exactly then (deferred mode)
   f.k0 = (uint32_t)seed;
   f.k1 = (uint32_t)(seed >> 32);
   f.cap = cap;

@@ -20,9 +20,10 @@ def gpu_sketch(lsq, handle, A, b, s, fmt, seed, **opts):
 
 
 @pytest.mark.parametrize("fmt", FMTS)
-def test_sketch_extracts_columns_exactly(lsq, handle, fmt):
-    """With one-hot columns each Y entry is a single product: exact on both sides."""
-    m, n, s = 4133, 40, 200
+@pytest.mark.parametrize("m,n,s", [(4133, 40, 200), (3100, 600, 640)])
+def test_sketch_extracts_columns_exactly(lsq, handle, fmt, m, n, s):
+    """With one-hot columns each Y entry is a single product: exact on both sides.  n = 600
+    takes two column groups, whose CTAs share the generated operand (half each)."""
     r = np.random.default_rng(1)
     perm = r.choice(m, n + 1, replace=False)
     A = np.zeros((m, n))
@@ -85,11 +86,12 @@ def test_sketch_full_size_sampled_entries(lsq, handle):
 
 
 @pytest.mark.parametrize("fmt", ["f16", "bf16", "e4m3", "bf16x3"])
-def test_sketch_deferred_correction_matches_exact_mode(lsq, handle, fmt):
+@pytest.mark.parametrize("m,n,s", [(20000, 70, 256), (12000, 700, 768)])
+def test_sketch_deferred_correction_matches_exact_mode(lsq, handle, fmt, m, n, s):
     """The GEMM on FP32 estimates plus the correction of near-midpoint entries gives the
     product with fl_s(G) itself: same values as resolving them inside the GEMM, up to the
-    FP32 accumulation order, and bit-identical from run to run."""
-    m, n, s = 20000, 70, 256
+    FP32 accumulation order, and bit-identical from run to run.  n = 700: two column
+    groups sharing the generated operand, with the corrections read from both lists."""
     P = randsvd_problem(m, n, 1e3, rho=1e-2, seed=11)
     got = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 5)
     again = gpu_sketch(lsq, handle, P.A, P.b, s, fmt, 5)
