@@ -162,8 +162,8 @@ FORMATS = {
 }
 
 #: unit roundoff of each format (2^-(mantissa bits + 1)); "bf16x3" is the
-#: three-term BF16 split of A (24 significant bits) with FP32 accumulation,
-#: i.e. single precision.
+#: single-precision cast of A carried as its three-term BF16 split, with FP32
+#: accumulation, i.e. single precision.
 UNIT_ROUNDOFF = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "f16": 2.0 ** -11,
                  "bf16": 2.0 ** -8, "e4m3": 2.0 ** -4, "bf16x3": 2.0 ** -24}
 

@@ -48,15 +48,18 @@ def column_scale_exponents(M, fmt):
 def cast_scaled(A, b, fmt):
     """Return (A_s, b_s, kA, kb): fl_s(A 2^kA), fl_s(b 2^kb) as FP64 arrays.
 
-    For ``bf16x3`` (a split-term reading of a single-precision
-    sketch on BF16 tensor cores) A_s is the exact sum hi + lo + lo2 of the
-    three BF16 terms of ``rng.split3``.
+    For ``bf16x3`` (u_s = single on BF16 tensor cores) the operand is
+    y = fl_single(A 2^k), Sec. 3.2's A_s for single precision, carried as the
+    three BF16 terms hi + lo + lo2 of ``rng.split3(y)``.  A_s is their exact
+    sum: y itself, except where y - hi - lo falls below BF16's normal range
+    (|y| below about 2^-110), where lo2 is rounded on BF16's subnormal grid.
     """
     Ab = np.concatenate([np.asarray(A, dtype=np.float64),
                          np.asarray(b, dtype=np.float64).reshape(-1, 1)], axis=1)
     k = column_scale_exponents(Ab, fmt)
     if fmt == "bf16x3":
-        hi, lo, lo2 = rng.split3(np.ldexp(Ab, k[None, :]), "bf16")
+        y = rng.round_to_format(np.ldexp(Ab, k[None, :]), "f32")
+        hi, lo, lo2 = rng.split3(y, "bf16")
         As = hi + lo + lo2
     else:
         As = rng.round_to_format(np.ldexp(Ab, k[None, :]), fmt)

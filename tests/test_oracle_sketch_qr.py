@@ -158,6 +158,29 @@ def test_split3_carries_single_precision():
     assert np.all(np.abs(lo) <= 2.0 ** -8 * np.abs(hi) + 1e-300)
 
 
+def test_bf16x3_operand_is_the_single_precision_cast():
+    """Sec. 3.2 with u_s = single: the BF16X3 operand is fl_single(2^k A), carried exactly by
+    three BF16 terms (numpy's own FP32 conversion is the reference).  Entries 2^-130 below
+    their column's maximum put the third term on BF16's subnormal grid, the one place the
+    terms may miss y (by at most half its spacing, 2^-134)."""
+    r = np.random.default_rng(12)
+    A = r.standard_normal((3000, 7)) * np.exp(r.uniform(-30, 30, (1, 7)))
+    A[::17, 3] *= 2.0 ** -60
+    A[::13, 5] *= 2.0 ** -130
+    b = r.standard_normal(3000)
+    As, bs, kA, kb = sketch.cast_scaled(A, b, "bf16x3")
+    y = np.ldexp(A, kA[None, :]).astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(As - y) <= 2.0 ** -134)
+    deep = np.abs(y) < 2.0 ** -100
+    assert deep.sum() > 100 and np.array_equal(As[~deep], y[~deep])
+    assert np.array_equal(bs, np.ldexp(b, kb).astype(np.float32).astype(np.float64))
+    for t in rng.split3(y, "bf16"):
+        assert np.array_equal(rng.round_to_format(t, "bf16"), t)
+    # a split of the FP64 entries (no single-precision cast first) is a different operand
+    hi, lo, lo2 = rng.split3(np.ldexp(A, kA[None, :]), "bf16")
+    assert np.mean((hi + lo + lo2) != y) > 0.2
+
+
 def test_split_sketch_restores_the_good_regime():
     """Sec. 3.4: with the single-precision split sketch kappa(A R^-1) stays ~3 at kappa(A) = 1e6."""
     P = paper_problem(1e6, seed=2)
