@@ -687,7 +687,10 @@ def run_ours(args):
     except Exception as exc:
         secondary = {"error": f"{type(exc).__name__}: {exc}"}
 
-    # ---- batched configuration: 512 uneven problems in one grouped call
+    # ---- batched configuration: 512 uneven problems in one grouped call (the headline
+    # handle's workspace -- tens of GB at m = 4e6 -- is released first)
+    h.close()
+    torch.cuda.empty_cache()
     batched = None
     if rank == 0 and not args.no_batched:
         try:

@@ -50,8 +50,8 @@ extern "C" {
 /* Precisions.  F16 = IEEE half (the paper's "half"), BF16 and E4M3 are the
  * GB300 tensor-core formats (sketch only), F32 = single, F64 = double.
  * BF16X3 (sketch only) = single precision on BF16 tensor cores: the sketch
- * operand is fl_bf16(G) and each scaled entry of [A | b] is split exactly into
- * three BF16 terms hi + lo + lo2 (24 significant bits), all products
+ * operand is fl_bf16(G) and each scaled entry y = fl32(2^k x) of [A | b] is
+ * carried by its exact three-term BF16 split hi + lo + lo2, all products
  * accumulated in FP32; its unit roundoff is taken as 2^-24. */
 typedef enum lsq_prec {
   LSQ_AUTO = -1,   /* sketch precision only (lsq_lsqr, lsq_lsir and their host/batched forms):
@@ -220,7 +220,10 @@ const char* lsq_last_cuda_error(const lsq_handle* h);
  * that precision.  The FP32 accumulation adds a relative error of about
  * 2^-24 sqrt(k/2) per entry of Y for splits of k rows (k is near m / 5 at the
  * largest m): negligible against the cast for F16/BF16/E4M3, but for BF16X3
- * at m in the millions it, not the cast, sets kappa(A R^-1).
+ * at m in the millions it, not the cast, sets kappa(A R^-1).  u_w = F32 with
+ * u_s = BF16X3 forms the FP32 working copy of A (m x n floats of workspace, as
+ * lsq_lsqr does) and the cast reads it where that is exact; any other u_w
+ * forms no copy.  Y is the same bit for bit either way.
  * Out: Y, device FP64, s x (n+1) column-major with leading dimension s; its
  * last column is Omega b (used for x_s = R^-1 Q^T Omega b, Sec. 4).
  */

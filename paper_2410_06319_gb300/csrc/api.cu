@@ -19,8 +19,9 @@ float* stage_cast(Ctx& c) {
   return a32;
 }
 
-// Alg. 1 (sketch) -> Y (s x (n+1), column-major, FP64).
-void stage_sketch(Ctx& c, double* Y) {
+// Alg. 1 (sketch) -> Y (s x (n+1), column-major, FP64).  a32: the FP32 copy of A left by
+// stage_cast (or null); the BF16X3 cast reads it.
+void stage_sketch(Ctx& c, double* Y, const float* a32) {
   const int fmt = fmt_of(c.us);
   const int64_t ncols = c.n + 1;
   auto* cmax = static_cast<unsigned long long*>(ws(c.h, "cmax", ncols * 8));
@@ -47,7 +48,7 @@ void stage_sketch(Ctx& c, double* Y) {
       StageTimer tt(c.h, ST_CAST);
       L(launch_scale_exps(cmax, ncols, t, kexp, c.st));
       Bt = ws(c.h, "bt", bt_bytes(fmt, c.m, rows));
-      L(launch_cast_transpose(fmt, c.A, c.lda, c.b, c.m, c.n, kexp, Bt, rows, c.st));
+      L(launch_cast_transpose(fmt, c.A, c.lda, c.b, a32, c.lda32, c.m, c.n, kexp, Bt, rows, c.st));
     }
     StageTimer tt(c.h, ST_SKETCH);
     CUtensorMap tm;
@@ -521,7 +522,7 @@ Front run_front(Ctx& c, double* x, lsq_info* info) {
     for (const lsq_prec f : {LSQ_BF16, LSQ_BF16X3, LSQ_F64}) {
       c.us = f;
       info->sketches += 1;
-      stage_sketch(c, Yw);
+      stage_sketch(c, Yw, fr.a32);
       stage_qr(c, Yw, R, fr.x0, &fr.rc);
       const double k = read_scalar(c, fr.rc.kappa);
       check_dev_error(c.h);
@@ -532,7 +533,7 @@ Front run_front(Ctx& c, double* x, lsq_info* info) {
     const double* Y = c.o.Y_in;
     if (!Y) {
       double* Yw = static_cast<double*>(ws(c.h, "Y", (size_t)c.s * (c.n + 1) * 8));
-      stage_sketch(c, Yw);
+      stage_sketch(c, Yw, fr.a32);
       Y = Yw;
       info->sketches += 1;
     }
@@ -664,10 +665,11 @@ lsq_status lsq_sketch(lsq_handle* h, const double* A, const double* b, int64_t m
   lsq_status v = validate(c, true);
   if (v != LSQ_OK) return v;
   if (!Y || u_s == LSQ_AUTO) return LSQ_E_INVAL;   // AUTO needs the QR that follows the sketch
-  c.uw = LSQ_F64;  // no FP32 working copy needed
+  // the FP32 working copy is formed only where the BF16X3 cast reads it
+  if (!(u_s == LSQ_BF16X3 && u_w == LSQ_F32)) c.uw = LSQ_F64;
   return run_guarded(h, nullptr, [&]() {
-    stage_cast(c);
-    stage_sketch(c, Y);
+    const float* a32 = stage_cast(c);
+    stage_sketch(c, Y, a32);
     return LSQ_OK;
   });
 }
@@ -686,7 +688,7 @@ lsq_status lsq_qr_r(lsq_handle* h, const double* A, const double* b, int64_t m, 
       c.uw = LSQ_F64;
       stage_cast(c);
       double* Yw = static_cast<double*>(ws(c.h, "Y", (size_t)c.s * (c.n + 1) * 8));
-      stage_sketch(c, Yw);
+      stage_sketch(c, Yw, nullptr);
       Y = Yw;
     }
     double* Rw = R ? R : static_cast<double*>(ws(c.h, "R", (size_t)c.n * c.n * 8));

@@ -419,7 +419,7 @@ lsq_status lsq_batch_grouped(lsq_handle* h, int32_t nprob, const lsq_problem* pr
       szY[p] = (size_t)b.s[p] * (b.n[p] + 1) * 8;
       cmx[p] = cdiv(b.m[p], kGroupedColmaxRows);
       exps[p] = cdiv(b.n[p] + 1, 256);
-      castc[p] = (bt_blocks(b.m[p]) * kBtBlock / 32) * cdiv(rows, 32);
+      castc[p] = cast_row_tiles(fmt, b.m[p]) * cdiv(rows, 32);
       skc[p] = (int64_t)pl.mtiles * pl.ngroups * pl.splits;
       redc[p] = cdiv(b.s[p], 256) * (b.n[p] + 1);
     }
@@ -441,7 +441,7 @@ lsq_status lsq_batch_grouped(lsq_handle* h, int32_t nprob, const lsq_problem* pr
       g.kexp = aK.at<int>(p);
       g.Bt = aBt.at<void>(p);
       g.plane_rows = (int64_t)pl.ngroups * pl.bn;
-      g.cast_gx = bt_blocks(b.m[p]) * kBtBlock / 32;
+      g.cast_gx = cast_row_tiles(fmt, b.m[p]);
       tcast[p] = g;
     }
     {

@@ -1,5 +1,6 @@
 // Exact rounding of FP64 values into the sketch formats on integer units
-// (Sec. 3.2's A_s = fl_s(2^k A); the three-term BF16 split hi + lo + lo2).
+// (Sec. 3.2's A_s = fl_s(2^k A)), and the BF16X3 operand: y = fl32(2^k A)
+// carried as its exact three-term BF16 split hi + lo + lo2.
 //
 // GB300's FP64 pipe, and FP64 conversions, are narrow.  Rounding an FP64 value
 // to a format with P significant bits is exact integer arithmetic on its
@@ -10,6 +11,7 @@
 // check it bit for bit against the oracle.
 #pragma once
 #include <cstdint>
+#include <cstring>
 
 #ifdef __CUDACC__
 #define LSQ_HD __host__ __device__ __forceinline__
@@ -80,36 +82,79 @@ LSQ_HD bool enc_term(uint32_t sg, uint64_t a, int sc, uint32_t& bits, uint64_t& 
   return true;
 }
 
-// The terms of v = 2^k * x (x given by its FP64 bits u) in format F: t[0] =
-// fl(v), and with SPLIT3 also t[1] = fl(v - t[0]), t[2] = fl(v - t[0] - t[1])
-// (differences exact).  False when some term needs the FP64 definition.
-template <class F, bool SPLIT3>
+// t[0] = fl(v), v = 2^k * x (x given by its FP64 bits u) in format F; t[1] = t[2]
+// = 0.  False when the result needs the FP64 definition (subnormal or
+// overflowing result, subnormal or non-finite input).
+template <class F>
 LSQ_HD bool cast_terms_int(uint64_t u, int k, uint32_t (&t)[3]) {
   const uint32_t sg = (uint32_t)(u >> 63);
   t[0] = t[1] = t[2] = 0;
-  if ((u << 1) == 0) {                     // fl(+-0) = +-0; the differences are +0
+  if ((u << 1) == 0) {                     // fl(+-0) = +-0
     t[0] = sg << (F::W - 1);
     return true;
   }
   const int E = (int)((u >> 52) & 0x7FF);
   if (E == 0 || E == 0x7FF) return false;  // subnormal or non-finite input
   const uint64_t a = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sc = E - 1075 + k;
   uint64_t rd;
-  if (!enc_term<F>(sg, a, sc, t[0], rd)) return false;
-  if (SPLIT3) {
-    const int64_t d1 = (int64_t)a - (int64_t)rd;   // v - hi
-    if (d1 == 0) return true;
-    const uint32_t s1 = sg ^ (d1 < 0 ? 1u : 0u);
-    const uint64_t a1 = (uint64_t)(d1 < 0 ? -d1 : d1);
-    uint64_t rd1;
-    if (!enc_term<F>(s1, a1, sc, t[1], rd1)) return false;
-    const int64_t d2 = (int64_t)a1 - (int64_t)rd1;  // v - hi - lo
-    if (d2 == 0) return true;
-    const uint32_t s2 = s1 ^ (d2 < 0 ? 1u : 0u);
-    uint64_t rd2;
-    if (!enc_term<F>(s2, (uint64_t)(d2 < 0 ? -d2 : d2), sc, t[2], rd2)) return false;
-  }
+  return enc_term<F>(sg, a, E - 1075 + k, t[0], rd);
+}
+
+// ---------------------------------------------------------------- BF16X3
+LSQ_HD float f32_of(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+LSQ_HD uint32_t bits_of(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return b;
+#endif
+}
+LSQ_HD float sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+
+// fl_bf16 of a finite FP32 value given by its bits, ties to even.  BF16 keeps
+// FP32's sign and exponent fields, so rounding away the low 16 bits of the
+// pattern rounds the value, on the subnormal grid too; a carry out of the
+// fraction moves into the exponent.
+LSQ_HD uint32_t bf16_rn(uint32_t f) { return (f + 0x7FFFu + ((f >> 16) & 1u)) >> 16; }
+
+// The split of y (FP32 bits): hi = fl_bf16(y), lo = fl_bf16(y - hi), lo2 =
+// fl_bf16(y - hi - lo).  Each difference is an exact FP32 subtraction (the
+// operands are within a factor of two of each other), and y - hi - lo has at
+// most eight significant bits, so hi + lo + lo2 = y unless lo2 lies below
+// BF16's normal range.
+LSQ_HD void split3_f32(uint32_t y, uint32_t (&t)[3]) {
+  t[0] = bf16_rn(y);
+  const float r1 = sub_rn(f32_of(y), f32_of(t[0] << 16));
+  t[1] = bf16_rn(bits_of(r1));
+  const float r2 = sub_rn(r1, f32_of(t[1] << 16));
+  t[2] = bf16_rn(bits_of(r2));
+}
+
+// fl32(2^k x) from a = fl32(x) (FP32 bits): 2^k a, exact when |a| and |2^k a|
+// both lie in [2^-125, 2^128) -- x was then rounded on the normal grid and
+// scaling by a power of two commutes with that rounding.  False otherwise
+// (zero, subnormal or near-subnormal, non-finite).
+LSQ_HD bool f32_scale_exact(uint32_t a, int k, uint32_t& y) {
+  const int ef = (int)((a >> 23) & 0xFFu);
+  const int es = ef + k;
+  if (ef < 2 || ef > 254 || es < 2 || es > 254) return false;
+  y = a + ((uint32_t)k << 23);
   return true;
 }
 

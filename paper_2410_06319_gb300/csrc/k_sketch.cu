@@ -82,12 +82,16 @@ cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t 
 // for out-of-range values (subnormal results, overflow, subnormal or
 // non-finite inputs).
 
-// FP64 bits -> FP32 value, round to nearest even.
-__device__ __forceinline__ float f64bits_to_f32(uint64_t u) {
+// fl32(2^k x) as FP32 bits, x given by its FP64 bits: integer rounding, else the FP64
+// definition (subnormal results, non-finite or subnormal x).
+__device__ __forceinline__ uint32_t f32_scaled_bits(uint64_t u, int k) {
   uint32_t t[3];
-  if (cast_terms_int<EncF32, false>(u, 0, t)) return __uint_as_float(t[0]);
-  return __double2float_rn(__longlong_as_double((long long)u));
+  if (cast_terms_int<EncF32>(u, k, t)) return t[0];
+  return __float_as_uint(__double2float_rn(ldexp(__longlong_as_double((long long)u), k)));
 }
+
+// FP64 bits -> FP32 value, round to nearest even.
+__device__ __forceinline__ float f64bits_to_f32(uint64_t u) { return __uint_as_float(f32_scaled_bits(u, 0)); }
 
 __device__ __forceinline__ void colmax_a32_body(const double* __restrict__ A, int64_t lda,
                                                 const double* __restrict__ b, int64_t m, int64_t n,
@@ -178,18 +182,14 @@ struct FmtEnc<FMT_E4M3> {
 };
 
 // The terms of fl_s(2^k x) (x given by its FP64 bits u): integer path, else the
-// FP64 definition (round-to-odd into FP32, then to the format).
+// FP64 definition (round-to-odd into FP32, then to the format).  BF16X3: the three
+// BF16 terms of y = fl32(2^k x).
 template <int FMT>
 __device__ __forceinline__ void cast_bits(uint64_t u, int k, uint32_t (&t)[3]) {
-  if (!cast_terms_int<typename FmtEnc<FMT>::T, FMT == FMT_BF16X3>(u, k, t)) {
-    const double v = ldexp(__longlong_as_double((long long)u), k);
-    constexpr int G = (FMT == FMT_BF16X3) ? FMT_BF16 : FMT;
-    t[0] = round_f64<G>(v);
-    if constexpr (FMT == FMT_BF16X3) {
-      const double r1 = v - bits_to_double<G>(t[0]);
-      t[1] = round_f64<G>(r1);
-      t[2] = round_f64<G>(r1 - bits_to_double<G>(t[1]));
-    }
+  if constexpr (FMT == FMT_BF16X3) {
+    split3_f32(f32_scaled_bits(u, k), t);
+  } else if (!cast_terms_int<typename FmtEnc<FMT>::T>(u, k, t)) {
+    t[0] = round_f64<FMT>(ldexp(__longlong_as_double((long long)u), k));
   }
 }
 
@@ -227,25 +227,70 @@ __device__ __forceinline__ void cast_transpose_body(const double* __restrict__ A
     const bool live = c <= n && j < m;
     const uint64_t u = tile[threadIdx.x][r];
     const int k = live ? kexp[c] : 0;
+    (void)pstride;
     if constexpr (FMT == FMT_F32) {
       const double v = ldexp(__longlong_as_double((long long)u), k);
       reinterpret_cast<float*>(Bt)[base] = live ? __double2float_rn(v) : 0.0f;
     } else {
       uint32_t tt[3] = {0u, 0u, 0u};
       if (live) cast_bits<FMT>(u, k, tt);
-      if constexpr (FMT == FMT_BF16X3) {
-        // three BF16 terms hi + lo + lo2, one plane each
-        uint16_t* P = reinterpret_cast<uint16_t*>(Bt);
-        P[base] = (uint16_t)tt[0];
-        P[base + pstride] = (uint16_t)tt[1];
-        P[base + 2 * pstride] = (uint16_t)tt[2];
-      } else if constexpr (FMT == FMT_E4M3) {
+      if constexpr (FMT == FMT_E4M3) {
         reinterpret_cast<uint8_t*>(Bt)[base] = (uint8_t)tt[0];
       } else {
         reinterpret_cast<uint16_t*>(Bt)[base] = (uint16_t)tt[0];
       }
     }
   }
+}
+
+// BF16X3: y = fl32(2^k x) in three BF16 planes hi, lo, lo2 (same Bt layout).  Tiles of
+// kCast3Rows rows x 32 columns.  y comes from the FP32 copy of A by a power-of-two
+// scaling where that is exact (f32_scale_exact), else from the FP64 value (the b
+// column, zeros, the bottom of FP32's range, or no FP32 copy); each thread writes two
+// consecutive k of a row per plane, so a warp stores 128 contiguous bytes.
+__device__ __forceinline__ void cast_bf16x3_body(const double* __restrict__ A, int64_t lda,
+                                                 const double* __restrict__ b, const float* __restrict__ a32,
+                                                 int64_t lda32, int64_t m, int64_t n,
+                                                 const int* __restrict__ kexp, void* __restrict__ Bt,
+                                                 int64_t plane_rows, int64_t bx, int64_t by) {
+  __shared__ uint32_t tile[32][kCast3Rows + 1];   // [column][row]: y bits
+  const int64_t j0 = bx * kCast3Rows, c0 = by * 32;
+  const int64_t c = c0 + threadIdx.x;
+  const int k = (c <= n) ? kexp[c] : 0;
+  const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
+  const uint64_t* bu = reinterpret_cast<const uint64_t*>(b);
+  for (int r = threadIdx.y; r < kCast3Rows; r += 8) {
+    const int64_t j = j0 + r;
+    uint32_t y = 0;
+    if (j < m && c <= n) {
+      bool done = false;
+      if (a32 != nullptr && c < n) done = f32_scale_exact(__float_as_uint(__ldcs(a32 + j * lda32 + c)), k, y);
+      if (!done) y = f32_scaled_bits(c < n ? __ldcs(Au + j * lda + c) : bu[j], k);
+    }
+    tile[threadIdx.x][r] = y;
+  }
+  __syncthreads();
+  uint32_t* P = reinterpret_cast<uint32_t*>(Bt);   // pairs of BF16 values, k even first
+  const int64_t pstride = plane_rows * kBtBlock / 2;
+  const int64_t j = j0 + 2 * threadIdx.x;
+  const int64_t blk = j / kBtBlock, kk = j % kBtBlock;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t cc = c0 + r;
+    if (cc >= plane_rows) continue;
+    const int64_t base = ((blk * 3 * plane_rows + cc) * kBtBlock + kk) / 2;
+    uint32_t t0[3], t1[3];
+    split3_f32(tile[r][2 * threadIdx.x], t0);
+    split3_f32(tile[r][2 * threadIdx.x + 1], t1);
+    P[base] = t0[0] | (t1[0] << 16);
+    P[base + pstride] = t0[1] | (t1[1] << 16);
+    P[base + 2 * pstride] = t0[2] | (t1[2] << 16);
+  }
+}
+
+__global__ void cast_bf16x3_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ b,
+                                   const float* __restrict__ a32, int64_t lda32, int64_t m, int64_t n,
+                                   const int* __restrict__ kexp, void* __restrict__ Bt, int64_t plane_rows) {
+  cast_bf16x3_body(A, lda, b, a32, lda32, m, n, kexp, Bt, plane_rows, blockIdx.x, blockIdx.y);
 }
 
 template <int FMT>
@@ -264,12 +309,16 @@ size_t bt_bytes(int fmt, int64_t m, int64_t plane_rows) {
   return (size_t)bt_blocks(m) * planes * plane_rows * kBtBlock * esz;
 }
 
-cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
-                                  int64_t n, const int* kexp, void* Bt, int64_t plane_rows,
-                                  cudaStream_t st) {
+int64_t cast_row_tiles(int fmt, int64_t m) {
+  return bt_blocks(m) * kBtBlock / (fmt == FMT_BF16X3 ? kCast3Rows : 32);
+}
+
+cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, const float* a32,
+                                  int64_t lda32, int64_t m, int64_t n, const int* kexp, void* Bt,
+                                  int64_t plane_rows, cudaStream_t st) {
   if (plane_rows < n + 1) return cudaErrorInvalidValue;
   const int planes = (fmt == FMT_BF16X3) ? 3 : 1;
-  const int64_t gx = bt_blocks(m) * kBtBlock / 32;
+  const int64_t gx = cast_row_tiles(fmt, m);
   if (gx > 2147483647LL) return cudaErrorInvalidValue;
   dim3 grid((unsigned)gx, (unsigned)((plane_rows + 31) / 32));
   dim3 block(32, 8);
@@ -278,7 +327,7 @@ cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const d
     case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
     case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
     case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
-    case FMT_BF16X3: cast_transpose_kernel<FMT_BF16X3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
+    case FMT_BF16X3: cast_bf16x3_kernel<<<grid, block, 0, st>>>(A, lda, b, a32, lda32, m, n, kexp, Bt, plane_rows); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1192,8 +1241,12 @@ __global__ void grouped_cast_kernel(const GCast* __restrict__ tab, const int* __
   const int p = group_of(start, nprob, blockIdx.x);
   const GCast& g = tab[p];
   const int64_t local = (int64_t)blockIdx.x - start[p];
-  cast_transpose_body<FMT>(g.A, g.lda, g.b, g.m, g.n, g.kexp, g.Bt, g.plane_rows, planes, local % g.cast_gx,
-                           local / g.cast_gx);
+  if constexpr (FMT == FMT_BF16X3)
+    cast_bf16x3_body(g.A, g.lda, g.b, g.a32, g.lda32, g.m, g.n, g.kexp, g.Bt, g.plane_rows, local % g.cast_gx,
+                     local / g.cast_gx);
+  else
+    cast_transpose_body<FMT>(g.A, g.lda, g.b, g.m, g.n, g.kexp, g.Bt, g.plane_rows, planes, local % g.cast_gx,
+                             local / g.cast_gx);
 }
 
 __global__ void grouped_sketch_reduce_kernel(const GReduce* __restrict__ tab, const int* __restrict__ start,

@@ -24,13 +24,17 @@ cudaError_t launch_scale_exps(const unsigned long long* cmax_bits, int64_t ncols
 // column c and data row j, stored in blocks of kBtBlock data rows, each block
 // [plane][row c < plane_rows][j % kBtBlock]; rows past n and data rows past m are
 // zero.  fmt in {F16, BF16, E4M3, F32, BF16X3}; element size 2, 2, 1, 4, 2;
-// BF16X3 has three planes (hi, lo, lo2).  plane_rows >= n + 1.
+// BF16X3 has three planes (hi, lo, lo2) of y = fl32(2^k_c x), read from the FP32
+// copy a32 (row-major, lda32; may be null) where its power-of-two scaling is exact
+// and from A elsewhere.  plane_rows >= n + 1.
 constexpr int64_t kBtBlock = 2048;
+constexpr int kCast3Rows = 64;   // data rows of a BF16X3 cast tile (32 for the other formats)
 int64_t bt_blocks(int64_t m);
 size_t bt_bytes(int fmt, int64_t m, int64_t plane_rows);
-cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, int64_t m,
-                                  int64_t n, const int* kexp, void* Bt, int64_t plane_rows,
-                                  cudaStream_t st);
+int64_t cast_row_tiles(int fmt, int64_t m);   // x extent of the cast grid
+cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const double* b, const float* a32,
+                                  int64_t lda32, int64_t m, int64_t n, const int* kexp, void* Bt,
+                                  int64_t plane_rows, cudaStream_t st);
 
 // Arguments of one tensor-core sketch launch (one problem).
 struct SketchTcArgs {
@@ -70,7 +74,7 @@ struct GCast {
   int* kexp;
   void* Bt;
   int64_t plane_rows;
-  int64_t cast_gx;            // row tiles of 32 in this problem's cast grid
+  int64_t cast_gx;            // row tiles of this problem's cast grid (cast_row_tiles)
 };
 // Per-problem arguments of the grouped split reduction of the FP32 sketch partials.
 struct GReduce {

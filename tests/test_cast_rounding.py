@@ -1,11 +1,14 @@
 """Integer rounding of the cast pass (csrc/cast.cuh) against the oracle.
 
-The cast A_s = fl_s(2^k A) of Sec. 3.2 (and the three-term BF16 split) runs on
-integer units on the GPU.  A host build of the same header is compared bit for
-bit with ``oracle.rng.round_to_format`` / ``split3`` (FP32: numpy's conversion)
-on random, sparse-bit (tie-heavy) and range-edge inputs; the integer path may
-decline (then the kernel uses the FP64 definition) only where a term leaves
-the format's normal range or the input is subnormal or non-finite.
+The cast A_s = fl_s(2^k A) of Sec. 3.2 runs on integer units on the GPU.  A
+host build of the same header is compared bit for bit with
+``oracle.rng.round_to_format`` (FP32: numpy's conversion) on random, sparse-bit
+(tie-heavy) and range-edge inputs; the integer path may decline (then the
+kernel uses the FP64 definition) only where the result leaves the format's
+normal range or the input is subnormal or non-finite.  The BF16X3 operand (the
+three BF16 terms of y = fl32(2^k A)) is compared with the oracle's cast for
+every finite input, through the FP32 copy's power-of-two scaling where that
+is exact and through the FP64 value elsewhere.
 """
 import os
 import shutil
@@ -46,7 +49,7 @@ def run(exe, fmt, u, k):
 def inputs(seed, fmt):
     """FP64 bit patterns and exponents k: random, sparse-bit and edge cases."""
     r = np.random.default_rng(seed)
-    mb, emin, emax, _ = ENC["bf16" if fmt == "bf16x3" else fmt]
+    mb, emin, emax, _ = ENC["f32" if fmt == "bf16x3" else fmt]
     n = 6000
     sign = r.integers(0, 2, n, dtype=np.uint64) << np.uint64(63)
     E = r.integers(1023 - 30, 1023 + 30, n).astype(np.uint64)
@@ -103,21 +106,18 @@ def in_normal_range(vals, fmt):
     return (v == 0) | (np.isfinite(v) & (lead >= emin) & (lead <= emax))
 
 
-@pytest.mark.parametrize("fmt", ["bf16", "f16", "e4m3", "f32", "bf16x3"])
+@pytest.mark.parametrize("fmt", ["bf16", "f16", "e4m3", "f32"])
 def test_integer_cast_matches_oracle_rounding(harness, fmt):
     u, k = inputs(11, fmt)
     ok, t = run(harness, fmt, u, k)
     x = u.view(np.float64)
     with np.errstate(over="ignore", invalid="ignore"):
         v = np.ldexp(x, k)
-    base = "bf16" if fmt == "bf16x3" else fmt
+    base = fmt
     finite_in = np.isfinite(x) & ((x == 0) | (np.abs(x) >= 2.2250738585072014e-308))
     if fmt == "f32":
         with np.errstate(over="ignore"):
             terms = [v.astype(np.float32).astype(np.float64)]
-    elif fmt == "bf16x3":
-        with np.errstate(invalid="ignore"):      # terms of overflowing edge values (declined below)
-            terms = list(rng.split3(np.where(finite_in, v, 0.0), "bf16"))
     else:
         terms = [rng.round_to_format(np.where(finite_in, v, 0.0), fmt)]
     expect_ok = finite_in.copy()
@@ -139,11 +139,36 @@ def test_integer_cast_matches_oracle_rounding(harness, fmt):
     for i, tv in enumerate(terms):
         want = bits_of(np.where(ok, tv, 0.0), base)
         assert np.array_equal(t[ok, i], want[ok]), (i, np.flatnonzero(t[ok, i] != want[ok])[:10])
-    if fmt != "bf16x3":
-        assert not np.any(t[:, 1:])
+    assert not np.any(t[:, 1:])
     # the integer path covers (almost) everything a scaled cast sees: values of
     # magnitude up to 2^(t+1) whose terms stay far above the normal range's floor
     if base in ("bf16", "f32"):
         assert ok[:12200].mean() > 0.99
     else:
         assert ok[:12200].sum() > 1000
+
+
+def test_bf16x3_terms_match_oracle_cast(harness):
+    """Every finite input, including values whose scaled FP32 rounding is subnormal or
+    near the bottom of the normal range (there the header leaves the FP32 copy and
+    rounds the FP64 value): the three terms are the oracle's split of fl32(2^k x)."""
+    u, k = inputs(12, "bf16x3")
+    # scalings that push entries to the bottom of FP32's range and below it
+    r = np.random.default_rng(13)
+    xs = np.ldexp(1.0 + r.random(3000), r.integers(-160, -110, 3000)) * np.where(r.random(3000) < 0.5, -1, 1)
+    u = np.concatenate([u, xs.view(np.uint64)])
+    k = np.concatenate([k, r.integers(-12, 13, 3000)])
+    x = u.view(np.float64)
+    keep = np.isfinite(x)
+    u, k, x = u[keep], k[keep], x[keep]
+    fast, t = run(harness, "bf16x3", u, k)
+    with np.errstate(over="ignore"):
+        y = rng.round_to_format(np.ldexp(x, k), "f32")
+    small = np.abs(y) < 2.0 ** 127   # edge values whose hi term overflows BF16 are left out
+    terms = rng.split3(np.where(small, y, 0.0), "bf16")
+    for i, tv in enumerate(terms):
+        want = (tv.astype(np.float32).view(np.uint32) >> 16).astype(np.uint32)
+        assert np.array_equal(t[small, i], want[small]), (i, np.flatnonzero(t[small, i] != want[small])[:10])
+    # the FP32 copy's scaling carries the bulk of a column's entries
+    assert fast[:12200].mean() > 0.99
+    assert not np.all(fast[-3000:])

@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 FMTS = ["f16", "bf16", "e4m3", "bf16x3", "f32", "f64"]
 
 
-def gpu_sketch(lsq, handle, A, b, s, fmt, seed, **opts):
+def gpu_sketch(lsq, handle, A, b, s, fmt, seed, uw="f32", **opts):
     m, n = A.shape
     Y = torch.full((s * (n + 1),), float("nan"), dtype=torch.float64, device="cuda")
-    lsq.lsq_sketch(handle, dev(A), dev(b), m, n, s, fmt, "f32", "f32", "f64", 1e-6, seed, opts or None, Y)
+    lsq.lsq_sketch(handle, dev(A), dev(b), m, n, s, fmt, "f32", uw, "f64", 1e-6, seed, opts or None, Y)
     return from_colmajor(Y, s, n + 1)
 
 
@@ -104,3 +104,29 @@ def test_sketch_deferred_correction_matches_exact_mode(lsq, handle, fmt, m, n, s
     assert np.all(np.abs(got - exact) <= 2 * (m + 2) * 2.0 ** -24 * mag + 1e-300)
     ref = sketch.sketch(P.A, P.b, s, 5, fmt)
     assert np.all(np.abs(got - ref) <= (m + 2) * 2.0 ** -24 * mag + 1e-300)
+
+
+@pytest.mark.parametrize("m,n,s", [(5000, 37, 150), (9001, 300, 320)])
+def test_bf16x3_cast_from_fp32_copy_is_bit_identical(lsq, handle, m, n, s):
+    """The BF16X3 operand y = fl32(2^k x) formed from the FP32 working copy (u_w = F32: a
+    power-of-two scaling of fl32(x) where that is exact) and from A alone (u_w = F64) is
+    the same, so the sketches agree bit for bit.  The input has zeros, exact FP32 ties,
+    columns whose FP32 copy is subnormal or overflows, and entries whose scaled value lands
+    at the bottom of FP32's range (the copy is passed over there)."""
+    P = randsvd_problem(m, n, 1e3, rho=1e-2, seed=21)
+    A = P.A.copy()
+    r = np.random.default_rng(3)
+    A[r.random(A.shape) < 0.01] = 0.0
+    A[:, 1] *= 2.0 ** -140                 # the FP32 copy of this column is subnormal
+    A[:, 2] *= 2.0 ** 135                  # ... and here partly infinite
+    A[::7, 3] *= 2.0 ** -136               # scaled entries near FP32's smallest normal
+    A[::11, 4] = np.sign(A[::11, 4]) * (1.0 + 2.0 ** -24) * 2.0 ** -8   # ties of the FP32 rounding
+    got32 = gpu_sketch(lsq, handle, A, P.b, s, "bf16x3", 9)
+    got64 = gpu_sketch(lsq, handle, A, P.b, s, "bf16x3", 9, uw="f64")
+    assert np.array_equal(got32, got64)
+    ref = sketch.sketch(A, P.b, s, 9, "bf16x3")
+    As, bs, kA, kb = sketch.cast_scaled(A, P.b, "bf16x3")
+    Gs = rng.sketch_operand(s, 0, m, 9, "bf16x3")
+    k = np.concatenate([kA, [kb]])
+    mag = np.ldexp(np.abs(Gs) @ np.abs(np.column_stack([As, bs])), -k[None, :]) / np.sqrt(s)
+    assert np.all(np.abs(got32 - ref) <= (m + 2) * 2.0 ** -24 * mag + 1e-300)
