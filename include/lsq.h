@@ -158,6 +158,12 @@ typedef struct lsq_opts {
   int32_t batch_grid;     /* grouped mode: CTAs of the persistent pass launches; 0 -> chosen by
                              timing the candidates on the first call for a batch shape (cached in
                              the handle); every choice gives the same result */
+  int32_t arnoldi;        /* FGMRES Arnoldi step (FP64): 0 by vector length (modified Gram-Schmidt
+                             from 786,432 rows of [r; x] on, below that classical Gram-Schmidt with a
+                             second pass where the first lost more than half of ||w||^2),
+                             1 classical with the selective second pass, 2 modified (its work
+                             vector in shared memory up to ~4.1e6 rows), 3 modified with the work
+                             vector in global memory (the form used past that size) */
 } lsq_opts;
 
 /* Diagnostics of one call. */

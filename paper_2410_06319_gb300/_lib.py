@@ -42,7 +42,8 @@ class Opts(ctypes.Structure):
                 ("expire_sync", ctypes.c_int32), ("sketch_kind", ctypes.c_int32),
                 ("sparse_zeta", ctypes.c_int32), ("ops_escalated", ctypes.c_int32),
                 ("aug_alpha", ctypes.c_double), ("h_in_ur", ctypes.c_int32),
-                ("batch_mode", ctypes.c_int32), ("batch_grid", ctypes.c_int32)]
+                ("batch_mode", ctypes.c_int32), ("batch_grid", ctypes.c_int32),
+                ("arnoldi", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -287,6 +287,8 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   GmState* gst = static_cast<GmState*>(ws(c.h, "gm_state", sizeof(GmState)));
   unsigned* gbar = static_cast<unsigned*>(ws(c.h, "gm_bar", 64));
   CK(cudaMemsetAsync(gbar, 0, 64, c.st));
+  auto* gseq = static_cast<unsigned long long*>(ws(c.h, "gm_seq", 64));
+  CK(cudaMemsetAsync(gseq, 0, 64, c.st));
   if (c.o.expire_sync) {
     // the arrival count starts where no arrival completes the Arnoldi step's grid sync:
     // its bounded waits run out (a test of the timeout path)
@@ -304,6 +306,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
   L(launch_gm_init(sqp, c.nblk2, gst, g, c.st));
   L(launch_gm_scale0(V, ld, gst, v32, m, c.nblk2, c.st));
   const int maxc = maxit + 1;
+  const int mgs = c.o.arnoldi == 3 ? 2 : (c.o.arnoldi == 2 || (c.o.arnoldi == 0 && ld >= kMgsMinRows)) ? 1 : 0;
   const Tri<double>* tri64 = reinterpret_cast<const Tri<double>*>(&tri);
   auto body = [&]() {
     for (int k = 0; k < kBatch; ++k) {
@@ -330,7 +333,8 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
         {
           KernTimer kt(c.h, K_ARNOLDI, c.o.timing);
           L(launch_gm_step<double>(V, ld, wv, ld, m, nullptr, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, nullptr,
-                                   gbar, c.h->d_err, c.h->num_sms, c.st, wait_ns, c.alpha));
+                                   gbar, c.h->d_err, c.h->num_sms, c.st, wait_ns, c.alpha, mgs, gseq,
+                                   c.o.expire_sync));
         }
         continue;
       }
@@ -348,12 +352,12 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
         KernTimer kt(c.h, K_TRSV, c.o.timing);
         L((launch_trsv<TOP, TOP, double>(false, tri, sb, 1.0, wv + m, dn, c.st)));
       }
-      // classical Gram-Schmidt; the second pass runs only when the first one lost
-      // more than half of ||w||^2 ("twice is enough"); Givens step; new column
+      // modified Gram-Schmidt, or classical with a second pass only where the first one
+      // lost more than half of ||w||^2 ("twice is enough"); Givens step; new column
       {
         KernTimer kt(c.h, K_ARNOLDI, c.o.timing);
         L(launch_gm_step<TOP>(V, ld, wv, ld, m, az, gst, maxc, Dp, sqp, hh, H, ldh, cs, sn, g, v32, gbar,
-                              c.h->d_err, c.h->num_sms, c.st, wait_ns, c.alpha));
+                              c.h->d_err, c.h->num_sms, c.st, wait_ns, c.alpha, mgs, gseq, c.o.expire_sync));
       }
     }
   };
@@ -369,7 +373,7 @@ GmOut stage_fgmres(Ctx& c, const TOP* Aop, int64_t ldop, const Tri<TOP>& tri, co
                                         PV(az), PV(v32),
                                         PV(sb), PV(H), PV(cs), PV(sn), PV(g), PV(hh), PV(Dp), PV(sqp),
                                         PV(gst), PV(gbar), PV(tri.R), PV(tri.L), PV(tri.DU), PV(tri.DL), c.nblk,
-                                        c.nblk2}),
+                                        c.nblk2, (int64_t)mgs, PV(gseq), (int64_t)c.o.expire_sync}),
                              body);
   int j = 0;
   GmState out{};

@@ -223,6 +223,7 @@ lsq_status validate(const Ctx& c, bool need_b) {
   if (c.ur != LSQ_F64 && c.ur != LSQ_F64X2) return LSQ_E_INVAL;
   if (c.o.ops_escalated < 0 || c.o.ops_escalated > 1) return LSQ_E_INVAL;
   if (c.o.h_in_ur < 0 || c.o.h_in_ur > 1) return LSQ_E_INVAL;
+  if (c.o.arnoldi < 0 || c.o.arnoldi > 3) return LSQ_E_INVAL;
   if (!(c.o.aug_alpha >= 0.0) || !std::isfinite(c.o.aug_alpha)) return LSQ_E_INVAL;
   if (c.o.gmres_maxit < 0 || c.o.gmres_maxit > kMaxGmres) return LSQ_E_INVAL;
   if (c.o.ir_maxit < 0 || c.o.ir_maxit > 32) return LSQ_E_INVAL;

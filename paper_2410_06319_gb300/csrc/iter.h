@@ -81,17 +81,24 @@ cudaError_t launch_gm_rhs(const double* f, const double* h, int64_t m, int64_t n
 cudaError_t launch_gm_init(const double* sq_partial, int nblk, GmState* st, double* g, cudaStream_t s);
 cudaError_t launch_gm_scale0(double* V0, int64_t len, const GmState* st, float* v32, int64_t m,
                              int nblk, cudaStream_t s);
-// The whole Arnoldi step in one cooperative launch (classical Gram-Schmidt with the
-// twice-is-enough second pass, Givens step, new column; blocks synchronised by a bounded
-// last-arrival reduction on bar[0..1], which must be zero before the first launch; each
-// launch leaves it reusable).  Dp holds (maxc + 1) x 2 num_sms doubles; maxc <= 128.
-// Each sync waits at most wait_ns (0: the library's limit); a wait that runs out records
-// DEV_TIMEOUT_GRID in *err and sets st->done, so the rest of the batch is skipped.
+// The whole Arnoldi step in one cooperative launch (gs = 0: classical Gram-Schmidt with the
+// twice-is-enough second pass; 1: modified Gram-Schmidt, w in shared memory where it fits;
+// 2: modified, w in global memory -- its grid sums use the 64-bit arrival counter *seq,
+// zero before the solve's first step, every step of a solve on the same grid; Givens step,
+// new column;
+// blocks synchronised by a bounded last-arrival reduction on bar[0..1], which must be zero
+// before the first launch; each launch leaves it reusable).  Dp holds (maxc + 1) x 2
+// num_sms doubles; maxc <= 128.  Each sync waits at most wait_ns (0: the library's
+// limit); a wait that runs out records DEV_TIMEOUT_GRID in *err and sets st->done, so the
+// rest of the batch is skipped.
 template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
-                           int num_sms, cudaStream_t s, uint64_t wait_ns = 0, double alpha = 1.0);
+                           int num_sms, cudaStream_t s, uint64_t wait_ns = 0, double alpha = 1.0,
+                           int gs = 0, unsigned long long* seq = nullptr, int expire = 0);
+// modified Gram-Schmidt from this many rows of [r; x] on (opts.arnoldi = 0)
+constexpr int64_t kMgsMinRows = (int64_t)3 << 18;   // 786,432: measured crossover ~7e5 on GB300
 cudaError_t launch_gm_solve(const GmState* st, const double* H, int ldh, const double* g, double* y,
                             cudaStream_t s);
 // d += scale (B y) over the first st->j columns of B; partial sums of ||scale B y||^2 and ||d||^2

@@ -941,6 +941,8 @@ struct GmStepArgs {
   int ldd;        // leading dimension of Dp (>= the grid size)
   uint64_t wait_ns;   // limit of each grid-sync wait
   double alpha;       // w_top = alpha v_top + A z (Sec. 4.1 scaling; 1 unscaled)
+  unsigned long long* seq;   // MGS: arrival counter of the grid sums (zero before the solve)
+  int expire;         // MGS: wait for one arrival more than the grid makes (the timeout test)
 };
 
 // Dp[c][block] = sum over rows [r0, r1) of V[c][i] w[i] for c < ncols; Dp[ncols][block] = sum of w[i]^2.
@@ -1209,29 +1211,209 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_step_kernel(const GmStepArgs
   }
 }
 
+// ---------------------------------------------------------------- MGS Arnoldi step
+// Modified Gram-Schmidt for long vectors, one cooperative launch per FGMRES iteration.
+// Sweep c = 0..j+1 over the CTA's rows: subtract the projection on v_{c-1} (its
+// coefficient h_{c-1} is the previous sweep's grid sum) and accumulate v_c^T w (sweep
+// j+1: ||w||^2); each sweep ends in one grid sum.  2(j+1) FP64 FMAs per row, the least
+// any Gram-Schmidt form needs for j+1 projections (classical Gram-Schmidt with its second
+// pass takes 4(j+1)); GB300's FP64 rate, not HBM, bounds the step at m in the millions.
+// Each row stays with one thread from sweep to sweep, so w needs no barrier between
+// sweeps.  WS: the CTA's rows of w live in shared memory for the whole step (one CTA per
+// SM; rows of [r; x] up to 152 x ~27,000), so a sweep reads only v_c from HBM and v_{c-1}
+// again (from L2); otherwise w is read and written in global memory every sweep.
+constexpr int kMgsThreads = 512;      // global-w form: two CTAs per SM
+constexpr int kMgsThreadsWs = 1024;   // shared-w form: one CTA per SM
+constexpr int kMgsUnroll = 4;
+constexpr int kMgsStaticSmem = 16384; // bound on the kernel's static shared memory
+
+// One grid-wide sum.  Thread 0 of each CTA stores its value in part[b] and takes a
+// ticket from a 64-bit arrival counter with a release add; the counter is zeroed before
+// the solve and every launch of the solve has the same grid, so the tickets of one sum
+// fill [k nb, (k + 1) nb) and the sum is complete when the counter reaches (k + 1) nb.
+// Thread 0 waits for that (acquire loads, bounded; plus_one: wait for one more arrival,
+// which never comes -- the timeout test), then warp 0 adds the values in block order
+// itself, the same order in every CTA, so every CTA gets the same sum.  part is a fresh
+// column per sum, so a CTA that has moved on disturbs no one still reading.  *out
+// (shared) receives the sum.  Returns false if the wait ran out.
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool gm_grid_sum_ctr(double* part, unsigned long long* ctr, int plus_one, double mine,
+                                                int* err, uint64_t wait_ns, double* out) {
+  const unsigned nb = gridDim.x;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = mine;
+    const unsigned long long ticket = atom_add_release_u64(ctr, 1ull);
+    const unsigned long long target = (ticket / nb + 1ull) * nb + (plus_one ? 1ull : 0ull);
+    int ok = 1;
+    const uint64_t t0 = globaltimer_ns();
+    while (ld_acquire_u64(ctr) < target) {
+      if (globaltimer_ns() - t0 > wait_ns) {
+        set_error(err, DEV_TIMEOUT_GRID);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  if (threadIdx.x < 32) {
+    double t0 = 0.0, t1 = 0.0;
+    unsigned q = threadIdx.x;
+    for (; q + 32 < nb; q += 64) {
+      t0 += __ldcg(part + q);
+      t1 += __ldcg(part + q + 32);
+    }
+    if (q < nb) t0 += __ldcg(part + q);
+    const double t = warp_sum(t0 + t1);
+    if (threadIdx.x == 0) *out = t;
+  }
+  __syncthreads();
+  return true;
+}
+
+template <typename TAZ, bool WS, int NT>
+__global__ void __launch_bounds__(NT, WS ? 1 : 2) gm_mgs_kernel(const GmStepArgs<TAZ> a) {
+  if (a.st->done) return;   // uniform: read before any grid sync
+  extern __shared__ double wsm[];   // WS: w[r0 .. r1)
+  __shared__ double hs[130];
+  __shared__ double red[NT];
+  __shared__ double hcol[130];
+  const int j = a.st->j, ncols = j + 1;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int64_t chunk = (a.len + nb - 1) / nb;
+  const int64_t r0 = (int64_t)b * chunk, r1 = min(a.len, r0 + chunk);
+  constexpr int64_t step = NT;
+  double* w = WS ? wsm - r0 : a.w;   // indexed by the row
+  const double* wg = a.w;
+  const double* V = a.V;
+  const double* vj = V + (int64_t)j * a.ld;
+  const double al = a.alpha;
+  const bool form = a.az != nullptr;
+  for (int c = 0; c <= ncols; ++c) {
+    const double* vp = V + (int64_t)(c > 0 ? c - 1 : 0) * a.ld;
+    const double* vc = V + (int64_t)(c < ncols ? c : 0) * a.ld;
+    const double hp = c > 0 ? hs[c - 1] : 0.0;
+    double t = 0.0;
+    int64_t i = r0 + threadIdx.x;
+    for (; i + (kMgsUnroll - 1) * step < r1; i += kMgsUnroll * step) {
+      double wv[kMgsUnroll], pv[kMgsUnroll], cv[kMgsUnroll];
+#pragma unroll
+      for (int u = 0; u < kMgsUnroll; ++u) {
+        const int64_t q = i + u * step;
+        if (c == 0) wv[u] = (form && q < a.m) ? fma(al, vj[q], (double)a.az[q]) : wg[q];
+        else wv[u] = w[q];
+        pv[u] = c > 0 ? vp[q] : 0.0;
+        cv[u] = c < ncols ? vc[q] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kMgsUnroll; ++u) {
+        const int64_t q = i + u * step;
+        if (c > 0) wv[u] = fma(-hp, pv[u], wv[u]);
+        if (WS || c > 0 || (form && q < a.m)) w[q] = wv[u];
+        t = fma(c < ncols ? cv[u] : wv[u], wv[u], t);
+      }
+    }
+    for (; i < r1; i += step) {
+      double wi = c > 0 ? w[i] : ((form && i < a.m) ? fma(al, vj[i], (double)a.az[i]) : wg[i]);
+      if (c > 0) wi = fma(-hp, vp[i], wi);
+      if (WS || c > 0 || (form && i < a.m)) w[i] = wi;
+      t = fma(c < ncols ? vc[i] : wi, wi, t);
+    }
+    // block sum in a fixed order: NT / 32 values per lane of warp 0 (four interleaved
+    // chains), then the warp
+    red[threadIdx.x] = t;
+    __syncthreads();
+    double mine = 0.0;
+    if (threadIdx.x < 32) {
+      static_assert(NT % 128 == 0, "four chains of NT / 128 values");
+      const double* rl = red + threadIdx.x * (NT / 32);
+      double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+#pragma unroll
+      for (int k = 0; k < NT / 32; k += 4) {
+        q0 += rl[k];
+        q1 += rl[k + 1];
+        q2 += rl[k + 2];
+        q3 += rl[k + 3];
+      }
+      mine = warp_sum((q0 + q1) + (q2 + q3));
+    }
+    if (!gm_grid_sum_ctr(a.Dp + (int64_t)c * a.ldd, a.seq, a.expire, mine, a.err, a.wait_ns, hs + c)) {
+      if (threadIdx.x == 0) a.st->done = 1;   // later launches of the batch skip; the host reads err
+      return;
+    }
+  }
+  double hn2 = hs[ncols];
+  if (!(hn2 > 0.0)) hn2 = 0.0;
+  if (b == 0) {
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hcol[c] = hs[c];
+    if (threadIdx.x == 0) a.st->reorth = 0;
+  }
+  const double inv = hn2 > 0.0 ? 1.0 / sqrt(hn2) : 0.0;
+  double* vn = a.V + (int64_t)(j + 1) * a.ld;
+  __syncthreads();   // block 0: hcol is complete; every thread's last w is visible to the CTA
+  if (b == 0 && threadIdx.x < 32) {
+    gm_finish_warp(hn2, a.st, hcol, a.H, a.ldh, a.cs, a.sn, a.g);
+    return;
+  }
+  const int64_t nstep = (b == 0) ? NT - 32 : NT;
+  for (int64_t i = r0 + threadIdx.x - ((b == 0) ? 32 : 0); i < r1; i += nstep) {
+    const double v = w[i] * inv;
+    vn[i] = v;
+    if (a.v32 && i < a.m) a.v32[i] = (float)v;
+  }
+}
+
 template <typename TAZ>
 cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_t m, const TAZ* az,
                            GmState* st, int maxc, double* Dp, double* sq, double* hsum, double* H, int ldh,
                            double* cs, double* sn, double* g, float* v32, unsigned* bar, int* err,
-                           int num_sms, cudaStream_t s, uint64_t wait_ns, double alpha) {
+                           int num_sms, cudaStream_t s, uint64_t wait_ns, double alpha, int gs,
+                           unsigned long long* seq, int expire) {
   static_assert(sizeof(GmStepArgs<TAZ>) < 4096, "kernel parameter block");
-  if (maxc > 128) return cudaErrorInvalidValue;
-  auto kern = gm_step_kernel<TAZ>;
+  if (maxc > 128 || gs < 0 || gs > 2 || (gs > 0 && seq == nullptr)) return cudaErrorInvalidValue;
+  const bool mgs = gs > 0;
+  // MGS keeps w in shared memory when one CTA per SM holds its rows (unless gs = 2)
+  const int64_t ws_rows = (len + num_sms - 1) / num_sms;
+  const size_t ws_bytes = (size_t)ws_rows * 8;
+  const bool ws = gs == 1 && ws_bytes + kMgsStaticSmem <= 227 * 1024;
+  auto kern = !mgs ? gm_step_kernel<TAZ>
+                   : (ws ? gm_mgs_kernel<TAZ, true, kMgsThreadsWs> : gm_mgs_kernel<TAZ, false, kMgsThreads>);
+  const int threads = !mgs ? kGmThreads : (ws ? kMgsThreadsWs : kMgsThreads);
+  const size_t dyn = ws ? ws_bytes : 0;
+  if (ws) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
   int occ = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGmThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   // co-resident CTAs (cooperative launch): two per SM for long vectors (more loads in
-  // flight), one per SM otherwise (fewer partials to sum)
-  const int nblk = num_sms * ((occ >= 2 && len >= ((int64_t)1 << 20)) ? 2 : 1);
+  // flight), one per SM otherwise (fewer partials to sum); shared w: one per SM
+  const int nblk = ws ? num_sms : num_sms * ((occ >= 2 && len >= ((int64_t)1 << 20)) ? 2 : 1);
   GmStepArgs<TAZ> a{V, ld, len, m, w, az, st, maxc, 0, Dp, sq, hsum, H, cs, sn, g, v32, bar, err};
   a.ldh = ldh;
   a.ldd = 2 * num_sms;   // the caller's Dp holds (maxc + 1) x 2 num_sms values
   a.wait_ns = wait_ns > 0 ? wait_ns : kWaitLimitNs;
   a.alpha = alpha;
+  a.seq = seq;
+  a.expire = expire;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
-  cfg.blockDim = dim3(kGmThreads);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -1243,11 +1425,11 @@ cudaError_t launch_gm_step(double* V, int64_t ld, double* w, int64_t len, int64_
 template cudaError_t launch_gm_step<float>(double*, int64_t, double*, int64_t, int64_t, const float*, GmState*,
                                            int, double*, double*, double*, double*, int, double*, double*,
                                            double*, float*, unsigned*, int*, int, cudaStream_t, uint64_t,
-                                           double);
+                                           double, int, unsigned long long*, int);
 template cudaError_t launch_gm_step<double>(double*, int64_t, double*, int64_t, int64_t, const double*,
                                             GmState*, int, double*, double*, double*, double*, int, double*,
                                             double*, double*, float*, unsigned*, int*, int, cudaStream_t,
-                                            uint64_t, double);
+                                            uint64_t, double, int, unsigned long long*, int);
 
 // y = H[:k,:k]^-1 g[:k]  (k = st->j): one warp, column-oriented back substitution
 __global__ void gm_solve_kernel(const GmState* st, const double* H, int ldh, const double* g, double* y) {

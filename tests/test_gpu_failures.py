@@ -37,14 +37,16 @@ def _solve_ok(lsq, handle, P):
     assert st == 0 and ex <= 4 * 2.0 ** -24 and er <= 4 * 2.0 ** -24, (st, ex, er)
 
 
-def test_expired_wait_reports_timeout_and_handle_recovers(lsq, handle):
+@pytest.mark.parametrize("arnoldi", [1, 2, 3])
+def test_expired_wait_reports_timeout_and_handle_recovers(lsq, handle, arnoldi):
+    """Classical (1) and modified (2: shared-memory work vector, 3: global) Arnoldi steps."""
     P = paper_problem(1e2, seed=5)
     m, n = P.A.shape
     x, r = zeros(n), zeros(m)
     t0 = time.time()
     with pytest.raises(lsq.LsqError) as e:
         lsq.lsq_lsir(handle, dev(P.A), dev(P.b), m, n, 4 * n, "bf16", "f32", "f32", "f64", 1e-6, 0,
-                     {"expire_sync": 1, "wait_limit_us": 20000}, x, r)
+                     {"expire_sync": 1, "wait_limit_us": 20000, "arnoldi": arnoldi}, x, r)
     assert e.value.status == TIMEOUT
     assert time.time() - t0 < 30.0          # one expired 20 ms wait, the rest of the batch skipped
     _solve_ok(lsq, handle, P)               # same handle, no leftover error or barrier state

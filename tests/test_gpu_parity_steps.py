@@ -17,6 +17,8 @@
 * lsq_lsir_host returns bit for bit what lsq_lsir returns on the same data.
 * Every problem of a batched call against the oracle's reference solution (4u).
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -32,6 +34,7 @@ def zeros(k):
     return torch.zeros(k, dtype=torch.float64, device="cuda")
 
 
+@functools.lru_cache(maxsize=2)
 def _setup(m, n, kappa, seed):
     P = randsvd_problem(m, n, kappa, rho=1e-3, seed=seed)
     s = 4 * n
@@ -43,9 +46,15 @@ def _setup(m, n, kappa, seed):
     return P, s, R, x0, r0, sv
 
 
-@pytest.mark.parametrize("uw,kappa", [("f64", 1e3), ("f64", 1e6), ("f32", 1e3), ("f32", 1e5)])
-def test_refinement_step_matches_oracle(lsq, handle, uw, kappa):
-    m, n = 3000, 60
+@pytest.mark.parametrize("uw,kappa,arnoldi,m", [
+    ("f64", 1e3, 1, 3000), ("f64", 1e6, 1, 3000), ("f32", 1e3, 1, 3000), ("f32", 1e5, 1, 3000),
+    ("f64", 1e6, 2, 3000), ("f32", 1e5, 2, 3000), ("f64", 1e5, 2, 400000), ("f32", 1e5, 2, 400000),
+    ("f64", 1e6, 3, 3000), ("f32", 1e5, 3, 400000)])
+def test_refinement_step_matches_oracle(lsq, handle, uw, kappa, arnoldi, m):
+    """arnoldi = 1: classical Gram-Schmidt with the selective second pass; 2: modified
+    Gram-Schmidt (the oracle's form) with the work vector in shared memory; 3: the same
+    with it in global memory (m = 4e5 runs the unrolled row loop)."""
+    n = 60 if m <= 3000 else 40
     P, s, R, x0, r0, sv = _setup(m, n, kappa, seed=11)
     tol = 1e-10 if uw == "f64" else 1e-6
     ua = 2.0 ** -53 if uw == "f64" else 2.0 ** -24
@@ -53,7 +62,7 @@ def test_refinement_step_matches_oracle(lsq, handle, uw, kappa):
     xo, ro, io = lsir.refine(P.A, P.b, R, x0, r0, ua, tol, 1, 50, dt, "f64")
     x, r = dev(x0), dev(r0)
     st, info = lsq.lsq_ir_step(handle, dev(P.A), dev(P.b), m, n, s, "f64", "f64", uw, "f64", tol, 5,
-                               {"gmres_maxit": 50}, dev(colmajor(R)), x, r)
+                               {"gmres_maxit": 50, "arnoldi": arnoldi}, dev(colmajor(R)), x, r)
     kg, ko = info.gmres_its[0], io["gmres_its"][0]
     assert st == (0 if info.gmres_relres[0] <= tol else 1)
     assert abs(kg - ko) <= (0 if uw == "f64" else 1), (kg, ko)
@@ -65,7 +74,7 @@ def test_refinement_step_matches_oracle(lsq, handle, uw, kappa):
     dg = np.concatenate([drg, R @ dxg])
     do = np.concatenate([dro, R @ dxo])
     rel = np.linalg.norm(dg - do) / np.linalg.norm(do)
-    print(uw, kappa, "its", kg, ko, "kappa_p", kp, "rel", rel, "bound", bound)
+    print(uw, kappa, arnoldi, m, "its", kg, ko, "kappa_p", kp, "rel", rel, "bound", bound)
     assert rel <= bound, (rel, bound)
     # the updated residual and solution themselves
     assert np.linalg.norm(r.cpu().numpy() - ro) <= bound * np.linalg.norm(do) + 1e-300
