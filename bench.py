@@ -737,8 +737,8 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- single cases for profilers
-CASES = ("lsir_m4e6", "fgmres_pass_m2e5_n1000", "arnoldi_m1e6_n1000", "sketch_m2e5_n1000", "batched_512",
-         "batched_64", "batched_16")
+CASES = ("lsir_m4e6", "fgmres_pass_m2e5_n1000", "arnoldi_m1e6_n1000", "arnoldi_m1e6_n200", "sketch_m2e5_n1000",
+         "batched_512", "batched_64", "batched_16")
 
 
 def run_case(name):
@@ -747,7 +747,8 @@ def run_case(name):
     lsir_m4e6: one lsq_lsir of the bench workload.  fgmres_pass_m2e5_n1000: one
     refinement step (six FGMRES iterations, CUDA graphs off) on a 200000 x 1000
     Gaussian A.  arnoldi_m1e6_n1000: one refinement step of up to 40 FGMRES
-    iterations on a 1e6 x 1000, kappa = 1e7 problem.  sketch_m2e5_n1000: one
+    iterations on a 1e6 x 1000, kappa = 1e7 problem (arnoldi_m1e6_n200: the same on a
+    1e6 x 200 problem, 2.4 GB on the device).  sketch_m2e5_n1000: one
     lsq_sketch (s = 4000, BF16X3) of a 200000 x 1000 Gaussian A.  batched_512: the batched
     configuration (512 problems, one warm-up and one timed grouped call); batched_64: its
     first 64 problems (and the per-problem mode on them); batched_16: its first 16 problems,
@@ -774,9 +775,10 @@ def run_case(name):
         return (torch.randn(m, n, dtype=torch.float64, device="cuda"),
                 torch.randn(m, dtype=torch.float64, device="cuda"))
 
-    if name == "lsir_m4e6" or name == "arnoldi_m1e6_n1000":
+    if name in ("lsir_m4e6", "arnoldi_m1e6_n1000", "arnoldi_m1e6_n200"):
         m = WL["m"] if name == "lsir_m4e6" else 1_000_000
-        n, s = WL["n"], WL["s"]
+        n = 200 if name == "arnoldi_m1e6_n200" else WL["n"]
+        s = 4 * n
         gen = DeviceRandsvd(m, n, seed=WL["data_seed"])
         A, b, _ = gen.problem(WL["kappa"], WL["rho"])
         gen.release()
