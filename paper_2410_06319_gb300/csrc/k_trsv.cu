@@ -282,11 +282,217 @@ __global__ void __launch_bounds__(kTrsvClThreads)
   cl_sync();
 }
 
+// ------------------------------------------------------------ cluster solve, streamed tiles
+// The same data flow where the row panels do not fit in the cluster's shared memory
+// (n = 1000 in FP32: 2 MB of triangle against 1.8 MB).  The owner warp of block k
+// needs M_kj only when x_j arrives, in a known order, so it streams the 32 x 32 tiles
+// through a ring of kTrsvRing slots of its own (one bulk copy per tile row, completion
+// on the slot's mbarrier), issued kTrsvRing dependencies ahead; the critical path is
+// unchanged (one cluster hop plus two 32 x 32 products per block).
+constexpr int kTrsvRing = 4;
+
+// Shared memory of a CTA of the streamed solve (the largest owner count).
+template <typename T>
+__host__ __device__ inline size_t cls_smem(int n) {
+  const int nb = (n + 31) / 32;
+  const size_t nown = (size_t)((nb + kTrsvCl - 1) / kTrsvCl);
+  const size_t head = ((size_t)32 * nb * sizeof(T) + 8 * (size_t)nb + 15) & ~(size_t)15;
+  const size_t slot = (size_t)32 * ClPanel<T>::stride(32) * sizeof(T);
+  return head + nown * kTrsvRing * 8 + nown * 1024 * sizeof(T) + nown * kTrsvRing * slot;
+}
+
+template <typename T, typename TIN, typename TOUT, bool UPPER>
+__global__ void __launch_bounds__(kTrsvClThreads)
+    trsv_stream_kernel(const T* __restrict__ Q, int64_t ld, const T* __restrict__ D, int n,
+                       const TIN* __restrict__ y, double yscale, TOUT* __restrict__ x, const int* done,
+                       const int* jp, int64_t ys, int64_t xstr, int* err) {
+  using P = ClPanel<T>;
+  constexpr int TS = 32 + P::VE;   // ring row stride (P::stride(32))
+  if (done && *done) return;   // uniform over the cluster: no CTA reaches a cluster barrier
+  if (jp) {
+    const int64_t j = *jp;
+    y += j * ys;
+    x += j * xstr;
+  }
+  extern __shared__ __align__(16) unsigned char cl_buf[];
+  const int nb = (n + 31) >> 5;
+  const uint32_t q = cl_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // ---- layout: [x: 32 nb][bars: nb] (same offsets in every CTA: remote addresses are
+  // mapped) [ring bars: nown x kTrsvRing][D of owned blocks][rings: nown x kTrsvRing x 32 x TS]
+  T* xall = reinterpret_cast<T*>(cl_buf);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cl_buf + (size_t)32 * nb * sizeof(T));
+  unsigned char* cur = cl_buf + (((size_t)32 * nb * sizeof(T) + 8 * (size_t)nb + 15) & ~(size_t)15);
+  const int nown = (nb - (int)q + kTrsvCl - 1) / kTrsvCl;   // blocks q, q + 8, ... below nb
+  uint64_t* rbars = reinterpret_cast<uint64_t*>(cur);
+  cur += (size_t)nown * kTrsvRing * 8;
+  T* dblk = reinterpret_cast<T*>(cur);
+  cur += (size_t)nown * 1024 * sizeof(T);
+  T* ring = reinterpret_cast<T*>(cur);
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t xall0 = smem_u32(xall);
+  __shared__ uint64_t load_bar;
+  const uint32_t lbar = smem_u32(&load_bar);
+  if (tid == 0) {
+    for (int k = 0; k < nb; ++k) mbar_init(bar0 + 8 * k, 1);
+    for (int e = 0; e < nown * kTrsvRing; ++e) mbar_init(smem_u32(rbars + e), 1);
+    mbar_init(lbar, 1);
+    fence_barrier_init();
+    for (int k = 0; k < nb; ++k) mbar_arrive_expect_tx(bar0 + 8 * k, 32u * (uint32_t)sizeof(T));
+  }
+  // zero what the copies never cover: rows past the matrix in every slot of the last
+  // block's ring, and (upper) the column tail of slot 0, which takes the partial last
+  // column block as every block's first dependency
+  const int tail_valid = n - 32 * (nb - 1);                                  // 1 .. 32
+  const int tail_copied = (tail_valid + P::VE - 1) / P::VE * P::VE;
+  for (int t = 0; t < nown; ++t) {
+    const int k = (int)q + t * kTrsvCl;
+    const int rows = min(32, n - 32 * k);
+    T* rt = ring + (size_t)t * kTrsvRing * 32 * TS;
+    for (int e = tid; e < kTrsvRing * (32 - rows) * 32; e += blockDim.x) {
+      const int sl = e / ((32 - rows) * 32), r = rows + (e / 32) % (32 - rows), cc = e % 32;
+      rt[((size_t)sl * 32 + r) * TS + cc] = T(0);
+    }
+    if (UPPER && tail_copied < 32)
+      for (int e = tid; e < 32 * (32 - tail_copied); e += blockDim.x)
+        rt[(size_t)(e / (32 - tail_copied)) * TS + tail_copied + e % (32 - tail_copied)] = T(0);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0) mbar_arrive_expect_tx(lbar, (uint32_t)(nown * 1024 * sizeof(T)));
+    __syncwarp();
+    if (lane < nown)
+      bulk_load(smem_u32(dblk + (size_t)lane * 1024), D + (size_t)((int)q + lane * kTrsvCl) * 1024,
+                1024u * (uint32_t)sizeof(T), lbar);
+  }
+  // every CTA's barriers are initialised before anyone sends
+  cl_sync();
+  if (warp < nown) {
+    const int t = warp;
+    const int k = (int)q + t * kTrsvCl;
+    const int rows = min(32, n - 32 * k);
+    T* rt = ring + (size_t)t * kTrsvRing * 32 * TS;
+    const uint32_t rb0 = smem_u32(rbars + t * kTrsvRing);
+    const int ndep = UPPER ? nb - 1 - k : k;
+    // tile M_kj of dependency d into slot d % kTrsvRing: row r is Q[32k + r][32j ..]
+    auto issue = [&](int d) {
+      const int j = UPPER ? nb - 1 - d : d;
+      const int valid = min(32, n - 32 * j);
+      const uint32_t seg = (uint32_t)((valid + P::VE - 1) / P::VE * 16);
+      const int sl = d % kTrsvRing;
+      if (lane == 0) mbar_arrive_expect_tx(rb0 + 8 * sl, seg * (uint32_t)rows);
+      __syncwarp();
+      if (lane < rows)
+        bulk_load(smem_u32(rt + ((size_t)sl * 32 + lane) * TS), Q + (size_t)(32 * k + lane) * ld + 32 * j, seg,
+                  rb0 + 8 * sl);
+    };
+    int issued = min(kTrsvRing, ndep), landed = 0;
+    for (int d = 0; d < issued; ++d) issue(d);
+    T acc = (lane < rows) ? (T)((double)y[32 * k + lane] * yscale) : T(0);
+    bool ok = mbar_wait(lbar, 0, err, DEV_TIMEOUT_FULL);
+    for (int d = 0; d < ndep && ok; ++d) {
+      const int j = UPPER ? nb - 1 - d : d;
+      ok = mbar_wait(rb0 + 8 * (d % kTrsvRing), (uint32_t)(d / kTrsvRing) & 1u, err, DEV_TIMEOUT_FULL);
+      if (!ok) break;
+      landed = d + 1;
+      ok = cl_wait(bar0 + 8 * j, err);
+      if (!ok) break;
+      const T* pr = rt + ((size_t)(d % kTrsvRing) * 32 + lane) * TS;
+      const T* xj = xall + 32 * j;
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 32; c += P::VE) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 mv = *reinterpret_cast<const float4*>(pr + c);
+          const float4 xv = *reinterpret_cast<const float4*>(xj + c);
+          s += mv.x * xv.x + mv.y * xv.y + mv.z * xv.z + mv.w * xv.w;
+        } else {
+          const double2 mv = *reinterpret_cast<const double2*>(pr + c);
+          const double2 xv = *reinterpret_cast<const double2*>(xj + c);
+          s += mv.x * xv.x + mv.y * xv.y;
+        }
+      }
+      acc -= s;
+      __syncwarp();   // every lane has read the slot before it is refilled
+      if (d + kTrsvRing < ndep) {
+        issue(d + kTrsvRing);
+        issued = d + kTrsvRing + 1;
+      }
+    }
+    // after an expired wait: let the copies still in flight land (bounded) before leaving
+    for (int d = landed; d < issued; ++d)
+      mbar_wait(rb0 + 8 * (d % kTrsvRing), (uint32_t)(d / kTrsvRing) & 1u, err, DEV_TIMEOUT_FULL);
+    // x_k = D_k^-1 y_k (lane r: sum_c D[c][r] y_c), then to every CTA of the cluster
+    const T* dk = dblk + (size_t)t * 1024;
+    T xa = T(0), xb = T(0);
+#pragma unroll 8
+    for (int c = 0; c < 32; c += 2) {
+      xa += dk[c * 32 + lane] * __shfl_sync(0xffffffffu, acc, c);
+      xb += dk[(c + 1) * 32 + lane] * __shfl_sync(0xffffffffu, acc, c + 1);
+    }
+    T xk = xa + xb;
+    if (lane >= rows) xk = T(0);
+    constexpr int EP = 16 / (int)sizeof(T);
+    constexpr int PIECES = 32 / EP;
+    const uint32_t dst = (uint32_t)(lane & (kTrsvCl - 1));
+    const uint32_t rx = cl_map(xall0 + (uint32_t)(32 * k * sizeof(T)), dst);
+    const uint32_t rbr = cl_map(bar0 + 8 * k, dst);
+#pragma unroll
+    for (int pc = lane / kTrsvCl; pc < PIECES; pc += 32 / kTrsvCl) {
+      uint4 v;
+      if constexpr (sizeof(T) == 4) {
+        v.x = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 0));
+        v.y = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 1));
+        v.z = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 2));
+        v.w = __float_as_uint(__shfl_sync(0xffffffffu, xk, pc * EP + 3));
+      } else {
+        const double d0 = __shfl_sync(0xffffffffu, xk, pc * EP + 0);
+        const double d1 = __shfl_sync(0xffffffffu, xk, pc * EP + 1);
+        v.x = (uint32_t)__double2loint(d0);
+        v.y = (uint32_t)__double2hiint(d0);
+        v.z = (uint32_t)__double2loint(d1);
+        v.w = (uint32_t)__double2hiint(d1);
+      }
+      st_async_16(rx + (uint32_t)(pc * 16), v, rbr);
+    }
+    if (lane < rows) x[32 * k + lane] = (TOUT)xk;
+  }
+  // ---- leave only when every x has landed here (no st.async still targets this CTA)
+  // and every tile copy issued here has completed
+  if (tid == 0)
+    for (int k = 0; k < nb; ++k) cl_wait(bar0 + 8 * k, err);
+  __syncthreads();
+  cl_sync();
+}
+
 template <typename T, typename TIN, typename TOUT, bool UPPER>
 static cudaError_t launch_trsv_cluster(const T* Q, int64_t ld, const T* D, int n, const TIN* y, double yscale,
                                        TOUT* x, const int* done, cudaStream_t st, const int* jp, int64_t ys,
                                        int64_t xstr, int* err, size_t smem) {
   auto kern = trsv_cluster_kernel<T, TIN, TOUT, UPPER>;
+  cudaError_t e = allow_dyn_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kTrsvCl);
+  cfg.blockDim = dim3(kTrsvClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTrsvCl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, Q, ld, D, n, y, yscale, x, done, jp, ys, xstr, err);
+}
+
+template <typename T, typename TIN, typename TOUT, bool UPPER>
+static cudaError_t launch_trsv_stream(const T* Q, int64_t ld, const T* D, int n, const TIN* y, double yscale,
+                                      TOUT* x, const int* done, cudaStream_t st, const int* jp, int64_t ys,
+                                      int64_t xstr, int* err, size_t smem) {
+  auto kern = trsv_stream_kernel<T, TIN, TOUT, UPPER>;
   cudaError_t e = allow_dyn_smem(kern, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -325,6 +531,15 @@ cudaError_t launch_trsv(bool upper, const Tri<T>& f, const TIN* y, double yscale
                                                           jp, ys, xstr, f.err, csm)
                  : launch_trsv_cluster<T, TIN, TOUT, false>(f.R, f.ld, f.DL, (int)f.n, y, yscale, x, done,
                                                            st, jp, ys, xstr, f.err, csm);
+  }
+  // past that, the cluster solve with streamed tiles (at most one block per warp)
+  const int nbk = (int)((f.n + 31) / 32);
+  const size_t ssm = cls_smem<T>((int)f.n);
+  if (f.n > 32 && nbk <= kTrsvCl * (kTrsvClThreads / 32) && ssm <= 200 * 1024) {
+    return upper ? launch_trsv_stream<T, TIN, TOUT, true>(f.L, f.ld, f.DU, (int)f.n, y, yscale, x, done, st, jp,
+                                                         ys, xstr, f.err, ssm)
+                 : launch_trsv_stream<T, TIN, TOUT, false>(f.R, f.ld, f.DL, (int)f.n, y, yscale, x, done, st,
+                                                          jp, ys, xstr, f.err, ssm);
   }
   const size_t smem = TrsvSmem<T>::bytes;
   if (upper) {

@@ -46,15 +46,16 @@ def _setup(m, n, kappa, seed):
     return P, s, R, x0, r0, sv
 
 
-@pytest.mark.parametrize("uw,kappa,arnoldi,m", [
-    ("f64", 1e3, 1, 3000), ("f64", 1e6, 1, 3000), ("f32", 1e3, 1, 3000), ("f32", 1e5, 1, 3000),
-    ("f64", 1e6, 2, 3000), ("f32", 1e5, 2, 3000), ("f64", 1e5, 2, 400000), ("f32", 1e5, 2, 400000),
-    ("f64", 1e6, 3, 3000), ("f32", 1e5, 3, 400000)])
-def test_refinement_step_matches_oracle(lsq, handle, uw, kappa, arnoldi, m):
+@pytest.mark.parametrize("uw,kappa,arnoldi,m,n", [
+    ("f64", 1e3, 1, 3000, 60), ("f64", 1e6, 1, 3000, 60), ("f32", 1e3, 1, 3000, 60), ("f32", 1e5, 1, 3000, 60),
+    ("f64", 1e6, 2, 3000, 60), ("f32", 1e5, 2, 3000, 60), ("f64", 1e5, 2, 400000, 40),
+    ("f32", 1e5, 2, 400000, 40), ("f64", 1e6, 3, 3000, 60), ("f32", 1e5, 3, 400000, 40),
+    ("f64", 1e4, 1, 4000, 1000), ("f32", 1e4, 1, 4000, 1000)])
+def test_refinement_step_matches_oracle(lsq, handle, uw, kappa, arnoldi, m, n):
     """arnoldi = 1: classical Gram-Schmidt with the selective second pass; 2: modified
     Gram-Schmidt (the oracle's form) with the work vector in shared memory; 3: the same
-    with it in global memory (m = 4e5 runs the unrolled row loop)."""
-    n = 60 if m <= 3000 else 40
+    with it in global memory (m = 4e5 runs the unrolled row loop).  n = 1000: the
+    triangular solves run on the cluster with streamed tiles."""
     P, s, R, x0, r0, sv = _setup(m, n, kappa, seed=11)
     tol = 1e-10 if uw == "f64" else 1e-6
     ua = 2.0 ** -53 if uw == "f64" else 2.0 ** -24
@@ -80,7 +81,8 @@ def test_refinement_step_matches_oracle(lsq, handle, uw, kappa, arnoldi, m):
     assert np.linalg.norm(r.cpu().numpy() - ro) <= bound * np.linalg.norm(do) + 1e-300
 
 
-@pytest.mark.parametrize("m,n,kappa", [(3000, 60, 1e2), (2500, 130, 1e4), (4000, 200, 1e6)])
+@pytest.mark.parametrize("m,n,kappa", [(3000, 60, 1e2), (2500, 130, 1e4), (4000, 200, 1e6), (3500, 760, 1e3),
+                                       (4000, 1000, 1e4)])
 def test_fp32_lsqr_iterates_elementwise(lsq, handle, m, n, kappa):
     """Both sides take exactly k FP32 iterations (tol 0) from the oracle's x_s with the
     oracle's R; the oracle's FP64 LSQR with the same R, start and k is the yardstick.
