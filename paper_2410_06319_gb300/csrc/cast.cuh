@@ -100,6 +100,20 @@ LSQ_HD bool cast_terms_int(uint64_t u, int k, uint32_t (&t)[3]) {
   return enc_term<F>(sg, a, E - 1075 + k, t[0], rd);
 }
 
+// fl32(x) for x given by its FP64 bits, when the result is a normal FP32 number or an
+// infinity reached by rounding (biased FP64 exponent 897 .. 1150): round the 53-bit
+// significand at bit 29 to nearest even by one 64-bit add (a carry out of the fraction
+// moves into the exponent, up to the infinity past FP32's largest value), then rebias
+// the exponent.  False otherwise (zero, subnormal results, non-finite x).
+LSQ_HD bool f64_to_f32_bits(uint64_t u, uint32_t& out) {
+  const uint32_t e = (uint32_t)(u >> 52) & 0x7FFu;
+  if (e < 897u || e > 1150u) return false;
+  const uint64_t r = u + 0x0FFFFFFFull + ((u >> 29) & 1ull);
+  const uint32_t mag = (uint32_t)(((r >> 29) & 0x3FFFFFFFFull) - (896ull << 23));
+  out = ((uint32_t)(u >> 32) & 0x80000000u) | mag;
+  return true;
+}
+
 // ---------------------------------------------------------------- BF16X3
 LSQ_HD float f32_of(uint32_t b) {
 #ifdef __CUDA_ARCH__

@@ -85,13 +85,23 @@ cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t 
 // fl32(2^k x) as FP32 bits, x given by its FP64 bits: integer rounding, else the FP64
 // definition (subnormal results, non-finite or subnormal x).
 __device__ __forceinline__ uint32_t f32_scaled_bits(uint64_t u, int k) {
+  // normal x with 2^k x in FP32's range: scale the FP64 exponent, one-add rounding
+  const int e = (int)((u >> 52) & 0x7FF);
+  uint32_t b;
+  if (e > 0 && e < 0x7FF && e + k > 0 && e + k < 0x7FF &&
+      f64_to_f32_bits(u + ((uint64_t)(int64_t)k << 52), b))
+    return b;
   uint32_t t[3];
   if (cast_terms_int<EncF32>(u, k, t)) return t[0];
   return __float_as_uint(__double2float_rn(ldexp(__longlong_as_double((long long)u), k)));
 }
 
 // FP64 bits -> FP32 value, round to nearest even.
-__device__ __forceinline__ float f64bits_to_f32(uint64_t u) { return __uint_as_float(f32_scaled_bits(u, 0)); }
+__device__ __forceinline__ float f64bits_to_f32(uint64_t u) {
+  uint32_t b;
+  if (f64_to_f32_bits(u, b)) return __uint_as_float(b);
+  return __uint_as_float(f32_scaled_bits(u, 0));
+}
 
 __device__ __forceinline__ void colmax_a32_body(const double* __restrict__ A, int64_t lda,
                                                 const double* __restrict__ b, int64_t m, int64_t n,
@@ -108,8 +118,18 @@ __device__ __forceinline__ void colmax_a32_body(const double* __restrict__ A, in
   for (int64_t c = threadIdx.x; c < cend; c += blockDim.x) {
     uint64_t mx = 0;
     if (c < n) {
-#pragma unroll 4
-      for (int64_t i = r0; i < r1; ++i) {
+      int64_t i = r0;
+      for (; i + 8 <= r1; i += 8) {   // eight loads in flight before any use
+        uint64_t u[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u[q] = __ldcs(Au + (i + q) * lda + c);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          mx = max(mx, u[q] & kAbs);
+          if (a32) a32[(i + q) * lda32 + c] = f64bits_to_f32(u[q]);
+        }
+      }
+      for (; i < r1; ++i) {
         const uint64_t u = __ldcs(Au + i * lda + c);
         mx = max(mx, u & kAbs);
         if (a32) a32[i * lda32 + c] = f64bits_to_f32(u);
@@ -259,12 +279,21 @@ __device__ __forceinline__ void cast_bf16x3_body(const double* __restrict__ A, i
   const int k = (c <= n) ? kexp[c] : 0;
   const uint64_t* Au = reinterpret_cast<const uint64_t*>(A);
   const uint64_t* bu = reinterpret_cast<const uint64_t*>(b);
-  for (int r = threadIdx.y; r < kCast3Rows; r += 8) {
+  // the FP32 copy's values of the thread's column, all loads in flight before any use
+  constexpr int kPer = kCast3Rows / 8;
+  uint32_t av[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int64_t j = j0 + threadIdx.y + 8 * q;
+    av[q] = (a32 != nullptr && c < n && j < m) ? __float_as_uint(__ldcs(a32 + j * lda32 + c)) : 0u;
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int r = threadIdx.y + 8 * q;
     const int64_t j = j0 + r;
     uint32_t y = 0;
     if (j < m && c <= n) {
-      bool done = false;
-      if (a32 != nullptr && c < n) done = f32_scale_exact(__float_as_uint(__ldcs(a32 + j * lda32 + c)), k, y);
+      const bool done = a32 != nullptr && c < n && f32_scale_exact(av[q], k, y);
       if (!done) y = f32_scaled_bits(c < n ? __ldcs(Au + j * lda + c) : bu[j], k);
     }
     tile[threadIdx.x][r] = y;

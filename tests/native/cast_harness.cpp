@@ -1,6 +1,7 @@
 // Host harness for csrc/cast.cuh: reads "fmt" then lines "u_hex k" (FP64 bits
 // and a power-of-two exponent) and prints "ok t0 t1 t2" (hex bit patterns).
 // bf16, f16, e4m3, f32: ok = the integer rounding of 2^k * x into fmt took it.
+// f32fast: the one-add FP64 -> FP32 rounding (k ignored).
 // bf16x3: the three BF16 terms of y = fl32(2^k x), formed as the kernels do --
 // from a = fl32(x) by a power-of-two scaling where that is exact (ok = 1), else
 // from x itself (integer rounding, else the host's FP64 -> FP32 conversion).
@@ -41,6 +42,17 @@ static void run_bf16x3() {
   }
 }
 
+// f32fast: the one-add rounding of f64_to_f32_bits (ok = it took the value)
+static void run_f32fast() {
+  unsigned long long u;
+  int k;
+  while (std::scanf("%llx %d", &u, &k) == 2) {
+    uint32_t b = 0;
+    const bool ok = lsq::f64_to_f32_bits((uint64_t)u, b);
+    std::printf("%d %x 0 0\n", ok ? 1 : 0, b);
+  }
+}
+
 int main() {
   char fmt[16] = {0};
   if (std::scanf("%15s", fmt) != 1) return 2;
@@ -49,6 +61,7 @@ int main() {
   else if (!std::strcmp(fmt, "f16")) run<lsq::EncF16>();
   else if (!std::strcmp(fmt, "e4m3")) run<lsq::EncE4M3>();
   else if (!std::strcmp(fmt, "f32")) run<lsq::EncF32>();
+  else if (!std::strcmp(fmt, "f32fast")) run_f32fast();
   else return 2;
   return 0;
 }

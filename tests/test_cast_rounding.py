@@ -172,3 +172,29 @@ def test_bf16x3_terms_match_oracle_cast(harness):
     # the FP32 copy's scaling carries the bulk of a column's entries
     assert fast[:12200].mean() > 0.99
     assert not np.all(fast[-3000:])
+
+
+def test_one_add_fp32_rounding_matches_numpy(harness):
+    """The column-max pass's FP64 -> FP32 rounding (one 64-bit add at bit 29, then an
+    exponent rebias) against numpy's conversion: bit-exact wherever it takes the value
+    (including the rounding overflow to infinity just below 2^128), and it takes every
+    input in [2^-126, 2^128); the rest goes to the FP64 definition."""
+    u, _ = inputs(14, "f32")
+    r = np.random.default_rng(15)
+    # ties at bit 29, values around FP32's largest and smallest normal numbers
+    tie = (np.uint64(1023 + r.integers(-100, 100, 3000)) << np.uint64(52)) | \
+          (r.integers(0, 2 ** 23, 3000).astype(np.uint64) << np.uint64(29)) | np.uint64(1 << 28)
+    big = np.ldexp(1.0 + r.random(2000) * 2.0 ** -20, 127) * (1.0 + 2.0 ** -23 * r.random(2000))
+    big = np.concatenate([big, [float.fromhex("0x1.fffffefp127"), float.fromhex("0x1.ffffffp127"),
+                                float.fromhex("0x1.fffffe8p127")]])
+    small = np.ldexp(1.0 + r.random(2000), -126 + r.integers(-2, 3, 2000))
+    u = np.concatenate([u, tie, big.view(np.uint64), small.view(np.uint64), (-small).view(np.uint64)])
+    ok, t = run(harness, "f32fast", u, np.zeros(len(u), dtype=np.int64))
+    x = u.view(np.float64)
+    with np.errstate(over="ignore", invalid="ignore"):
+        y = x.astype(np.float32)
+    with np.errstate(invalid="ignore"):
+        normal_in = np.isfinite(x) & (np.abs(x) >= 2.0 ** -126) & (np.abs(x) < 2.0 ** 128)
+    assert np.all(ok[normal_in]), np.flatnonzero(normal_in & ~ok)[:10]
+    assert np.array_equal(t[ok, 0], y[ok].view(np.uint32)), np.flatnonzero(t[ok, 0] != y[ok].view(np.uint32))[:10]
+    assert np.any(ok & np.isinf(y)) and ok.sum() > 10000
