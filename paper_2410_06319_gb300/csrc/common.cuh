@@ -268,6 +268,22 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Warp totals of two values by a reduce-scatter butterfly: at the first exchange lanes
+// 0-15 keep a and lanes 16-31 keep b, each adding its partner's copy, so a lane adds
+// 1 + 4 numbers instead of 2 x 5 (the FP64 pipe is narrow on GB300).  Every lane of a
+// half ends with the same bits; a and b receive the totals in every lane.
+template <typename T>
+__device__ __forceinline__ void warp_sum2(T& a, T& b) {
+  const bool hi = (threadIdx.x & 16) != 0;
+  T keep = hi ? b : a;
+  const T give = hi ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, give, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  a = __shfl_sync(0xffffffffu, keep, 0);
+  b = __shfl_sync(0xffffffffu, keep, 16);
+}
+
 // Sums of eight values over a warp by a reduce-scatter butterfly: at each exchange a
 // lane keeps half of its values and adds its partner's copies of them, so a lane adds
 // 4 + 2 + 1 + 1 + 1 FP64 numbers instead of 8 x 5 (GB300's FP64 pipe is narrow).

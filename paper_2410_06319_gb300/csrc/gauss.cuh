@@ -249,6 +249,18 @@ __device__ __forceinline__ double bits_to_double(uint32_t v) {
   }
 }
 
+template <int FMT>
+__device__ __forceinline__ float bits_to_float(uint32_t v) {
+  if constexpr (FMT == FMT_F16) {
+    return __half2float(__ushort_as_half((unsigned short)v));
+  } else if constexpr (FMT == FMT_BF16) {
+    return __uint_as_float(v << 16);
+  } else {
+    __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)v, __NV_E4M3);
+    return __half2float(__half(hr));
+  }
+}
+
 // Rounds one FP32 estimate g to u_s; returns false when the FP64 definition is
 // needed.  The true value lies within d = 2^-19 |g| of g, which is below 32
 // FP32 ulps of g; if the nearest rounding midpoint of u_s (the FP32 pattern

@@ -114,8 +114,7 @@ __device__ __forceinline__ void pass_body(PassArgs<T> p, int64_t blk, int64_t nb
         d = fma(a[v][k], xv[v][k], d);
         d2 = fma(a2[v][k], xv[v][k], d2);
       }
-    d = warp_sum(d);
-    d2 = warp_sum(d2);
+    warp_sum2(d, d2);
     T c1, c2 = T(0);
     if (MODE == PM_LSQR) {
       const T q = d + cu * p.uin[i];

@@ -963,7 +963,7 @@ struct SketchFixArgs {
 struct FixRec {
   uint32_t i, pad;
   uint64_t j0;
-  double de, dodd;
+  float de, dodd;   // exact minus estimate: differences of nearby values of the format, exact in FP32
 };
 
 template <int FMT>
@@ -1020,9 +1020,9 @@ __global__ void __launch_bounds__(kFixThreads)
       uint32_t fe, fo, xe, xo;
       gauss_pair_fast<GF>(pa, pb, fe, fo);
       gauss_pair_slow<GF>(pa, pb, xe, xo);
-      r.de = bits_to_double<GF>(xe) - bits_to_double<GF>(fe);
-      r.dodd = bits_to_double<GF>(xo) - bits_to_double<GF>(fo);
-      keep = (r.de != 0.0 || r.dodd != 0.0) && (int64_t)r.i < f.s;
+      r.de = __fsub_rn(bits_to_float<GF>(xe), bits_to_float<GF>(fe));
+      r.dodd = __fsub_rn(bits_to_float<GF>(xo), bits_to_float<GF>(fo));
+      keep = (r.de != 0.0f || r.dodd != 0.0f) && (int64_t)r.i < f.s;
     }
     // ---- ordered compaction of the kept pairs
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -1035,25 +1035,29 @@ __global__ void __launch_bounds__(kFixThreads)
     }
     if (keep) kept[before + __popc(bal & ((1u << lane) - 1u))] = r;
     __syncthreads();
-    // ---- phase 2: partial[i][col] += d * A_s[j][col]
+    // ---- phase 2: partial[i][col] += d * A_s[j][col], in FP32 like the GEMM.  d is one
+    // step of the format (a power of two) or the difference of two nearby values of it,
+    // and A_s[j][col] has at most 24 significant bits (BF16X3: hi + lo + lo2, exact in
+    // FP32), so each product is exact; the two of a pair are summed in FP32.
     if (has_col) {
       float* pc = f.partial + (split * f.ncols + col) * f.s_pad;
       for (int q = 0; q < nkept; ++q) {
         const FixRec& k = kept[q];
-        double add = 0.0;
+        float add = 0.0f;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const double d = e ? k.dodd : k.de;
+          const float d = e ? k.dodd : k.de;
           const int64_t j = (int64_t)k.j0 + e;
-          if (d == 0.0 || j >= f.m) continue;
+          if (d == 0.0f || j >= f.m) continue;
           const uint64_t u = (col < f.n) ? Au[j * f.lda + col] : bu[j];
           uint32_t t[3];
           cast_bits<FMT>(u, kc, t);
-          double v = bits_to_double<GF>(t[0]);
-          if constexpr (FMT == FMT_BF16X3) v += bits_to_double<GF>(t[1]) + bits_to_double<GF>(t[2]);
-          add += d * v;
+          float v = bits_to_float<GF>(t[0]);
+          if constexpr (FMT == FMT_BF16X3)
+            v = __fadd_rn(__fadd_rn(v, bits_to_float<GF>(t[1])), bits_to_float<GF>(t[2]));
+          add = __fmaf_rn(d, v, add);
         }
-        pc[k.i] += (float)add;
+        pc[k.i] += add;
       }
     }
     __syncthreads();
