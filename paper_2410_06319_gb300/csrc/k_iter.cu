@@ -322,11 +322,13 @@ __global__ void __launch_bounds__(kBulkThreads, 1) pass_bulk_kernel(BulkArgs<T> 
             for (int k = 0; k < VW; ++k) a[v][k] = T(0);
           }
         }
-        T d = 0;
+        // four interleaved chains: in LSQR the row's A^T q update waits on this sum
+        T dq[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int v = 0; v < VPL; ++v)
 #pragma unroll
-          for (int k = 0; k < VW; ++k) d = fma(a[v][k], xv[v][k], d);
+          for (int k = 0; k < VW; ++k) dq[(v * VW + k) & 3] = fma(a[v][k], xv[v][k], dq[(v * VW + k) & 3]);
+        T d = (dq[0] + dq[1]) + (dq[2] + dq[3]);
         d = warp_sum(d);
         T coef;
         if (MODE == PM_LSQR) {
