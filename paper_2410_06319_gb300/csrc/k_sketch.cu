@@ -243,11 +243,9 @@ __device__ __forceinline__ void cast_transpose_body(const double* __restrict__ A
     // every (row, k) of the padded blocks is written: zeros past column n and row m
     const int64_t blk = j / kBtBlock, kk = j % kBtBlock;
     const int64_t base = (blk * planes * plane_rows + c) * kBtBlock + kk;
-    const int64_t pstride = plane_rows * kBtBlock;
     const bool live = c <= n && j < m;
     const uint64_t u = tile[threadIdx.x][r];
     const int k = live ? kexp[c] : 0;
-    (void)pstride;
     if constexpr (FMT == FMT_F32) {
       const double v = ldexp(__longlong_as_double((long long)u), k);
       reinterpret_cast<float*>(Bt)[base] = live ? __double2float_rn(v) : 0.0f;
