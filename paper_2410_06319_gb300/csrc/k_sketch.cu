@@ -314,10 +314,14 @@ __device__ __forceinline__ void cast_bf16x3_body(const double* __restrict__ A, i
   }
 }
 
+// One-dimensional grid, column tile fastest: the column tiles of a row tile run together,
+// so the 128-byte lines that neighbouring tiles share (rows of the FP32 copy need not start
+// on a line) are read from DRAM once.
 __global__ void cast_bf16x3_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ b,
                                    const float* __restrict__ a32, int64_t lda32, int64_t m, int64_t n,
                                    const int* __restrict__ kexp, void* __restrict__ Bt, int64_t plane_rows) {
-  cast_bf16x3_body(A, lda, b, a32, lda32, m, n, kexp, Bt, plane_rows, blockIdx.x, blockIdx.y);
+  const int64_t ct = (plane_rows + 31) / 32, id = blockIdx.x;
+  cast_bf16x3_body(A, lda, b, a32, lda32, m, n, kexp, Bt, plane_rows, id / ct, id % ct);
 }
 
 template <int FMT>
@@ -354,7 +358,12 @@ cudaError_t launch_cast_transpose(int fmt, const double* A, int64_t lda, const d
     case FMT_BF16: cast_transpose_kernel<FMT_BF16><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
     case FMT_E4M3: cast_transpose_kernel<FMT_E4M3><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
     case FMT_F32: cast_transpose_kernel<FMT_F32><<<grid, block, 0, st>>>(A, lda, b, m, n, kexp, Bt, plane_rows, planes); break;
-    case FMT_BF16X3: cast_bf16x3_kernel<<<grid, block, 0, st>>>(A, lda, b, a32, lda32, m, n, kexp, Bt, plane_rows); break;
+    case FMT_BF16X3: {
+      const int64_t tiles = gx * ((plane_rows + 31) / 32);
+      if (tiles > 2147483647LL) return cudaErrorInvalidValue;
+      cast_bf16x3_kernel<<<(unsigned)tiles, block, 0, st>>>(A, lda, b, a32, lda32, m, n, kexp, Bt, plane_rows);
+      break;
+    }
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1272,12 +1281,13 @@ __global__ void grouped_cast_kernel(const GCast* __restrict__ tab, const int* __
   const int p = group_of(start, nprob, blockIdx.x);
   const GCast& g = tab[p];
   const int64_t local = (int64_t)blockIdx.x - start[p];
-  if constexpr (FMT == FMT_BF16X3)
-    cast_bf16x3_body(g.A, g.lda, g.b, g.a32, g.lda32, g.m, g.n, g.kexp, g.Bt, g.plane_rows, local % g.cast_gx,
-                     local / g.cast_gx);
-  else
+  if constexpr (FMT == FMT_BF16X3) {   // column tile fastest, as cast_bf16x3_kernel
+    const int64_t ct = (g.plane_rows + 31) / 32;
+    cast_bf16x3_body(g.A, g.lda, g.b, g.a32, g.lda32, g.m, g.n, g.kexp, g.Bt, g.plane_rows, local / ct, local % ct);
+  } else {
     cast_transpose_body<FMT>(g.A, g.lda, g.b, g.m, g.n, g.kexp, g.Bt, g.plane_rows, planes, local % g.cast_gx,
                              local / g.cast_gx);
+  }
 }
 
 __global__ void grouped_sketch_reduce_kernel(const GReduce* __restrict__ tab, const int* __restrict__ start,
