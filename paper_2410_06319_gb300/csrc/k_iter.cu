@@ -1464,9 +1464,19 @@ __global__ void gm_apply_kernel(const TB* __restrict__ B, int64_t ld, int64_t le
   double s1 = 0.0, s2 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int c = 0; c < k; ++c) acc += (double)B[(int64_t)c * ld + i] * ys[c];
-    acc *= scale;
+    // four interleaved chains, their loads issued together (the loop is latency-bound)
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int c = 0;
+    for (; c + 3 < k; c += 4) {
+      const TB* bc = B + (int64_t)c * ld + i;
+      const double b0 = (double)bc[0], b1 = (double)bc[ld], b2 = (double)bc[2 * ld], b3 = (double)bc[3 * ld];
+      a0 = fma(b0, ys[c], a0);
+      a1 = fma(b1, ys[c + 1], a1);
+      a2 = fma(b2, ys[c + 2], a2);
+      a3 = fma(b3, ys[c + 3], a3);
+    }
+    for (; c < k; ++c) a0 = fma((double)B[(int64_t)c * ld + i], ys[c], a0);
+    double acc = ((a0 + a1) + (a2 + a3)) * scale;
     const double nv = d[i] + acc;
     d[i] = nv;
     s1 += acc * acc;
