@@ -49,3 +49,27 @@ def test_invalid_arguments_are_rejected_before_any_launch(lsq):
     args = [None, 1, 1, 100, 10, 40, 0, 1, 1, 0, 1e-6, 0, None, 1]
     assert lsq.lib.lsq_sketch(*args) == -1
     assert lsq.lib.lsq_omega(None, 4, 0, 4, 0, 0, 1) == -1
+
+
+def test_struct_field_offsets_match_header(lsq, tmp_path):
+    """Field by field: a C program compiled against include/lsq.h prints the offset of every
+    field the binding declares, and each equals the ctypes offset (a reordering or a type
+    change in either place fails here even where the sizes still agree)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "lsq.h"', 'int main(void) {']
+    want = []
+    for cname, cls in (("lsq_opts", lsq.Opts), ("lsq_info", lsq.Info)):
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append(getattr(cls, fname).offset)
+    lines += ['  return 0;', '}']
+    src = tmp_path / "offsets.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "offsets"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
