@@ -114,6 +114,14 @@ LSQ_HD bool f64_to_f32_bits(uint64_t u, uint32_t& out) {
   return true;
 }
 
+// fl32(2^k x) by f64_to_f32_bits on the exponent-shifted bits, for normal x with 2^k x
+// a normal FP64 number (then 2^k x is exact in FP64).  False otherwise.
+LSQ_HD bool f64_scaled_to_f32_bits(uint64_t u, int k, uint32_t& out) {
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e == 0 || e == 0x7FF || e + k <= 0 || e + k >= 0x7FF) return false;
+  return f64_to_f32_bits(u + ((uint64_t)(int64_t)k << 52), out);
+}
+
 // ---------------------------------------------------------------- BF16X3
 LSQ_HD float f32_of(uint32_t b) {
 #ifdef __CUDA_ARCH__

@@ -85,12 +85,8 @@ cudaError_t launch_omega(int fmt, int64_t s, int64_t j0, int64_t cols, uint64_t 
 // fl32(2^k x) as FP32 bits, x given by its FP64 bits: integer rounding, else the FP64
 // definition (subnormal results, non-finite or subnormal x).
 __device__ __forceinline__ uint32_t f32_scaled_bits(uint64_t u, int k) {
-  // normal x with 2^k x in FP32's range: scale the FP64 exponent, one-add rounding
-  const int e = (int)((u >> 52) & 0x7FF);
   uint32_t b;
-  if (e > 0 && e < 0x7FF && e + k > 0 && e + k < 0x7FF &&
-      f64_to_f32_bits(u + ((uint64_t)(int64_t)k << 52), b))
-    return b;
+  if (f64_scaled_to_f32_bits(u, k, b)) return b;   // normal x, 2^k x in FP32's range
   uint32_t t[3];
   if (cast_terms_int<EncF32>(u, k, t)) return t[0];
   return __float_as_uint(__double2float_rn(ldexp(__longlong_as_double((long long)u), k)));

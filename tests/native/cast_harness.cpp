@@ -32,9 +32,10 @@ static void run_bf16x3() {
     const uint32_t a = lsq::bits_of((float)x);
     uint32_t y;
     const bool fast = lsq::f32_scale_exact(a, k, y);
-    if (!fast) {
+    if (!fast) {   // the kernels' route from the FP64 value: one-add, integer, then the FP64 definition
       uint32_t t1[3];
-      y = lsq::cast_terms_int<lsq::EncF32>((uint64_t)u, k, t1) ? t1[0] : lsq::bits_of((float)std::ldexp(x, k));
+      if (!lsq::f64_scaled_to_f32_bits((uint64_t)u, k, y))
+        y = lsq::cast_terms_int<lsq::EncF32>((uint64_t)u, k, t1) ? t1[0] : lsq::bits_of((float)std::ldexp(x, k));
     }
     uint32_t t[3];
     lsq::split3_f32(y, t);
